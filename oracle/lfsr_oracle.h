@@ -1,0 +1,72 @@
+/*
+ * FP64 CPU oracle for the light-field super-resolution ADMM of
+ * "A GPU-Accelerated Light-field Super-resolution Framework Based on Mixed
+ * Noise Model and Weighted Regularization" (arXiv 2206.05047).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the slow, plain reference that
+ * the CUDA path is checked against.  Only the test-suite, the smoke check and
+ * the benchmark's CPU-baseline leg may load it; the product path never does.
+ * It shares no code, header or table with the CUDA library.
+ *
+ * Images are row-major double arrays.  HR images are (zeta*H) x (zeta*W),
+ * LR images H x W, view k = v*U + u.
+ */
+#ifndef LFSR_ORACLE_H
+#define LFSR_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_problem {
+  int U, V;               /* angular grid                                   */
+  int H, W;               /* LR size                                        */
+  int zeta;               /* scale factor                                   */
+  int kb;                 /* blur kernel size (odd)                         */
+  const double *blur;     /* kb*kb taps, K[a+r][b+r]                        */
+  const double *disp;     /* HR disparity map on the reference grid         */
+  double lambda1, lambda2;/* data-term weights (Eq. sr_fin)                 */
+  double mu;              /* ADMM penalty (vartheta in Algorithm 1)         */
+  int window, patch;      /* NLTV search window and patch (odd)             */
+  double h;               /* NLTV filtering parameter                       */
+  int cg_iters;           /* K of Algorithm 2                               */
+  double cg_tol;          /* tau of Algorithm 2 (stop when pi <= tau)       */
+  int freeze_weights;     /* test option: weights from x0, then fixed       */
+} orc_problem;
+
+int    orc_num_threads(void);
+void   orc_set_threads(int n);
+
+/* geometry */
+int    orc_num_dirs(const orc_problem *P);
+void   orc_dirs(const orc_problem *P, int *di, int *dj);
+void   orc_view_theta(const orc_problem *P, int k, double *tu, double *tv);
+
+/* degradation operators (Eq. sr_model_op, Sec. 4.1) and their adjoints */
+void   orc_warp  (const orc_problem *P, int k, const double *x, double *out);
+void   orc_warp_T(const orc_problem *P, int k, const double *g, double *out);
+void   orc_blur  (const orc_problem *P, const double *x, double *out);
+void   orc_blur_T(const orc_problem *P, const double *g, double *out);
+void   orc_down  (const orc_problem *P, const double *x, double *out);
+void   orc_up    (const orc_problem *P, const double *g, double *out);
+void   orc_A     (const orc_problem *P, int k, const double *x, double *out);
+void   orc_A_T   (const orc_problem *P, int k, const double *g, double *out);
+
+/* weighted non-local TV (Eq. sr_reg, Sec. 4.1 wdg / wdd) */
+void   orc_weights(const orc_problem *P, const double *x, double *w);
+void   orc_S  (const orc_problem *P, const double *w, const double *x, double *out);
+void   orc_S_T(const orc_problem *P, const double *w, const double *g, double *out);
+
+/* ADMM pieces */
+void   orc_prox(long n, const double *u, double t, double *z);
+void   orc_normal_apply(const orc_problem *P, const double *w, const double *p, double *q);
+double orc_cost(const orc_problem *P, const double *y, const double *w, const double *x);
+int    orc_cg(const orc_problem *P, const double *w, const double *v, double *x,
+              int K, double tau, double *pi_out);
+int    orc_admm(const orc_problem *P, const double *y, const double *x0, int N,
+                double *x, double *wA, double *wS, double *diag);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

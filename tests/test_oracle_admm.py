@@ -1,0 +1,146 @@
+"""Pins of the oracle's ADMM (Algorithm 1 + Algorithm 2) against mathematics:
+exact fixed points, exact recovery, ADMM residual theory, and an
+independent convex solver (scipy SLSQP) for the minimiser of J (Eq. sr_fin).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+from paper_2206_05047_gb300 import synth
+
+
+def test_constant_image_is_exact_fixed_point(oracle_mod):
+    """y_k = A_k c and x0 = c: residuals, S x and duals are all zero, so CG
+    takes no step and x stays c bit for bit."""
+    rng = np.random.default_rng(4)
+    H, W, z = 6, 5, 2
+    o = oracle_mod.Oracle(3, 3, H, W, z, synth.gaussian_blur_kernel(3, 0.9),
+                          rng.uniform(-1.5, 1.5, (z * H, z * W)), window=5)
+    c = np.full(o.hr, 0.4375)
+    y = np.stack([o.A(k, c) for k in range(o.s_k)])
+    x, wA, wS, diag = o.admm(y, c, 3, diagnostics=True)
+    assert np.array_equal(x, c)
+    assert not wA.any() and not wS.any()
+    assert (diag[:, 4] == 0).all()
+
+
+def test_exact_recovery_identity_operators():
+    """zeta = 1, zero disparity, delta blur, no noise: A_k = I.  With
+    lambda1 * s_k > 2 s_d the l1 data term dominates every TV subgradient
+    (weights <= 1), so x = y is the unique minimiser and ADMM converges to
+    it whatever the weights of each iteration."""
+    from oracle import oracle as om
+    rng = np.random.default_rng(0)
+    H = W = 8
+    gt = rng.random((H, W))
+    o = om.Oracle(3, 3, H, W, 1, np.array([[1.0]]), np.zeros((H, W)), lambda1=2.0,
+                  lambda2=1.0, mu=1.0, window=3, patch=3, h=0.3, cg_iters=5)
+    assert 2.0 * 9 > 2 * 8
+    y = np.repeat(gt[None], 9, axis=0)
+    x0 = gt + 0.1 * rng.standard_normal((H, W))
+    errs = []
+    x, wA, wS = x0, None, None
+    for _ in range(4):
+        x, wA, wS = o.admm(y, x, 100, wA=wA, wS=wS)
+        errs.append(np.linalg.norm(x - gt) / np.linalg.norm(gt))
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-5
+
+
+def _tiny(oracle_mod, seed=0, mu=1.0, K=200):
+    rng = np.random.default_rng(seed)
+    o = oracle_mod.Oracle(3, 3, 2, 2, 2, synth.gaussian_blur_kernel(3, 0.8),
+                          rng.uniform(-1, 1, (4, 4)), lambda1=0.5, lambda2=2.0, mu=mu,
+                          window=3, patch=3, h=0.3, cg_iters=K, cg_tol=1e-28,
+                          freeze_weights=True)
+    y = rng.random((9, 2, 2))
+    x0 = rng.random((4, 4))
+    return o, y, x0
+
+
+def test_he_yuan_residual_non_increasing(oracle_mod):
+    """Frozen weights and an exact x-step: ||z_{n+1}-z_n||^2 + ||w_{n+1}-w_n||^2
+    (scaled dual) never increases (He and Yuan's non-ergodic ADMM result)."""
+    rng = np.random.default_rng(1)
+    o = oracle_mod.Oracle(3, 3, 3, 3, 2, synth.gaussian_blur_kernel(3, 0.8),
+                          rng.uniform(-1, 1, (6, 6)), lambda1=0.5, lambda2=2.0, mu=1.0,
+                          window=3, patch=3, h=0.3, cg_iters=200, cg_tol=1e-28,
+                          freeze_weights=True)
+    y = rng.random((9, 3, 3))
+    x0 = rng.random((6, 6))
+    _, _, _, diag = o.admm(y, x0, 60, diagnostics=True)
+    R = diag[1:, 0] + diag[1:, 1]
+    assert np.all(np.diff(R) <= 1e-10 * R[:-1])
+    assert R[-1] < 1e-2 * R[0]
+
+
+def test_fixed_point_is_minimiser_of_J(oracle_mod):
+    """With frozen weights, ADMM's limit minimises J: compare with an
+    independent solver (SLSQP on the slack reformulation of the l1 terms)."""
+    o, y, x0 = _tiny(oracle_mod, mu=3.0)
+    w = o.weights(x0)
+    p = o.p
+    cols_A, cols_S = [], []
+    for n in range(p):
+        e = np.zeros(p); e[n] = 1.0
+        e = e.reshape(o.hr)
+        cols_A.append(np.concatenate([o.A(k, e).ravel() for k in range(o.s_k)]))
+        cols_S.append(o.S(w, e).ravel())
+    A = np.array(cols_A).T
+    S = np.array(cols_S).T
+    S = S[np.abs(S).sum(1) > 0]
+    nA, nS = A.shape[0], S.shape[0]
+    yy = y.ravel()
+    l1, l2 = 0.5, 2.0
+
+    def f(v):
+        r = A @ v[:p] - yy
+        return l1 * v[p:p + nA].sum() + l2 * r @ r + v[p + nA:].sum()
+
+    def g(v):
+        out = np.zeros_like(v)
+        out[:p] = 2 * l2 * A.T @ (A @ v[:p] - yy)
+        out[p:p + nA] = l1
+        out[p + nA:] = 1.0
+        return out
+
+    Z = np.zeros
+    I = np.eye
+    Cm = np.vstack([np.hstack([A, -I(nA), Z((nA, nS))]), np.hstack([-A, -I(nA), Z((nA, nS))]),
+                    np.hstack([S, Z((nS, nA)), -I(nS)]), np.hstack([-S, Z((nS, nA)), -I(nS)])])
+    ub = np.concatenate([yy, -yy, Z(nS), Z(nS)])
+    v0 = np.concatenate([x0.ravel(), np.abs(A @ x0.ravel() - yy) + 1, np.abs(S @ x0.ravel()) + 1])
+    res = minimize(f, v0, jac=g, method="SLSQP", options={"maxiter": 2000, "ftol": 1e-14},
+                   constraints=[{"type": "ineq", "fun": lambda v: ub - Cm @ v, "jac": lambda v: -Cm}])
+    J_qp = o.cost(y, w, res.x[:p].reshape(o.hr))
+    x, _, _ = o.admm(y, x0, 1000)
+    J_admm = o.cost(y, w, x)
+    assert abs(J_admm - J_qp) <= 1e-7 * J_qp
+    assert np.abs(x.ravel() - res.x[:p]).max() < 1e-4
+
+
+def test_diagnostics_and_fixed_K(oracle_mod):
+    prob = synth.make_problem(synth.custom(U=3, V=3, H=10, W=9, scale=2, kb=5,
+                                           blur_sigma=1.0, window=5), seed=3)
+    o = oracle_mod.Oracle.from_problem(prob)
+    x, wA, wS, diag = o.admm(prob.y, prob.x0, 4, diagnostics=True)
+    assert math.isnan(diag[0, 1]) and np.isfinite(diag[1:, 1]).all()
+    assert (diag[:, 4] == 5).all()
+    assert np.abs(wA).max() <= 1.0 / o.params["mu"] + 1e-15
+    assert np.abs(wS).max() <= 1.0 / o.params["mu"] + 1e-15
+
+
+def test_quality_improves_over_iterations(oracle_mod):
+    """Synthetic analogue of the paper's PSNR-vs-iteration trend (Sec. 6.1)."""
+    wl = synth.custom(U=5, V=5, H=24, W=24, scale=2, kb=5, blur_sigma=1.0,
+                      disparities=(-1.0, 0.0, 0.8), noise_sigma=0.02, impulse=0.05,
+                      window=5, iterations=10)
+    prob = synth.make_problem(wl, seed=11)
+    o = oracle_mod.Oracle.from_problem(prob, h=0.3)
+    x1, wA, wS = o.admm(prob.y, prob.x0, 1)
+    x5, _, _ = o.admm(prob.y, x1, 4, wA=wA, wS=wS)
+    p0, p1, p5 = (synth.psnr(v, prob.gt) for v in (prob.x0, x1, x5))
+    assert p5 > p0 + 1.5
+    assert p5 > p1 + 1.0
