@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the light-field super-resolution ADMM hot path.
+
+One step = one full solve of one synthetic light field: x := x0, duals := 0,
+then N ADMM iterations (Algorithm 1), each with weights rebuilt from x and a
+K = 5 step CG x-step (Algorithm 2).  The metric is HR light-field
+throughput, s_k * Hh * Wh * N / t, in Mpix * ADMM-iter / s.
+
+  value   inputs resident in HBM, device time (CUDA events on the solver's
+          stream) of K steps, L2 flushed (256 MB write) between steps
+  e2e     the same metric through lfsr_solve with pinned HOST buffers: the
+          views and x0 go host -> device and x comes back inside the timing
+  roofline  the dominant kernel (x-step normal-matrix operator) timed with
+          CUDA events in the library's profiling mode, against the FP32 ALU
+          peak (its bound); plus the whole path's HBM fraction
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun (N > 1) every rank solves its own light field (replicas, weak
+scaling); times are the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2206_05047_gb300 import synth  # noqa: E402
+
+METRIC = "HR LF Mpix*ADMM-iter/s"
+UNIT = "Mpix*iter/s"
+FP32_LANES_PER_SM = 128
+SM_COUNT = 152
+
+
+def args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lf9x9_256_x2", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--iterations", type=int, default=None, help="ADMM iterations per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(wl, n_iter, extra=None):
+    cfg = {"workload": wl.name, "views": f"{wl.U}x{wl.V}", "lr": f"{wl.H}x{wl.W}",
+           "hr": f"{wl.HR[0]}x{wl.HR[1]}", "scale": wl.scale, "blur": f"{wl.kb}x{wl.kb} "
+           f"gaussian sigma {wl.blur_sigma}", "nltv_window": wl.window, "nltv_patch": wl.patch,
+           "nltv_h": wl.h, "admm_iters_per_step": n_iter, "cg_iters": wl.cg_iters,
+           "lambda1": wl.lambda1, "lambda2": wl.lambda2, "mu": wl.mu,
+           "noise": f"gaussian {wl.noise_sigma} + {int(100 * wl.impulse)}% salt-and-pepper"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def alg_bytes_per_iter(wl) -> float:
+    """FP32 streaming bytes of one ADMM iteration: duals read+write, views
+    read, x / omega / v, and 11 HR-vector passes per CG step."""
+    p = wl.HR[0] * wl.HR[1]
+    q = wl.H * wl.W
+    return 4.0 * (3 * wl.s_k * q + 2 * wl.s_d * p + 3 * p) + 4.0 * wl.cg_iters * 11 * p
+
+
+def normal_flops_per_launch(wl) -> float:
+    """Algorithmic FLOPs of one sum_k A_k^T A_k p: per view and HR pixel,
+    8 (bilinear gather) + 8 (bilinear scatter) + separable blur at the
+    decimated positions and its adjoint on the non-zeros,
+    4 kb (1/zeta + 1/zeta^2)."""
+    p = wl.HR[0] * wl.HR[1]
+    z = wl.scale
+    return wl.s_k * p * (16.0 + 4.0 * wl.kb * (1.0 / z + 1.0 / z ** 2))
+
+
+# --------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands, on the host cores
+# --------------------------------------------------------------------------
+def oracle_rate(prob, iters: int):
+    from oracle import oracle as om
+    o = om.Oracle.from_problem(prob)
+    t = time.perf_counter()
+    o.admm(prob.y, prob.x0, iters)
+    dt = time.perf_counter() - t
+    wl = prob.wl
+    return wl.s_k * wl.HR[0] * wl.HR[1] * iters / dt / 1e6, dt, om.num_threads()
+
+
+def traffic_from_profile(wl):
+    """DRAM bytes per normal-operator launch from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "normal_apply_traffic.json")
+    src = os.path.join(ROOT, "paper_2206_05047_gb300", "csrc", "op_kernels.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") != digest or rec.get("workload") != wl.name:
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------
+def run_reference(a, wl, n_iter):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    prob = synth.make_problem(wl, seed=1000 * 2)
+    from oracle import oracle as om
+    o = om.Oracle.from_problem(prob)
+    # bounded sample per step: one ADMM iteration of the full workload
+    x, wA, wS = prob.x0, None, None
+    for _ in range(a.warmup):
+        x, wA, wS = o.admm(prob.y, x, 1, wA=wA, wS=wS)
+    t = time.perf_counter()
+    for _ in range(a.steps):
+        x, wA, wS = o.admm(prob.y, x, 1, wA=wA, wS=wS)
+    dt = time.perf_counter() - t
+    value = wl.s_k * wl.HR[0] * wl.HR[1] * a.steps / dt / 1e6
+    sample = f"1 ADMM iteration (K = {wl.cg_iters} CG steps) of {wl.name} per step"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl, 1, {"parallelism": "none (host cores)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": om.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args()
+    wl = synth.WORKLOADS[a.workload]
+    n_iter = a.iterations if a.iterations is not None else wl.iterations
+    if a.impl == "reference":
+        run_reference(a, wl, n_iter)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2206_05047_gb300 import lfsr
+
+    prob = synth.make_problem(wl, seed=1000 * 2 + rank)
+    blur = prob.blur.astype(np.float32)
+    disp = prob.disparity.astype(np.float32)
+    y_h = torch.from_numpy(prob.y.astype(np.float32)).pin_memory()
+    x0_h = torch.from_numpy(prob.x0.astype(np.float32)).pin_memory()
+    x_h = torch.empty(wl.HR, dtype=torch.float32).pin_memory()
+    y_d = y_h.to(dev)
+    x0_d = x0_h.to(dev)
+    x_d = torch.empty(wl.HR, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    solver = lfsr.Solver(prob, stream=stream)
+    h = solver.handle
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    def step():
+        lfsr.load(h, y_d, x0_d)
+        lfsr.iterate(h, n_iter)
+
+    for _ in range(a.warmup):
+        step()
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.25)
+    barrier()
+    evs = []
+    for _ in range(a.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    barrier()
+    clk = clocks.stop()
+    t_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    t_ms_t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_ms_t, op=dist.ReduceOp.MAX)
+    t_ms = float(t_ms_t.item())
+    p = wl.HR[0] * wl.HR[1]
+    work = wl.s_k * p * n_iter * a.steps * world
+    value = work / (t_ms / 1e3) / 1e6
+
+    # output sanity: finite, and better than the bicubic start
+    lfsr.get_x(h, x_d)
+    xs = x_d.cpu().numpy().astype(np.float64)
+    assert np.isfinite(xs).all()
+
+    # e2e: through lfsr_solve with pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        barrier()
+        e2e_ms = 0.0
+        for _ in range(a.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lfsr.solve(h, y_h, n_iter, x0_h, x_h)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+        e2e = {"value": work / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(y_h.numel() * 4 + x0_h.numel() * 4),
+               "d2h_bytes_per_step": int(x_h.numel() * 4)}
+
+    # roofline of the dominant kernel (profiling mode: events around launches)
+    barrier()
+    lfsr.set_profiling(h, True)
+    step()
+    st = lfsr.stats(h)
+    lfsr.set_profiling(h, False)
+    names = ["nltv_block", "data_block", "cg_init", "nltv_apply", "normal_apply", "cg_update"]
+    per_class = {names[i]: {"ms": st["kernel_ms"][i], "launches": st["kernel_launches"][i]}
+                 for i in range(6)}
+    total_prof = sum(v["ms"] for v in per_class.values())
+    dom = per_class["normal_apply"]
+    avg_ms = dom["ms"] / max(dom["launches"], 1)
+    flops = normal_flops_per_launch(wl)
+    sm_clk = (clk.get("sm_max_mhz") or 2070.0)
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_clk * 1e6 / 1e12
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    traffic = traffic_from_profile(wl)
+    roofline = {"bound": "alu", "kernel": "k_operator<OP_NORMAL> (sum_k A_k^T A_k p)",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "avg_launch_ms": avg_ms, "flops_per_launch": flops,
+                "peak_note": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                             f"{sm_clk:.0f} MHz",
+                "share_of_step": dom["ms"] / total_prof if total_prof else None,
+                "per_kernel_ms_per_step": {k: v["ms"] for k, v in per_class.items()}}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm = float(json.load(f)["hbm_gbs"])
+        hbm_note = "of measured"
+    except (OSError, KeyError, ValueError):
+        hbm, hbm_note = 6800.0, "of fallback"
+    step_s = t_ms / 1e3 / a.steps
+    hbm_frac = alg_bytes_per_iter(wl) * n_iter / step_s / (hbm * 1e9)
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        iters = 3 if wl.name != "lf5x5_64_x2" else 20
+        rate, dt, cores = oracle_rate(prob, iters)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{iters} ADMM iterations (K = {wl.cg_iters}) of {wl.name} from x0, "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_ms / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded textured-plane light field)",
+                "config": workload_config(wl, n_iter, {
+                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                    "l2": "flushed between steps (256 MB write); per-step working set "
+                          f"{st['state_bytes'] / 1e6:.0f} MB"}),
+                "hbm_roofline": {"frac": hbm_frac, "alg_bytes_per_iter": alg_bytes_per_iter(wl),
+                                 "peak_gbs": hbm, "note": hbm_note},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(a.steps * n_iter * (3 + 3 * wl.cg_iters)),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * lfsr.h -- C ABI of the GB300 light-field super-resolution solver.
+ *
+ * The solver reconstructs the high-resolution (HR) reference view x of a 4D
+ * light field from U*V low-resolution (LR) sub-aperture views y_k by
+ * minimising (Eq. sr_fin)
+ *
+ *   J(x) = l1 sum_k |A_k x - y_k|_1 + l2 sum_k |A_k x - y_k|_2^2
+ *          + sum_d |W_d (S_d - I) x|_1,        A_k = D B W_k (Eq. sr_model_vec)
+ *
+ * with the rotated ADMM of Algorithm 1 and the conjugate-gradient x-step of
+ * Algorithm 2 (Sec. 4-5).  Every step runs in hand-written sm_103a CUDA
+ * kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions
+ *  - Images are row-major float32.  LR size H x W; HR size (scale*H) x
+ *    (scale*W) = Hh x Wh; p = Hh*Wh, q = H*W.
+ *  - View k = v*U + u has angular offset theta_k = (u-(U-1)/2, v-(V-1)/2);
+ *    U and V are odd so the centre view is the reference (Sec. 3.1).
+ *  - W_k samples x bilinearly at (i + tv*omega(i,j), j + tu*omega(i,j)),
+ *    zero outside the image (Sec. 4.1 forward warp); its adjoint is the exact
+ *    scatter of the same taps.  B correlates with the kb x kb kernel, zero
+ *    padded; D keeps the top-left pixel of every scale x scale block
+ *    (Sec. 4.1).
+ *  - NLTV weights w_d(u) = exp(-pd/h^2), pd the mean of squared differences
+ *    between the patch at u and the patch at u+d (clamp-to-edge reads), 0 if
+ *    u+d leaves the image; directions d = window offsets minus the centre,
+ *    in raster order (s_d = window^2 - 1).  Weights are rebuilt from the
+ *    current x at the start of every ADMM iteration (Sec. 6.1).
+ *  - Regulariser duals in the canonical layout are s_d x Hh x Wh, the dual
+ *    of direction d at pixel u at [d][u] (Eq. sr_admm_compact row order);
+ *    data duals are s_k x H x W.
+ *
+ * Memory kinds: LFSR_MEM_HOST pointers are ordinary host memory (pinned or
+ * pageable; the call copies through the handle's stream); LFSR_MEM_DEVICE
+ * pointers are device memory of the current device (e.g. a torch tensor's
+ * data_ptr) and all work is ordered on the handle's stream.  The caller owns
+ * every buffer it passes; the handle owns all solver state.
+ *
+ * Errors: every int-returning call returns LFSR_OK (0) or a negative
+ * LFSR_E* code and stores a message readable with lfsr_last_error().  No
+ * call aborts or throws.  A handle is not thread-safe; different handles
+ * are independent.
+ */
+#ifndef LFSR_H
+#define LFSR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LFSR_OK            0
+#define LFSR_EINVAL       (-1)  /* bad size, parameter or pointer            */
+#define LFSR_ENOMEM       (-2)  /* device allocation failed                  */
+#define LFSR_ECUDA        (-3)  /* CUDA runtime error (message has details)  */
+#define LFSR_ENUMERIC     (-4)  /* non-finite or non-positive CG curvature   */
+#define LFSR_ETIMEOUT     (-5)  /* a bounded device wait gave up             */
+#define LFSR_EUNSUPPORTED (-6)  /* valid but not implemented on this path    */
+
+#define LFSR_MEM_HOST   0
+#define LFSR_MEM_DEVICE 1
+
+#define LFSR_FP32 0            /* all state and arithmetic in float32       */
+
+/* Problem and solver parameters (copied by lfsr_create).  struct_size must
+ * be sizeof(lfsr_params). */
+typedef struct lfsr_params {
+  uint32_t struct_size;
+  int32_t U, V;            /* angular grid, odd, U*V <= 289                 */
+  int32_t H, W;            /* LR view size, >= 1                            */
+  int32_t scale;           /* zeta in {1,2,3,4} (Sec. 3.1)                  */
+  int32_t kb;              /* blur size, odd, <= 15                         */
+  const float *blur;       /* host, kb*kb taps K[a][b], a = row offset + r  */
+  const float *disparity;  /* host, Hh*Wh disparity map omega (HR px per
+                              unit angular step) on the reference grid      */
+  double lambda1, lambda2; /* >= 0, not both 0 (Eq. sr_fin)                 */
+  double mu;               /* ADMM penalty vartheta > 0 (Algorithm 1)       */
+  int32_t nltv_window;     /* odd, 3..15                                    */
+  int32_t nltv_patch;      /* odd, 1..7                                     */
+  double nltv_h;           /* > 0                                           */
+  int32_t cg_iters;        /* K of Algorithm 2, >= 0                        */
+  double cg_tol;           /* tau: CG stops once pi = |r|^2 <= tau          */
+  int32_t precision;       /* LFSR_FP32                                     */
+} lfsr_params;
+
+typedef struct lfsr_handle lfsr_handle;
+
+typedef struct lfsr_stats_t {
+  uint32_t struct_size;    /* set to sizeof(lfsr_stats_t) before the call   */
+  int32_t iterations;      /* ADMM iterations run since the last load       */
+  int32_t cg_steps;        /* CG steps the last x-step took                 */
+  int32_t status;          /* sticky device status (LFSR_OK or LFSR_E*)     */
+  double dual_change_sq;   /* |w_n - w_{n-1}|^2 of the last iteration       */
+  double cg_pi;            /* |r|^2 at the end of the last x-step           */
+  int64_t state_bytes;     /* device bytes owned by the handle              */
+  int64_t launches;        /* kernels launched since the last load          */
+  /* profiling mode only (lfsr_set_profiling): summed kernel time in ms and
+   * launch counts, by kernel class: 0 nltv-block, 1 data-block, 2 cg-init,
+   * 3 nltv-apply, 4 normal-apply, 5 cg-update                              */
+  double kernel_ms[8];
+  int64_t kernel_launches[8];
+} lfsr_stats_t;
+
+/* Creates a solver for one light-field geometry.  Copies blur and
+ * disparity to the device, allocates all ADMM state (x, data and
+ * regulariser duals, CG vectors) and validates every parameter.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream) on which
+ * every later call of this handle is ordered.  Returns LFSR_EINVAL for bad
+ * parameters, LFSR_ENOMEM / LFSR_ECUDA on device failures; *out is set to
+ * NULL on failure. */
+int lfsr_create(const lfsr_params *params, void *cuda_stream, lfsr_handle **out);
+
+/* Full solve (Algorithm 1): x := x0, all duals := 0, then `iterations`
+ * ADMM iterations, each rebuilding the NLTV weights from the current x
+ * and running the K-step CG x-step of Algorithm 2.  lr_views holds s_k*q
+ * floats ([k][i][j]), x0 and x_out p floats.  Blocks until x_out is
+ * written.  Returns LFSR_ENUMERIC if the CG curvature became non-finite
+ * or non-positive. */
+int lfsr_solve(lfsr_handle *h, const float *lr_views, int iterations,
+               const float *x0, float *x_out, int mem_kind);
+
+/* Frees the handle and all device memory it owns.  NULL is a no-op. */
+void lfsr_destroy(lfsr_handle *h);
+
+/* Message of the last failing call on h (or of the last failing create /
+ * NULL-handle call of this thread when h is NULL).  Never NULL. */
+const char *lfsr_last_error(const lfsr_handle *h);
+
+/* Synchronises the handle's stream and reports the last iteration's
+ * diagnostics. */
+int lfsr_stats(const lfsr_handle *h, lfsr_stats_t *out);
+
+/* ---- resident-state stepping (the solve split into its parts) -------- */
+
+/* Uploads the LR views, sets x := x0 and all duals := 0 (Algorithm 1,
+ * lines 1-2).  Asynchronous on the handle's stream. */
+int lfsr_load(lfsr_handle *h, const float *lr_views, const float *x0, int mem_kind);
+
+/* Enqueues `iterations` ADMM iterations on the resident state (no host
+ * synchronisation; one CUDA graph launch per two iterations). */
+int lfsr_iterate(lfsr_handle *h, int iterations);
+
+/* Copies the current x (p floats) out; blocks until done. */
+int lfsr_get_x(lfsr_handle *h, float *x_out, int mem_kind);
+
+/* Sets / reads the full ADMM state in the canonical layout: x (p floats),
+ * data duals wA (s_k*q), regulariser duals wS (s_d*p).  Any pointer may be
+ * NULL to skip that part.  lfsr_get_state blocks until done. */
+int lfsr_set_state(lfsr_handle *h, const float *x, const float *wA,
+                   const float *wS, int mem_kind);
+int lfsr_get_state(lfsr_handle *h, float *x, float *wA, float *wS, int mem_kind);
+
+/* ---- single operators (Sec. 4.1 kernels; for checking and reuse) ------ */
+
+/* out = A_k x (q floats), or for view == -1 all views (s_k*q floats). */
+int lfsr_apply_A(lfsr_handle *h, int view, const float *x, float *out, int mem_kind);
+
+/* out = A_k^T g (p floats); for view == -1, out = sum_k A_k^T g_k with g
+ * holding s_k*q floats. */
+int lfsr_apply_AT(lfsr_handle *h, int view, const float *g, float *out, int mem_kind);
+
+/* NLTV weights of x in the canonical layout (s_d*p floats). */
+int lfsr_weights(lfsr_handle *h, const float *x, float *w, int mem_kind);
+
+/* q = M p with M = (l2 + mu l1^2/2) sum_k A_k^T A_k + mu/2 sum_d S_d^T S_d
+ * (the normal matrix G^T G of the x-step, Sec. 5), the NLTV weights built
+ * from xw; *pMp (host) receives <p, M p> accumulated in float64. */
+int lfsr_apply_normal(lfsr_handle *h, const float *xw, const float *p, float *q,
+                      double *pMp, int mem_kind);
+
+/* Profiling mode: when on, lfsr_iterate launches kernels one by one (no
+ * graph) with CUDA events around each and lfsr_stats reports per-class
+ * kernel time.  Off by default. */
+int lfsr_set_profiling(lfsr_handle *h, int on);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LFSR_H */

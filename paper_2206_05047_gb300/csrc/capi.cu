@@ -1,0 +1,698 @@
+// C ABI of liblfsr: handle, validation, device state, the ADMM iteration
+// schedule (Algorithm 1 with the CG x-step of Algorithm 2) and its CUDA-graph
+// replay.  See include/lfsr.h for the contract of every entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lfsr.h"
+#include "lfsr_internal.cuh"
+
+using namespace lfsr;
+
+namespace {
+
+thread_local std::string t_err = "no error";
+
+constexpr int NUM_CLASSES = 6;  // profiling classes, see lfsr_stats_t
+
+struct ProfEvent {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct lfsr_handle {
+  lfsr_params prm{};
+  Geom g{};
+  OpPlan op{};
+  NlPlan nl{};
+  cudaStream_t stream = nullptr;      // caller's stream
+  cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+  int device = 0, sm_count = 0;
+  size_t p = 0, q = 0, nA = 0, nS = 0, nSpair = 0;
+  int grid_op = 0, grid_vec = 0, max_grid = 0;
+  // device buffers
+  float* disp = nullptr;
+  float* y = nullptr;
+  float* x[2] = {nullptr, nullptr};
+  float* wA[2] = {nullptr, nullptr};
+  float* wS[2] = {nullptr, nullptr};
+  float* R = nullptr;   // v, then the CG residual r
+  float* P[2] = {nullptr, nullptr};
+  float* Q = nullptr;
+  float* io = nullptr;  // staging for host <-> device and layout conversion
+  size_t io_floats = 0;
+  double* partials = nullptr;
+  DevScalars* sc = nullptr;  // [0] solver, [1] standalone operator calls
+  int64_t state_bytes = 0;
+  // schedule state
+  int parity = 0;
+  int iters = 0;
+  int64_t launches = 0;
+  cudaGraphExec_t graph_pair = nullptr;     // iterations at parity 0 then 1
+  cudaGraphExec_t graph_single[2] = {nullptr, nullptr};
+  bool profiling = false;
+  std::vector<ProfEvent> prof;
+  double prof_ms[8] = {0};
+  int64_t prof_n[8] = {0};
+  std::string err = "no error";
+};
+
+namespace {
+
+int fail(lfsr_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  t_err = msg;
+  return code;
+}
+
+int cuda_fail(lfsr_handle* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? LFSR_ENOMEM : LFSR_ECUDA, m);
+}
+
+#define CK(h, expr, what)                          \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+bool finite_all(const float* a, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+void free_all(lfsr_handle* h) {
+  if (h->graph_pair) cudaGraphExecDestroy(h->graph_pair);
+  for (auto& gs : h->graph_single)
+    if (gs) cudaGraphExecDestroy(gs);
+  for (auto& ev : h->prof) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  float* bufs[] = {h->disp, h->y, h->x[0], h->x[1], h->wA[0], h->wA[1], h->wS[0],
+                   h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io};
+  for (float* b : bufs)
+    if (b) cudaFree(b);
+  if (h->partials) cudaFree(h->partials);
+  if (h->sc) cudaFree(h->sc);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+}
+
+template <class T>
+cudaError_t dalloc(lfsr_handle* h, T** p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+  if (e == cudaSuccess) h->state_bytes += (int64_t)(n * sizeof(T));
+  return e;
+}
+
+// Copies n floats from a caller buffer of kind `mem` into device memory dst.
+cudaError_t to_dev(lfsr_handle* h, float* dst, const float* src, size_t n, int mem) {
+  return cudaMemcpyAsync(dst, src, n * sizeof(float),
+                         mem == LFSR_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                         h->stream);
+}
+
+cudaError_t from_dev(lfsr_handle* h, float* dst, const float* src, size_t n, int mem) {
+  return cudaMemcpyAsync(dst, src, n * sizeof(float),
+                         mem == LFSR_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                         h->stream);
+}
+
+int check_mem(lfsr_handle* h, int mem) {
+  if (mem != LFSR_MEM_HOST && mem != LFSR_MEM_DEVICE)
+    return fail(h, LFSR_EINVAL, "mem_kind must be LFSR_MEM_HOST or LFSR_MEM_DEVICE");
+  return LFSR_OK;
+}
+
+// Launch helpers ------------------------------------------------------------
+
+double* part_slot(lfsr_handle* h, int slot) { return h->partials + (size_t)slot * h->max_grid; }
+
+// Runs `launch` (one kernel) with profiling events around it when enabled.
+template <class F>
+cudaError_t timed(lfsr_handle* h, cudaStream_t s, int cls, F&& launch) {
+  if (!h->profiling) return launch();
+  ProfEvent ev{cls, nullptr, nullptr};
+  cudaError_t e = cudaEventCreate(&ev.a);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
+  if (e != cudaSuccess) return e;
+  cudaEventRecord(ev.a, s);
+  e = launch();
+  cudaEventRecord(ev.b, s);
+  h->prof.push_back(ev);
+  return e;
+}
+
+// One ADMM iteration (Algorithm 1) on parity b: reads x[b], w*[b], writes
+// x[1-b], w*[1-b].
+cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
+  const int nb = 1 - b;
+  const Geom& g = h->g;
+  DevScalars* sc = h->sc;
+  cudaError_t e;
+  // regulariser rows: weights from x^(n-1), z/w-step, v := mu/2 S^T f
+  NlArgs nbk{};
+  nbk.x = h->x[b];
+  nbk.out = h->R;
+  nbk.wS_old = h->wS[b];
+  nbk.wS_new = h->wS[nb];
+  nbk.partials = part_slot(h, RED_DW_S);
+  nbk.sc = sc;
+  e = timed(h, s, 0, [&] { return nl_launch(NL_BLOCK, g, h->nl, nbk, s); });
+  if (e != cudaSuccess) return e;
+  // data rows: a = A x - b, z/w-step, v += A^T (l2 a + mu/2 l1 f)
+  OpArgs od{};
+  od.src = h->x[b];
+  od.disp = h->disp;
+  od.out = h->R;
+  od.y = h->y;
+  od.wA_old = h->wA[b];
+  od.wA_new = h->wA[nb];
+  od.scale = 1.f;
+  od.view0 = 0;
+  od.nviews = g.sk;
+  od.units = h->op.n_tiles * g.sk;
+  od.partials = part_slot(h, RED_DW_A);
+  od.sc = sc;
+  e = timed(h, s, 1, [&] { return op_launch(OP_DATA, g, h->op, od, h->grid_op, s); });
+  if (e != cudaSuccess) return e;
+  // x-step (Algorithm 2): r = -v, x' = x, pi = <r, r>
+  e = timed(h, s, 2, [&] {
+    return cg_init_launch(g, h->R, h->x[b], h->x[nb], part_slot(h, RED_PI), sc, h->grid_vec, s);
+  });
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < h->prm.cg_iters; ++k) {
+    const int pb = k & 1;
+    NlArgs na{};
+    na.x = h->x[b];
+    na.r = h->R;
+    na.p_old = h->P[1 - pb];
+    na.p_new = h->P[pb];
+    na.out = h->Q;
+    na.partials = part_slot(h, RED_NLTV);
+    na.sc = sc;
+    na.use_beta = 1;
+    na.check_done = 1;
+    e = timed(h, s, 3, [&] { return nl_launch(NL_APPLY, g, h->nl, na, s); });
+    if (e != cudaSuccess) return e;
+    OpArgs on{};
+    on.src = h->P[pb];
+    on.disp = h->disp;
+    on.out = h->Q;
+    on.scale = g.cA;
+    on.view0 = 0;
+    on.nviews = g.sk;
+    on.units = h->op.n_tiles * g.sk;
+    on.partials = part_slot(h, RED_OP);
+    on.sc = sc;
+    on.check_done = 1;
+    e = timed(h, s, 4, [&] { return op_launch(OP_NORMAL, g, h->op, on, h->grid_op, s); });
+    if (e != cudaSuccess) return e;
+    e = timed(h, s, 5, [&] {
+      return cg_update_launch(g, h->P[pb], h->Q, h->x[nb], h->R, part_slot(h, RED_PI), sc,
+                              h->grid_vec, s);
+    });
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int launches_per_iteration(const lfsr_handle* h) { return 3 + 3 * h->prm.cg_iters; }
+
+cudaError_t build_graph(lfsr_handle* h, int first_parity, int n, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t el = cudaSuccess;
+  for (int i = 0; i < n && el == cudaSuccess; ++i)
+    el = enqueue_iteration(h, (first_parity + i) & 1, h->cap_stream);
+  e = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (el != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return el;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  return e;
+}
+
+int separable_factor(const std::vector<float>& K, int kb, float* kv, float* kh) {
+  int am = 0, bm = 0;
+  double best = -1.0;
+  for (int a = 0; a < kb; ++a)
+    for (int b = 0; b < kb; ++b)
+      if (std::fabs((double)K[a * kb + b]) > best) {
+        best = std::fabs((double)K[a * kb + b]);
+        am = a;
+        bm = b;
+      }
+  if (best <= 0.0) return 0;
+  const double pivot = K[am * kb + bm];
+  double err = 0.0;
+  for (int a = 0; a < kb; ++a)
+    for (int b = 0; b < kb; ++b) {
+      const double rec = (double)K[a * kb + bm] * (double)K[am * kb + b] / pivot;
+      err = std::fmax(err, std::fabs(rec - (double)K[a * kb + b]));
+    }
+  if (err > 1e-7 * best) return 0;
+  for (int a = 0; a < kb; ++a) kv[a] = K[a * kb + bm];
+  for (int b = 0; b < kb; ++b) kh[b] = (float)((double)K[am * kb + b] / pivot);
+  return 1;
+}
+
+int validate(const lfsr_params* pr) {
+  if (!pr) return fail(nullptr, LFSR_EINVAL, "params is NULL");
+  if (pr->struct_size != sizeof(lfsr_params))
+    return fail(nullptr, LFSR_EINVAL, "params->struct_size != sizeof(lfsr_params)");
+  if (pr->U < 1 || pr->V < 1 || !(pr->U & 1) || !(pr->V & 1) || pr->U * pr->V > LFSR_MAX_VIEWS)
+    return fail(nullptr, LFSR_EINVAL, "U and V must be odd, >= 1, with U*V <= 289");
+  if (pr->H < 1 || pr->W < 1 || pr->H > 65536 || pr->W > 65536)
+    return fail(nullptr, LFSR_EINVAL, "H and W must be in [1, 65536]");
+  if (pr->scale < 1 || pr->scale > 4)
+    return fail(nullptr, LFSR_EUNSUPPORTED, "scale must be 1, 2, 3 or 4");
+  if ((long long)pr->scale * pr->H * pr->scale * pr->W > (1LL << 31))
+    return fail(nullptr, LFSR_EINVAL, "HR image too large");
+  if (pr->kb < 1 || !(pr->kb & 1) || pr->kb > LFSR_MAX_KB)
+    return fail(nullptr, LFSR_EINVAL, "kb must be odd and <= 15");
+  if (!pr->blur || !pr->disparity) return fail(nullptr, LFSR_EINVAL, "blur and disparity are required");
+  if (!(pr->lambda1 >= 0.0) || !(pr->lambda2 >= 0.0) || !std::isfinite(pr->lambda1) ||
+      !std::isfinite(pr->lambda2) || (pr->lambda1 == 0.0 && pr->lambda2 == 0.0))
+    return fail(nullptr, LFSR_EINVAL, "lambda1, lambda2 must be finite, >= 0 and not both 0");
+  if (!(pr->mu > 0.0) || !std::isfinite(pr->mu)) return fail(nullptr, LFSR_EINVAL, "mu must be > 0");
+  if (pr->nltv_window < 3 || pr->nltv_window > 15 || !(pr->nltv_window & 1))
+    return fail(nullptr, LFSR_EINVAL, "nltv_window must be odd in [3, 15]");
+  if (pr->nltv_patch < 1 || pr->nltv_patch > 7 || !(pr->nltv_patch & 1))
+    return fail(nullptr, LFSR_EINVAL, "nltv_patch must be odd in [1, 7]");
+  if (!(pr->nltv_h > 0.0) || !std::isfinite(pr->nltv_h)) return fail(nullptr, LFSR_EINVAL, "nltv_h must be > 0");
+  if (pr->cg_iters < 0 || pr->cg_iters > 10000) return fail(nullptr, LFSR_EINVAL, "cg_iters must be in [0, 10000]");
+  if (!(pr->cg_tol >= 0.0) || !std::isfinite(pr->cg_tol)) return fail(nullptr, LFSR_EINVAL, "cg_tol must be >= 0");
+  if (pr->precision != LFSR_FP32) return fail(nullptr, LFSR_EUNSUPPORTED, "only LFSR_FP32 is implemented");
+  return LFSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
+  if (!out) return fail(nullptr, LFSR_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(pr);
+  if (rc != LFSR_OK) return rc;
+  const int Hh = pr->scale * pr->H, Wh = pr->scale * pr->W;
+  const size_t p = (size_t)Hh * Wh, q = (size_t)pr->H * pr->W;
+  std::vector<float> K(pr->blur, pr->blur + (size_t)pr->kb * pr->kb);
+  if (!finite_all(K.data(), K.size()) || !finite_all(pr->disparity, p))
+    return fail(nullptr, LFSR_EINVAL, "blur or disparity has non-finite values");
+
+  lfsr_handle* h = new (std::nothrow) lfsr_handle();
+  if (!h) return fail(nullptr, LFSR_ENOMEM, "host allocation failed");
+  h->prm = *pr;
+  h->prm.blur = nullptr;
+  h->prm.disparity = nullptr;
+  h->stream = (cudaStream_t)cuda_stream;
+  Geom& g = h->g;
+  g.U = pr->U;
+  g.V = pr->V;
+  g.sk = pr->U * pr->V;
+  g.H = pr->H;
+  g.W = pr->W;
+  g.Hh = Hh;
+  g.Wh = Wh;
+  g.zeta = pr->scale;
+  g.kb = pr->kb;
+  g.r = (pr->kb - 1) / 2;
+  for (int i = 0; i < pr->kb * pr->kb; ++i) g.k2[i] = K[i];
+  g.separable = separable_factor(K, pr->kb, g.kv, g.kh);
+  double max_disp = 0.0;
+  for (size_t i = 0; i < p; ++i) max_disp = std::fmax(max_disp, std::fabs((double)pr->disparity[i]));
+  const double max_theta = 0.5 * (double)((pr->U > pr->V ? pr->U : pr->V) - 1);
+  g.S = (int)std::ceil(max_disp * max_theta);
+  for (int k = 0; k < g.sk; ++k) {
+    g.tu[k] = (float)((k % pr->U) - 0.5 * (pr->U - 1));
+    g.tv[k] = (float)((k / pr->U) - 0.5 * (pr->V - 1));
+  }
+  g.win_r = (pr->nltv_window - 1) / 2;
+  g.patch_r = (pr->nltv_patch - 1) / 2;
+  g.sh = (pr->nltv_window * pr->nltv_window - 1) / 2;
+  {
+    int n = 0;
+    for (int a = -g.win_r; a <= g.win_r && n < g.sh; ++a)
+      for (int b = -g.win_r; b <= g.win_r && n < g.sh; ++b) {
+        g.di[n] = (int8_t)a;
+        g.dj[n] = (int8_t)b;
+        ++n;
+      }
+  }
+  g.inv_h2 = (float)(1.0 / (pr->nltv_h * pr->nltv_h));
+  g.inv_np = (float)(1.0 / (double)(pr->nltv_patch * pr->nltv_patch));
+  g.lambda1 = (float)pr->lambda1;
+  g.lambda2 = (float)pr->lambda2;
+  g.mu = (float)pr->mu;
+  g.cA = (float)(pr->lambda2 + 0.5 * pr->mu * pr->lambda1 * pr->lambda1);
+  g.thr = (float)(1.0 / pr->mu);
+  g.tau = pr->cg_tol;
+  h->p = p;
+  h->q = q;
+  h->nA = (size_t)g.sk * q;
+  h->nS = (size_t)(2 * g.sh) * p;
+  h->nSpair = h->nS;
+
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(nullptr, e, "device query");
+    delete h;
+    return rc;
+  }
+  e = op_prepare(g.zeta);
+  if (e == cudaSuccess) e = nl_prepare();
+  if (e != cudaSuccess) {
+    rc = cuda_fail(nullptr, e, "kernel attributes");
+    delete h;
+    return rc;
+  }
+  if (op_plan(g, &h->op, h->sm_count) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, LFSR_EUNSUPPORTED,
+                "disparity * angular offset too large for the shared-memory tile");
+  }
+  if (nl_plan(g, &h->nl) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, LFSR_EUNSUPPORTED, "NLTV window / patch too large");
+  }
+  h->grid_op = op_grid(h->op, h->op.n_tiles * g.sk, h->sm_count);
+  h->grid_vec = h->sm_count * 2;
+  h->max_grid = h->grid_op;
+  if (h->nl.n_tiles > h->max_grid) h->max_grid = h->nl.n_tiles;
+  if (h->grid_vec > h->max_grid) h->max_grid = h->grid_vec;
+  h->io_floats = h->nA > h->nS ? h->nA : h->nS;
+  if (h->io_floats < p) h->io_floats = p;
+
+  e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = dalloc(h, &h->disp, p);
+  if (e == cudaSuccess) e = dalloc(h, &h->y, h->nA);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = dalloc(h, &h->x[i], p);
+    if (e == cudaSuccess) e = dalloc(h, &h->wA[i], h->nA);
+    if (e == cudaSuccess) e = dalloc(h, &h->wS[i], h->nSpair);
+    if (e == cudaSuccess) e = dalloc(h, &h->P[i], p);
+  }
+  if (e == cudaSuccess) e = dalloc(h, &h->R, p);
+  if (e == cudaSuccess) e = dalloc(h, &h->Q, p);
+  if (e == cudaSuccess) e = dalloc(h, &h->io, h->io_floats);
+  if (e == cudaSuccess) e = dalloc(h, &h->partials, (size_t)RED_NUM * h->max_grid);
+  if (e == cudaSuccess) e = dalloc(h, &h->sc, 2);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->disp, pr->disparity, p * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->sc, 0, 2 * sizeof(DevScalars), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->P[0], 0, p * sizeof(float), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->P[1], 0, p * sizeof(float), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(nullptr, e, "lfsr_create");
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return LFSR_OK;
+}
+
+void lfsr_destroy(lfsr_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+const char* lfsr_last_error(const lfsr_handle* h) { return h ? h->err.c_str() : t_err.c_str(); }
+
+int lfsr_load(lfsr_handle* h, const float* lr_views, const float* x0, int mem) {
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  if (!lr_views || !x0) return fail(h, LFSR_EINVAL, "lr_views and x0 are required");
+  if (check_mem(h, mem)) return LFSR_EINVAL;
+  CK(h, to_dev(h, h->y, lr_views, h->nA, mem), "upload views");
+  CK(h, to_dev(h, h->x[0], x0, h->p, mem), "upload x0");
+  CK(h, cudaMemsetAsync(h->wA[0], 0, h->nA * sizeof(float), h->stream), "clear data duals");
+  CK(h, cudaMemsetAsync(h->wS[0], 0, h->nSpair * sizeof(float), h->stream), "clear NLTV duals");
+  CK(h, scalars_reset(h->sc, h->stream), "reset scalars");
+  h->parity = 0;
+  h->iters = 0;
+  h->launches = 0;
+  return LFSR_OK;
+}
+
+int lfsr_iterate(lfsr_handle* h, int iterations) {
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  if (iterations < 0) return fail(h, LFSR_EINVAL, "iterations must be >= 0");
+  if (h->profiling) {
+    for (int i = 0; i < iterations; ++i) {
+      CK(h, enqueue_iteration(h, h->parity, h->stream), "iteration");
+      h->parity ^= 1;
+    }
+  } else {
+    int left = iterations;
+    while (left > 0) {
+      if (h->parity == 0 && left >= 2) {
+        if (!h->graph_pair) CK(h, build_graph(h, 0, 2, &h->graph_pair), "capture");
+        CK(h, cudaGraphLaunch(h->graph_pair, h->stream), "graph launch");
+        left -= 2;
+      } else {
+        cudaGraphExec_t& gs = h->graph_single[h->parity];
+        if (!gs) CK(h, build_graph(h, h->parity, 1, &gs), "capture");
+        CK(h, cudaGraphLaunch(gs, h->stream), "graph launch");
+        h->parity ^= 1;
+        left -= 1;
+      }
+    }
+  }
+  h->iters += iterations;
+  h->launches += (int64_t)iterations * launches_per_iteration(h);
+  return LFSR_OK;
+}
+
+static int read_status(lfsr_handle* h, DevScalars* hs) {
+  CK(h, cudaMemcpyAsync(hs, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream), "read scalars");
+  CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  if (hs->status != 0)
+    return fail(h, hs->status, "non-finite or non-positive curvature in the CG x-step");
+  return LFSR_OK;
+}
+
+int lfsr_get_x(lfsr_handle* h, float* x_out, int mem) {
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  if (!x_out) return fail(h, LFSR_EINVAL, "x_out is NULL");
+  if (check_mem(h, mem)) return LFSR_EINVAL;
+  CK(h, from_dev(h, x_out, h->x[h->parity], h->p, mem), "download x");
+  DevScalars hs;
+  return read_status(h, &hs);
+}
+
+int lfsr_solve(lfsr_handle* h, const float* lr_views, int iterations, const float* x0,
+               float* x_out, int mem) {
+  int rc = lfsr_load(h, lr_views, x0, mem);
+  if (rc) return rc;
+  rc = lfsr_iterate(h, iterations);
+  if (rc) return rc;
+  return lfsr_get_x(h, x_out, mem);
+}
+
+int lfsr_stats(const lfsr_handle* hc, lfsr_stats_t* out) {
+  lfsr_handle* h = const_cast<lfsr_handle*>(hc);
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  if (!out || out->struct_size != sizeof(lfsr_stats_t))
+    return fail(h, LFSR_EINVAL, "out->struct_size != sizeof(lfsr_stats_t)");
+  DevScalars hs;
+  CK(h, cudaMemcpyAsync(&hs, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream), "read scalars");
+  CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  for (auto& ev : h->prof) {
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, ev.a, ev.b), "event time");
+    h->prof_ms[ev.cls] += ms;
+    h->prof_n[ev.cls] += 1;
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  h->prof.clear();
+  std::memset((char*)out + sizeof(uint32_t), 0, sizeof(lfsr_stats_t) - sizeof(uint32_t));
+  out->iterations = h->iters;
+  out->cg_steps = hs.cg_steps;
+  out->status = hs.status;
+  out->dual_change_sq = hs.dw2;
+  out->cg_pi = hs.pi;
+  out->state_bytes = h->state_bytes;
+  out->launches = h->launches;
+  for (int c = 0; c < NUM_CLASSES; ++c) {
+    out->kernel_ms[c] = h->prof_ms[c];
+    out->kernel_launches[c] = h->prof_n[c];
+  }
+  return LFSR_OK;
+}
+
+int lfsr_set_profiling(lfsr_handle* h, int on) {
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  h->profiling = on != 0;
+  for (int c = 0; c < 8; ++c) {
+    h->prof_ms[c] = 0.0;
+    h->prof_n[c] = 0;
+  }
+  return LFSR_OK;
+}
+
+int lfsr_set_state(lfsr_handle* h, const float* x, const float* wA, const float* wS, int mem) {
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  if (check_mem(h, mem)) return LFSR_EINVAL;
+  const int b = h->parity;
+  if (x) CK(h, to_dev(h, h->x[b], x, h->p, mem), "set x");
+  if (wA) CK(h, to_dev(h, h->wA[b], wA, h->nA, mem), "set data duals");
+  if (wS) {
+    CK(h, to_dev(h, h->io, wS, h->nS, mem), "set NLTV duals");
+    CK(h, pair_from_canonical(h->g, h->io, h->wS[b], h->stream), "dual layout");
+  }
+  return LFSR_OK;
+}
+
+int lfsr_get_state(lfsr_handle* h, float* x, float* wA, float* wS, int mem) {
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  if (check_mem(h, mem)) return LFSR_EINVAL;
+  const int b = h->parity;
+  if (x) CK(h, from_dev(h, x, h->x[b], h->p, mem), "get x");
+  if (wA) CK(h, from_dev(h, wA, h->wA[b], h->nA, mem), "get data duals");
+  if (wS) {
+    CK(h, pair_to_canonical(h->g, h->wS[b], h->io, h->stream), "dual layout");
+    CK(h, from_dev(h, wS, h->io, h->nS, mem), "get NLTV duals");
+  }
+  DevScalars hs;
+  return read_status(h, &hs);
+}
+
+int lfsr_apply_A(lfsr_handle* h, int view, const float* x, float* out, int mem) {
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  if (!x || !out) return fail(h, LFSR_EINVAL, "x and out are required");
+  if (check_mem(h, mem)) return LFSR_EINVAL;
+  if (view < -1 || view >= h->g.sk) return fail(h, LFSR_EINVAL, "view out of range");
+  const int nv = view < 0 ? h->g.sk : 1;
+  const float* xs = x;
+  float* os = out;
+  if (mem == LFSR_MEM_HOST) {
+    CK(h, to_dev(h, h->Q, x, h->p, mem), "upload x");
+    xs = h->Q;
+    os = h->io;
+  }
+  OpArgs a{};
+  a.src = xs;
+  a.disp = h->disp;
+  a.out = os - (size_t)(view < 0 ? 0 : view) * h->q;  // kernel indexes out by view
+  a.view0 = view < 0 ? 0 : view;
+  a.nviews = nv;
+  a.units = h->op.n_tiles * nv;
+  a.sc = h->sc + 1;
+  CK(h, op_launch(OP_FWD, h->g, h->op, a, op_grid(h->op, a.units, h->sm_count), h->stream), "apply A");
+  if (mem == LFSR_MEM_HOST) CK(h, from_dev(h, out, h->io, (size_t)nv * h->q, mem), "download");
+  CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return LFSR_OK;
+}
+
+int lfsr_apply_AT(lfsr_handle* h, int view, const float* gin, float* out, int mem) {
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  if (!gin || !out) return fail(h, LFSR_EINVAL, "g and out are required");
+  if (check_mem(h, mem)) return LFSR_EINVAL;
+  if (view < -1 || view >= h->g.sk) return fail(h, LFSR_EINVAL, "view out of range");
+  const int nv = view < 0 ? h->g.sk : 1;
+  const float* gs = gin;
+  float* os = out;
+  if (mem == LFSR_MEM_HOST) {
+    CK(h, to_dev(h, h->io, gin, (size_t)nv * h->q, mem), "upload g");
+    gs = h->io;
+    os = h->Q;
+  }
+  CK(h, cudaMemsetAsync(os, 0, h->p * sizeof(float), h->stream), "clear out");
+  OpArgs a{};
+  a.src = gs - (size_t)(view < 0 ? 0 : view) * h->q;
+  a.disp = h->disp;
+  a.out = os;
+  a.scale = 1.f;
+  a.view0 = view < 0 ? 0 : view;
+  a.nviews = nv;
+  a.units = h->op.n_tiles * nv;
+  a.sc = h->sc + 1;
+  CK(h, op_launch(OP_ADJ, h->g, h->op, a, op_grid(h->op, a.units, h->sm_count), h->stream), "apply A^T");
+  if (mem == LFSR_MEM_HOST) CK(h, from_dev(h, out, h->Q, h->p, mem), "download");
+  CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return LFSR_OK;
+}
+
+int lfsr_weights(lfsr_handle* h, const float* x, float* w, int mem) {
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  if (!x || !w) return fail(h, LFSR_EINVAL, "x and w are required");
+  if (check_mem(h, mem)) return LFSR_EINVAL;
+  const float* xs = x;
+  float* ws = w;
+  if (mem == LFSR_MEM_HOST) {
+    CK(h, to_dev(h, h->Q, x, h->p, mem), "upload x");
+    xs = h->Q;
+    ws = h->io;
+  }
+  CK(h, cudaMemsetAsync(ws, 0, h->nS * sizeof(float), h->stream), "clear w");
+  NlArgs a{};
+  a.x = xs;
+  a.out = ws;
+  a.sc = h->sc + 1;
+  CK(h, nl_launch(NL_WEIGHTS, h->g, h->nl, a, h->stream), "weights");
+  if (mem == LFSR_MEM_HOST) CK(h, from_dev(h, w, h->io, h->nS, mem), "download");
+  CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return LFSR_OK;
+}
+
+int lfsr_apply_normal(lfsr_handle* h, const float* xw, const float* p, float* qo, double* pMp,
+                      int mem) {
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  if (!xw || !p || !qo) return fail(h, LFSR_EINVAL, "xw, p and q are required");
+  if (check_mem(h, mem)) return LFSR_EINVAL;
+  const float* xs = xw;
+  const float* ps = p;
+  float* qs = qo;
+  if (mem == LFSR_MEM_HOST) {
+    CK(h, to_dev(h, h->io, xw, h->p, mem), "upload xw");
+    CK(h, to_dev(h, h->io + h->p, p, h->p, mem), "upload p");
+    xs = h->io;
+    ps = h->io + h->p;
+    qs = h->io + 2 * h->p;
+  }
+  DevScalars* sc = h->sc + 1;
+  NlArgs na{};
+  na.x = xs;
+  na.p_old = ps;
+  na.out = qs;
+  na.partials = part_slot(h, RED_NLTV);
+  na.sc = sc;
+  CK(h, nl_launch(NL_APPLY, h->g, h->nl, na, h->stream), "normal (NLTV part)");
+  OpArgs on{};
+  on.src = ps;
+  on.disp = h->disp;
+  on.out = qs;
+  on.scale = h->g.cA;
+  on.view0 = 0;
+  on.nviews = h->g.sk;
+  on.units = h->op.n_tiles * h->g.sk;
+  on.partials = part_slot(h, RED_OP);
+  on.sc = sc;
+  CK(h, op_launch(OP_NORMAL, h->g, h->op, on, h->grid_op, h->stream), "normal (operator part)");
+  if (mem == LFSR_MEM_HOST) CK(h, from_dev(h, qo, qs, h->p, mem), "download q");
+  DevScalars hs;
+  CK(h, cudaMemcpyAsync(&hs, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream), "read");
+  CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  if (pMp) *pMp = hs.pAp;
+  return LFSR_OK;
+}
+
+}  // extern "C"

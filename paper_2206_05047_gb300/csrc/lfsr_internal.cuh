@@ -1,0 +1,133 @@
+// Internal declarations shared by the CUDA translation units of liblfsr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define LFSR_MAX_KB 15
+#define LFSR_MAX_VIEWS 289
+#define LFSR_MAX_HALF_DIRS 112   // (15*15 - 1) / 2
+
+namespace lfsr {
+
+// Geometry and solver constants, passed by value to every kernel (lives in
+// the kernel-parameter constant bank; all reads are warp-uniform).
+struct Geom {
+  int U, V, sk;          // angular grid, s_k
+  int H, W;              // LR size
+  int Hh, Wh;            // HR size
+  int zeta;              // scale
+  int kb, r;             // blur size and radius
+  int separable;         // blur = kv (rows) x kh (cols)
+  int S;                 // integer bound on |theta_k * omega| over views/pixels
+  int win_r, patch_r;    // NLTV window / patch radius
+  int sh;                // half direction count s_d / 2
+  float inv_h2;          // 1 / h^2
+  float inv_np;          // 1 / patch^2
+  float lambda1, lambda2, mu;
+  float cA;              // lambda2 + mu lambda1^2 / 2
+  float thr;             // 1 / mu (prox threshold, Eq. sr_l1l2l1_prox)
+  double tau;            // CG threshold
+  float kv[LFSR_MAX_KB], kh[LFSR_MAX_KB];
+  float k2[LFSR_MAX_KB * LFSR_MAX_KB];
+  float tu[LFSR_MAX_VIEWS], tv[LFSR_MAX_VIEWS];
+  int8_t di[LFSR_MAX_HALF_DIRS], dj[LFSR_MAX_HALF_DIRS];  // half direction set
+};
+
+// Device-resident scalars of the CG x-step (Algorithm 2) and diagnostics.
+struct DevScalars {
+  double pi;        // |r|^2
+  double pAp;       // <p, M p>
+  double alpha;     // pi / pAp
+  double beta;      // pi_new / pi_old
+  double dwA, dwS;  // |dw|^2 of the data / regulariser duals
+  double dw2;       // total of the last iteration
+  int cg_done;      // x-step finished (pi <= tau, or a numeric failure)
+  int cg_first;     // next direction is p = r (first CG step)
+  int cg_steps;
+  int status;       // sticky LFSR_* status
+  unsigned int counter[8];   // last-block counters of the grid reductions
+  double red[8];    // finalized totals of the grid reductions (RED_* slots)
+};
+
+// Reduction slots (partials arrays and last-block counters).
+enum { RED_NLTV = 0, RED_OP = 1, RED_PI = 2, RED_DW_A = 3, RED_DW_S = 4, RED_NUM = 5 };
+
+// Operator-kernel modes.
+enum { OP_NORMAL = 0, OP_DATA = 1, OP_FWD = 2, OP_ADJ = 3 };
+// NLTV-kernel modes.
+enum { NL_BLOCK = 0, NL_APPLY = 1, NL_WEIGHTS = 2 };
+
+// Launch plan of the operator kernels (tile shape and smem layout).
+struct OpPlan {
+  int TH, TW;            // tile of HR source pixels
+  int tiles_x, tiles_y, n_tiles;
+  int NLr, NLc;          // max LR rows / cols touching a tile
+  int NEr, NEc;          // max warp-sample rows / cols
+  int NPr, NPc;          // staged source rows / cols
+  int NAr, NAc;          // accumulator rows / cols
+  int off_P, off_W, off_H, off_G, off_A;   // float offsets in dynamic smem
+  size_t smem_bytes;
+  int ctas_per_sm;
+  int threads;
+};
+
+struct OpArgs {
+  const float* src;      // HR source (x or p) for FWD/NORMAL/DATA; LR g for ADJ
+  const float* disp;     // HR disparity
+  float* out;            // HR accumulator target (atomics) or LR output (FWD)
+  const float* y;        // DATA: LR views
+  const float* wA_old;   // DATA: data duals (read)
+  float* wA_new;         // DATA: data duals (written)
+  float scale;           // multiplies the accumulator on flush
+  int view0, nviews;     // views of this launch
+  int units;             // n_tiles * nviews
+  double* partials;      // per-CTA partials of this kernel's reduction
+  DevScalars* sc;
+  int check_done;        // return at once when sc->cg_done (CG steps)
+};
+
+struct NlArgs {
+  const float* x;        // weights source x^(n-1)
+  const float* r;        // APPLY: CG residual
+  const float* p_old;    // APPLY: previous direction
+  float* p_new;          // APPLY: new direction (written)
+  float* out;            // BLOCK: v (stored); APPLY: q (stored); WEIGHTS: w
+  const float* wS_old;   // BLOCK: pair-layout duals (read)
+  float* wS_new;         // BLOCK: pair-layout duals (written)
+  double* partials;
+  DevScalars* sc;
+  int use_beta;          // APPLY: p_new = r + beta p_old (else p_new = src p)
+  int check_done;
+};
+
+struct NlPlan {
+  int TH, TW, tiles_x, tiles_y, n_tiles;
+  int NXr, NXc;          // staged x region
+  int NQr, NQc;          // squared-difference / box region
+  size_t smem_bytes;
+  int threads;
+};
+
+// Host launchers (stream-ordered, no synchronisation).
+cudaError_t op_prepare(int zeta);
+cudaError_t nl_prepare();
+cudaError_t op_plan(const Geom& g, OpPlan* plan, int sm_count);
+cudaError_t op_launch(int mode, const Geom& g, const OpPlan& plan, const OpArgs& a,
+                      int grid, cudaStream_t s);
+int op_grid(const OpPlan& plan, int units, int sm_count);
+
+cudaError_t nl_plan(const Geom& g, NlPlan* plan);
+cudaError_t nl_launch(int mode, const Geom& g, const NlPlan& plan, const NlArgs& a,
+                      cudaStream_t s);
+
+cudaError_t cg_init_launch(const Geom& g, float* r_inout_v, const float* x, float* x_next,
+                           double* partials_pi, DevScalars* sc, int grid, cudaStream_t s);
+cudaError_t cg_update_launch(const Geom& g, const float* p, const float* q, float* x_next,
+                             float* r, double* partials_pi, DevScalars* sc, int grid,
+                             cudaStream_t s);
+cudaError_t pair_from_canonical(const Geom& g, const float* can, float* pair, cudaStream_t s);
+cudaError_t pair_to_canonical(const Geom& g, const float* pair, float* can, cudaStream_t s);
+cudaError_t scalars_reset(DevScalars* sc, cudaStream_t s);
+
+}  // namespace lfsr

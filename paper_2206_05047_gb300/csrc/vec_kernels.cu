@@ -1,0 +1,139 @@
+// Vector steps of the conjugate-gradient x-step (Algorithm 2): the
+// initialisation r = -v, pi = <r, r> and the update x += alpha p,
+// r -= alpha q, pi' = <r, r>, beta = pi'/pi.  Inner products accumulate in
+// float64 and finish with a last-block reduction, so the scalars never leave
+// the device.  Also the conversions between the canonical regulariser-dual
+// layout [d][u] and the kernels' edge-pair layout.
+#include "lfsr_device.cuh"
+
+namespace lfsr {
+
+constexpr int VEC_THREADS = 512;
+
+__global__ void __launch_bounds__(VEC_THREADS)
+k_cg_init(const Geom g, float* __restrict__ rv, const float* __restrict__ x,
+          float* __restrict__ x_next, double* partials, DevScalars* sc) {
+  const size_t n = (size_t)g.Hh * g.Wh;
+  double part = 0.0;
+  for (size_t i = (size_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * VEC_THREADS) {
+    const float r = -rv[i];
+    rv[i] = r;
+    x_next[i] = x[i];
+    part += (double)r * (double)r;
+  }
+  double total = 0.0;
+  if (grid_sum_last<VEC_THREADS>(part, partials, &sc->counter[RED_PI], &total) &&
+      threadIdx.x == 0) {
+    sc->pi = total;
+    sc->cg_first = 1;
+    sc->cg_steps = 0;
+    sc->beta = 0.0;
+    sc->dw2 = sc->dwA + sc->dwS;
+    if (!isfinite(total)) sc->status = -4;
+    sc->cg_done = (total > g.tau && isfinite(total)) ? 0 : 1;
+  }
+}
+
+__global__ void __launch_bounds__(VEC_THREADS)
+k_cg_update(const Geom g, const float* __restrict__ p, const float* __restrict__ q,
+            float* __restrict__ x_next, float* __restrict__ r, double* partials,
+            DevScalars* sc) {
+  if (sc->cg_done) return;
+  const float alpha = (float)sc->alpha;
+  const size_t n = (size_t)g.Hh * g.Wh;
+  double part = 0.0;
+  for (size_t i = (size_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * VEC_THREADS) {
+    x_next[i] = fmaf(alpha, p[i], x_next[i]);
+    const float rn = fmaf(-alpha, q[i], r[i]);
+    r[i] = rn;
+    part += (double)rn * (double)rn;
+  }
+  double total = 0.0;
+  if (grid_sum_last<VEC_THREADS>(part, partials, &sc->counter[RED_PI], &total) &&
+      threadIdx.x == 0) {
+    const double pi_old = sc->pi;
+    sc->beta = total / pi_old;
+    sc->pi = total;
+    sc->cg_first = 0;
+    sc->cg_steps += 1;
+    if (!isfinite(total)) sc->status = -4;
+    if (!(total > g.tau) || !isfinite(total)) sc->cg_done = 1;
+  }
+}
+
+cudaError_t cg_init_launch(const Geom& g, float* rv, const float* x, float* x_next,
+                           double* partials, DevScalars* sc, int grid, cudaStream_t s) {
+  k_cg_init<<<grid, VEC_THREADS, 0, s>>>(g, rv, x, x_next, partials, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t cg_update_launch(const Geom& g, const float* p, const float* q, float* x_next,
+                             float* r, double* partials, DevScalars* sc, int grid,
+                             cudaStream_t s) {
+  k_cg_update<<<grid, VEC_THREADS, 0, s>>>(g, p, q, x_next, r, partials, sc);
+  return cudaGetLastError();
+}
+
+// canonical [d][u] (d over the full window minus the centre, raster order)
+// <-> pair layout [idx][0][u] = dual of d_idx at u,
+//                 [idx][1][u] = dual of -d_idx at u + d_idx   (idx < s_d/2)
+__global__ void k_pair_from_canonical(const Geom g, const float* __restrict__ can,
+                                      float* __restrict__ pair) {
+  const size_t p = (size_t)g.Hh * g.Wh;
+  const int sd = 2 * g.sh;
+  const size_t total = (size_t)g.sh * p;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int idx = (int)(t / p);
+    const size_t u = t - (size_t)idx * p;
+    const int ui = (int)(u / g.Wh), uj = (int)(u - (size_t)ui * g.Wh);
+    const int vi = ui + g.di[idx], vj = uj + g.dj[idx];
+    pair[(size_t)(2 * idx) * p + u] = can[(size_t)idx * p + u];
+    float b = 0.f;
+    if (vi >= 0 && vi < g.Hh && vj >= 0 && vj < g.Wh)
+      b = can[(size_t)(sd - 1 - idx) * p + (size_t)vi * g.Wh + vj];
+    pair[(size_t)(2 * idx + 1) * p + u] = b;
+  }
+}
+
+__global__ void k_pair_to_canonical(const Geom g, const float* __restrict__ pair,
+                                    float* __restrict__ can) {
+  const size_t p = (size_t)g.Hh * g.Wh;
+  const int sd = 2 * g.sh;
+  const size_t total = (size_t)sd * p;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int d = (int)(t / p);
+    const size_t u = t - (size_t)d * p;
+    float val = 0.f;
+    if (d < g.sh) {
+      val = pair[(size_t)(2 * d) * p + u];
+    } else {
+      // direction -d_idx at u is the second dual of edge (u - d_idx, u)
+      const int idx = sd - 1 - d;
+      const int ui = (int)(u / g.Wh), uj = (int)(u - (size_t)ui * g.Wh);
+      const int vi = ui - g.di[idx], vj = uj - g.dj[idx];
+      if (vi >= 0 && vi < g.Hh && vj >= 0 && vj < g.Wh)
+        val = pair[(size_t)(2 * idx + 1) * p + (size_t)vi * g.Wh + vj];
+    }
+    can[t] = val;
+  }
+}
+
+cudaError_t pair_from_canonical(const Geom& g, const float* can, float* pair, cudaStream_t s) {
+  k_pair_from_canonical<<<1024, 256, 0, s>>>(g, can, pair);
+  return cudaGetLastError();
+}
+
+cudaError_t pair_to_canonical(const Geom& g, const float* pair, float* can, cudaStream_t s) {
+  k_pair_to_canonical<<<1024, 256, 0, s>>>(g, pair, can);
+  return cudaGetLastError();
+}
+
+cudaError_t scalars_reset(DevScalars* sc, cudaStream_t s) {
+  return cudaMemsetAsync(sc, 0, sizeof(DevScalars), s);
+}
+
+}  // namespace lfsr

@@ -1,0 +1,270 @@
+"""Python binding of liblfsr (include/lfsr.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Arrays are
+either CUDA torch tensors (passed as device pointers, LFSR_MEM_DEVICE) or
+numpy arrays (host memory, LFSR_MEM_HOST); float32, C-contiguous.  All work
+runs in the CUDA library; if the library is missing or fails to load the
+import raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+LFSR_OK = 0
+LFSR_EINVAL = -1
+LFSR_ENOMEM = -2
+LFSR_ECUDA = -3
+LFSR_ENUMERIC = -4
+LFSR_ETIMEOUT = -5
+LFSR_EUNSUPPORTED = -6
+LFSR_MEM_HOST = 0
+LFSR_MEM_DEVICE = 1
+LFSR_FP32 = 0
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblfsr.so")
+
+# Entry points declared in include/lfsr.h (checked by the test-suite).
+EXPORTS = ("lfsr_create", "lfsr_solve", "lfsr_destroy", "lfsr_last_error", "lfsr_stats",
+           "lfsr_load", "lfsr_iterate", "lfsr_get_x", "lfsr_set_state", "lfsr_get_state",
+           "lfsr_apply_A", "lfsr_apply_AT", "lfsr_weights", "lfsr_apply_normal",
+           "lfsr_set_profiling")
+
+
+class lfsr_params(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("U", C.c_int32), ("V", C.c_int32),
+                ("H", C.c_int32), ("W", C.c_int32), ("scale", C.c_int32), ("kb", C.c_int32),
+                ("blur", C.POINTER(C.c_float)), ("disparity", C.POINTER(C.c_float)),
+                ("lambda1", C.c_double), ("lambda2", C.c_double), ("mu", C.c_double),
+                ("nltv_window", C.c_int32), ("nltv_patch", C.c_int32), ("nltv_h", C.c_double),
+                ("cg_iters", C.c_int32), ("cg_tol", C.c_double), ("precision", C.c_int32)]
+
+
+class lfsr_stats_t(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("iterations", C.c_int32), ("cg_steps", C.c_int32),
+                ("status", C.c_int32), ("dual_change_sq", C.c_double), ("cg_pi", C.c_double),
+                ("state_bytes", C.c_int64), ("launches", C.c_int64),
+                ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_int64 * 8)]
+
+
+class LfsrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lfsr error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = _LIB_PATH):
+    """Loads liblfsr.so (raises if it is missing: there is no CPU path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing; build it with __graft_entry__.build()")
+    lib = C.CDLL(path)
+    H = C.c_void_p
+    fp = C.c_void_p
+    sig = {
+        "lfsr_create": (C.c_int, [C.POINTER(lfsr_params), C.c_void_p, C.POINTER(C.c_void_p)]),
+        "lfsr_solve": (C.c_int, [H, fp, C.c_int, fp, fp, C.c_int]),
+        "lfsr_destroy": (None, [H]),
+        "lfsr_last_error": (C.c_char_p, [H]),
+        "lfsr_stats": (C.c_int, [H, C.POINTER(lfsr_stats_t)]),
+        "lfsr_load": (C.c_int, [H, fp, fp, C.c_int]),
+        "lfsr_iterate": (C.c_int, [H, C.c_int]),
+        "lfsr_get_x": (C.c_int, [H, fp, C.c_int]),
+        "lfsr_set_state": (C.c_int, [H, fp, fp, fp, C.c_int]),
+        "lfsr_get_state": (C.c_int, [H, fp, fp, fp, C.c_int]),
+        "lfsr_apply_A": (C.c_int, [H, C.c_int, fp, fp, C.c_int]),
+        "lfsr_apply_AT": (C.c_int, [H, C.c_int, fp, fp, C.c_int]),
+        "lfsr_weights": (C.c_int, [H, fp, fp, C.c_int]),
+        "lfsr_apply_normal": (C.c_int, [H, fp, fp, fp, C.POINTER(C.c_double), C.c_int]),
+        "lfsr_set_profiling": (C.c_int, [H, C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a, count: Optional[int] = None):
+    """(pointer, mem_kind) of a float32 contiguous array / CUDA tensor."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags.c_contiguous:
+            raise TypeError("numpy arrays must be float32 and C-contiguous")
+        if count is not None and a.size != count:
+            raise ValueError(f"expected {count} elements, got {a.size}")
+        return a.ctypes.data, LFSR_MEM_HOST
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise TypeError("expected a numpy array or a torch tensor")
+    if a.dtype != torch.float32 or not a.is_contiguous():
+        raise TypeError("tensors must be float32 and contiguous")
+    if count is not None and a.numel() != count:
+        raise ValueError(f"expected {count} elements, got {a.numel()}")
+    if a.is_cuda:
+        return a.data_ptr(), LFSR_MEM_DEVICE
+    return a.data_ptr(), LFSR_MEM_HOST
+
+
+def _kind(*kinds):
+    ks = {k for k in kinds if k is not None}
+    if len(ks) != 1:
+        raise ValueError("all arrays of one call must live in the same memory (host or device)")
+    return ks.pop()
+
+
+def last_error(handle) -> str:
+    return load_library().lfsr_last_error(handle).decode()
+
+
+def _check(rc: int, handle=None):
+    if rc != LFSR_OK:
+        raise LfsrError(rc, last_error(handle))
+
+
+def create(U, V, H, W, scale, blur, disparity, lambda1=1.0, lambda2=4.0, mu=1.0,
+           nltv_window=5, nltv_patch=3, nltv_h=0.1, cg_iters=5, cg_tol=0.0,
+           precision=LFSR_FP32, stream=None):
+    """lfsr_create; returns an opaque handle.  stream: torch.cuda.Stream,
+    an integer cudaStream_t, or None (the current torch stream if torch has
+    CUDA, else the legacy default stream)."""
+    lib = load_library()
+    blur = np.ascontiguousarray(blur, dtype=np.float32)
+    disp = np.ascontiguousarray(disparity, dtype=np.float32)
+    prm = lfsr_params(C.sizeof(lfsr_params), U, V, H, W, scale, blur.shape[0],
+                      blur.ctypes.data_as(C.POINTER(C.c_float)),
+                      disp.ctypes.data_as(C.POINTER(C.c_float)),
+                      lambda1, lambda2, mu, nltv_window, nltv_patch, nltv_h, cg_iters, cg_tol,
+                      precision)
+    if stream is None:
+        try:
+            import torch
+            s = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        except ImportError:
+            s = 0
+    elif isinstance(stream, int):
+        s = stream
+    else:
+        s = stream.cuda_stream
+    h = C.c_void_p()
+    _check(lib.lfsr_create(C.byref(prm), C.c_void_p(s), C.byref(h)))
+    return h
+
+
+def destroy(handle) -> None:
+    load_library().lfsr_destroy(handle)
+
+
+def solve(handle, lr_views, iterations: int, x0, x_out) -> None:
+    py, ky = _ptr(lr_views)
+    px, kx = _ptr(x0)
+    po, ko = _ptr(x_out)
+    _check(load_library().lfsr_solve(handle, py, int(iterations), px, po, _kind(ky, kx, ko)), handle)
+
+
+def load(handle, lr_views, x0) -> None:
+    py, ky = _ptr(lr_views)
+    px, kx = _ptr(x0)
+    _check(load_library().lfsr_load(handle, py, px, _kind(ky, kx)), handle)
+
+
+def iterate(handle, iterations: int) -> None:
+    _check(load_library().lfsr_iterate(handle, int(iterations)), handle)
+
+
+def get_x(handle, x_out) -> None:
+    po, ko = _ptr(x_out)
+    _check(load_library().lfsr_get_x(handle, po, ko), handle)
+
+
+def set_state(handle, x=None, wA=None, wS=None) -> None:
+    (a, ka), (b, kb), (c, kc) = _ptr(x), _ptr(wA), _ptr(wS)
+    _check(load_library().lfsr_set_state(handle, a, b, c, _kind(ka, kb, kc)), handle)
+
+
+def get_state(handle, x=None, wA=None, wS=None) -> None:
+    (a, ka), (b, kb), (c, kc) = _ptr(x), _ptr(wA), _ptr(wS)
+    _check(load_library().lfsr_get_state(handle, a, b, c, _kind(ka, kb, kc)), handle)
+
+
+def apply_A(handle, view: int, x, out) -> None:
+    (a, ka), (b, kb) = _ptr(x), _ptr(out)
+    _check(load_library().lfsr_apply_A(handle, int(view), a, b, _kind(ka, kb)), handle)
+
+
+def apply_AT(handle, view: int, g, out) -> None:
+    (a, ka), (b, kb) = _ptr(g), _ptr(out)
+    _check(load_library().lfsr_apply_AT(handle, int(view), a, b, _kind(ka, kb)), handle)
+
+
+def weights(handle, x, w) -> None:
+    (a, ka), (b, kb) = _ptr(x), _ptr(w)
+    _check(load_library().lfsr_weights(handle, a, b, _kind(ka, kb)), handle)
+
+
+def apply_normal(handle, xw, p, q) -> float:
+    (a, ka), (b, kb), (c, kc) = _ptr(xw), _ptr(p), _ptr(q)
+    out = C.c_double(0.0)
+    _check(load_library().lfsr_apply_normal(handle, a, b, c, C.byref(out), _kind(ka, kb, kc)),
+           handle)
+    return out.value
+
+
+def set_profiling(handle, on: bool) -> None:
+    _check(load_library().lfsr_set_profiling(handle, int(bool(on))), handle)
+
+
+def stats(handle) -> dict:
+    st = lfsr_stats_t()
+    st.struct_size = C.sizeof(lfsr_stats_t)
+    _check(load_library().lfsr_stats(handle, C.byref(st)), handle)
+    return dict(iterations=st.iterations, cg_steps=st.cg_steps, status=st.status,
+                dual_change_sq=st.dual_change_sq, cg_pi=st.cg_pi, state_bytes=st.state_bytes,
+                launches=st.launches, kernel_ms=list(st.kernel_ms),
+                kernel_launches=list(st.kernel_launches))
+
+
+class Solver:
+    """Owns one handle; a convenience wrapper over the functions above."""
+
+    def __init__(self, problem=None, **kw):
+        if problem is not None:
+            wl = problem.wl
+            base = dict(U=wl.U, V=wl.V, H=wl.H, W=wl.W, scale=wl.scale, blur=problem.blur,
+                        disparity=problem.disparity, lambda1=wl.lambda1, lambda2=wl.lambda2,
+                        mu=wl.mu, nltv_window=wl.window, nltv_patch=wl.patch, nltv_h=wl.h,
+                        cg_iters=wl.cg_iters)
+            base.update(kw)
+            kw = base
+        self.kw = kw
+        self.handle = create(**kw)
+        self.s_k = kw["U"] * kw["V"]
+        self.hr = (kw["scale"] * kw["H"], kw["scale"] * kw["W"])
+        self.s_d = kw.get("nltv_window", 5) ** 2 - 1
+
+    def close(self):
+        if self.handle is not None:
+            destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,60 @@
+"""Helpers shared by the GPU parity tests: build the same float32 inputs for
+the CUDA path and (as float64) for the oracle."""
+import numpy as np
+
+from paper_2206_05047_gb300 import synth
+
+
+def f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def rel_err(a, ref):
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.linalg.norm(a - ref) / max(np.linalg.norm(ref), 1e-30))
+
+
+def max_err(a, ref):
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.abs(a - ref).max() / max(np.abs(ref).max(), 1e-30))
+
+
+class Case:
+    """One problem: float32 arrays, an oracle on their float64 images and a
+    GPU solver on the same float32 values."""
+
+    def __init__(self, wl, seed=0, blur=None, disparity=None, **overrides):
+        import torch
+        from oracle import oracle as om
+        from paper_2206_05047_gb300 import lfsr
+        self.wl = wl
+        self.prob = synth.make_problem(wl, seed=seed)
+        self.blur = f32(self.prob.blur if blur is None else blur)
+        self.disp = f32(self.prob.disparity if disparity is None else disparity)
+        self.y = f32(self.prob.y)
+        self.x0 = f32(self.prob.x0)
+        self.params = dict(lambda1=wl.lambda1, lambda2=wl.lambda2, mu=wl.mu, window=wl.window,
+                           patch=wl.patch, h=wl.h, cg_iters=wl.cg_iters, cg_tol=0.0)
+        self.params.update(overrides)
+        p = self.params
+        self.oracle = om.Oracle(wl.U, wl.V, wl.H, wl.W, wl.scale, self.blur.astype(np.float64),
+                                self.disp.astype(np.float64), **p)
+        self.solver = lfsr.Solver(U=wl.U, V=wl.V, H=wl.H, W=wl.W, scale=wl.scale, blur=self.blur,
+                                  disparity=self.disp, lambda1=p["lambda1"], lambda2=p["lambda2"],
+                                  mu=p["mu"], nltv_window=p["window"], nltv_patch=p["patch"],
+                                  nltv_h=p["h"], cg_iters=p["cg_iters"], cg_tol=p["cg_tol"])
+        self.h = self.solver.handle
+        self.torch = torch
+        self.dev = torch.device("cuda:0")
+
+    def t(self, a):
+        return self.torch.from_numpy(f32(a)).to(self.dev)
+
+    def empty(self, *shape):
+        return self.torch.empty(*shape, dtype=self.torch.float32, device=self.dev)
+
+    @staticmethod
+    def np(t):
+        return t.detach().cpu().numpy().astype(np.float64)
