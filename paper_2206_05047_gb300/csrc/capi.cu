@@ -366,26 +366,31 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   h->nS = (size_t)(2 * g.sh) * p;
   h->nSpair = h->nS;
 
+  int optin = 0;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (e != cudaSuccess) {
     rc = cuda_fail(nullptr, e, "device query");
     delete h;
     return rc;
   }
-  e = op_prepare(g.zeta);
-  if (e == cudaSuccess) e = nl_prepare();
+  e = op_prepare(g.zeta, optin);
+  if (e == cudaSuccess) e = nl_prepare(optin);
   if (e != cudaSuccess) {
     rc = cuda_fail(nullptr, e, "kernel attributes");
     delete h;
     return rc;
   }
-  if (op_plan(g, &h->op, h->sm_count) != cudaSuccess) {
+  // static shared memory of the kernels (reduction scratch) stays below 1 KB
+  const int smem_limit = optin - 1024;
+  if (op_plan(g, &h->op, h->sm_count, smem_limit) != cudaSuccess) {
     delete h;
     return fail(nullptr, LFSR_EUNSUPPORTED,
                 "disparity * angular offset too large for the shared-memory tile");
   }
-  if (nl_plan(g, &h->nl) != cudaSuccess) {
+  if (nl_plan(g, &h->nl, smem_limit) != cudaSuccess) {
     delete h;
     return fail(nullptr, LFSR_EUNSUPPORTED, "NLTV window / patch too large");
   }

@@ -109,15 +109,26 @@ struct NlPlan {
   int threads;
 };
 
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum minus the kernel's static shared memory.
+template <class K>
+inline cudaError_t set_max_dynamic_smem(K kernel, int smem_optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_optin - (int)fa.sharedSizeBytes);
+}
+
 // Host launchers (stream-ordered, no synchronisation).
-cudaError_t op_prepare(int zeta);
-cudaError_t nl_prepare();
-cudaError_t op_plan(const Geom& g, OpPlan* plan, int sm_count);
+cudaError_t op_prepare(int zeta, int smem_optin);
+cudaError_t nl_prepare(int smem_optin);
+cudaError_t op_plan(const Geom& g, OpPlan* plan, int sm_count, int smem_limit);
 cudaError_t op_launch(int mode, const Geom& g, const OpPlan& plan, const OpArgs& a,
                       int grid, cudaStream_t s);
 int op_grid(const OpPlan& plan, int units, int sm_count);
 
-cudaError_t nl_plan(const Geom& g, NlPlan* plan);
+cudaError_t nl_plan(const Geom& g, NlPlan* plan, int smem_limit);
 cudaError_t nl_launch(int mode, const Geom& g, const NlPlan& plan, const NlArgs& a,
                       cudaStream_t s);
 

@@ -192,7 +192,7 @@ k_nltv(const Geom g, const NlPlan P, const NlArgs a) {
   }
 }
 
-cudaError_t nl_plan(const Geom& g, NlPlan* P) {
+cudaError_t nl_plan(const Geom& g, NlPlan* P, int smem_limit) {
   const int wr = g.win_r, pr = g.patch_r;
   P->TH = NL_TH;
   P->TW = NL_TW;
@@ -207,7 +207,7 @@ cudaError_t nl_plan(const Geom& g, NlPlan* P) {
                         2 * (size_t)P->NQr * P->NQc;
   P->smem_bytes = floats * sizeof(float);
   P->threads = NL_THREADS;
-  return P->smem_bytes <= 227 * 1024 ? cudaSuccess : cudaErrorInvalidValue;
+  return P->smem_bytes <= (size_t)smem_limit ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <int MODE>
@@ -218,11 +218,10 @@ static cudaError_t nl_launch_t(const Geom& g, const NlPlan& P, const NlArgs& a, 
 
 // Raises the dynamic shared-memory limit of the NLTV kernels (current
 // device; called outside any stream capture).
-cudaError_t nl_prepare() {
-  const int lim = 227 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_nltv<NL_BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_nltv<NL_APPLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_nltv<NL_WEIGHTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+cudaError_t nl_prepare(int optin) {
+  cudaError_t e = set_max_dynamic_smem(k_nltv<NL_BLOCK>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(k_nltv<NL_APPLY>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(k_nltv<NL_WEIGHTS>, optin);
   return e;
 }
 

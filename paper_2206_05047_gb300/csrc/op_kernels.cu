@@ -328,24 +328,22 @@ static cudaError_t op_launch_t(const Geom& g, const OpPlan& P, const OpArgs& a, 
 }
 
 template <int Z>
-static cudaError_t op_prepare_z() {
-  cudaError_t e = cudaSuccess;
-  const int lim = 227 * 1024;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_operator<OP_NORMAL, Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_operator<OP_DATA, Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_operator<OP_FWD, Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_operator<OP_ADJ, Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+static cudaError_t op_prepare_z(int optin) {
+  cudaError_t e = set_max_dynamic_smem(k_operator<OP_NORMAL, Z>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator<OP_DATA, Z>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator<OP_FWD, Z>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator<OP_ADJ, Z>, optin);
   return e;
 }
 
 // Raises the dynamic shared-memory limit of every operator kernel of this
 // scale (the current device; called outside any stream capture).
-cudaError_t op_prepare(int zeta) {
+cudaError_t op_prepare(int zeta, int optin) {
   switch (zeta) {
-    case 1: return op_prepare_z<1>();
-    case 2: return op_prepare_z<2>();
-    case 3: return op_prepare_z<3>();
-    case 4: return op_prepare_z<4>();
+    case 1: return op_prepare_z<1>(optin);
+    case 2: return op_prepare_z<2>(optin);
+    case 3: return op_prepare_z<3>(optin);
+    case 4: return op_prepare_z<4>(optin);
   }
   return cudaErrorInvalidValue;
 }
@@ -385,9 +383,9 @@ static int op_occupancy(size_t smem) {
 
 // Picks the largest tile whose shared-memory layout fits, and the resident
 // CTAs per SM (op_prepare must have raised the smem limit first).
-cudaError_t op_plan(const Geom& g, OpPlan* P, int sm_count) {
+cudaError_t op_plan(const Geom& g, OpPlan* P, int sm_count, int smem_limit) {
   (void)sm_count;
-  const size_t limit = 227 * 1024;
+  const size_t limit = (size_t)smem_limit;
   static const int shapes[][2] = {{64, 64}, {32, 64}, {32, 32}, {16, 32}, {16, 16}, {8, 16}, {8, 8}};
   for (auto& sh : shapes) {
     if (op_layout(g, sh[0], sh[1], P) <= limit) {
