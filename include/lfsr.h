@@ -175,6 +175,44 @@ int lfsr_apply_normal(lfsr_handle *h, const float *xw, const float *p, float *q,
  * kernel time.  Off by default. */
 int lfsr_set_profiling(lfsr_handle *h, int on);
 
+/* ---- no-allocation variant ------------------------------------------
+ *
+ * Some callers cannot allocate device memory: code that runs inside a host
+ * framework whose allocator owns the whole device heap (a cudaMalloc behind
+ * its back fragments or exhausts its pool), callers in processes held to a
+ * hard device-memory cap, and latency-critical callers that cannot afford
+ * the device-wide synchronisation cudaMalloc and cudaFree may imply.  For
+ * them this entry point computes what lfsr_apply_normal computes -- q = M p
+ * and <p, M p> -- without a handle and without allocating anything.  It has
+ * no counterpart in the paper; it is a packaging of the same kernels.
+ *
+ * The kernels' scratch (float64 block partials, reduction counters and
+ * totals) lives in one fixed array of LFSR_NOALLOC_SCRATCH_BYTES in device
+ * memory, defined at file scope in the library: every GPU that loads the
+ * library holds it until the process exits.
+ *   - The first call on each device (with that device current) looks up
+ *     the array's device address and raises the kernels' shared-memory
+ *     limits; make that first call before any stream capture.
+ *   - Every call uses the same array and clears its counters first.  Calls
+ *     that overlap on the GPU (other streams, other host threads) race on
+ *     it: serialise them.
+ *   - Sizes beyond the array are rejected with LFSR_EINVAL: the HR image may
+ *     hold at most LFSR_NOALLOC_MAX_TILES tiles of 32 x 32 pixels (e.g.
+ *     2048 x 2048).
+ *
+ * params: as for lfsr_create (host blur; host disparity, read only for the
+ * shift bound).  d_disparity, d_xw (weights source), d_p and d_q are device
+ * pointers of the current device (Hh*Wh floats each); *pMp (host) receives
+ * <p, M p> in float64.  Work is ordered on cuda_stream and the call blocks
+ * until it is done.  The message of a failure is readable with
+ * lfsr_last_error(NULL). */
+#define LFSR_NOALLOC_MAX_TILES 4096
+#define LFSR_NOALLOC_SCRATCH_BYTES (64 * 1024 + 256)
+
+int lfsr_apply_normal_noalloc(const lfsr_params *params, const float *d_disparity,
+                              const float *d_xw, const float *d_p, float *d_q,
+                              double *pMp, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -300,6 +300,8 @@ int validate(const lfsr_params* pr) {
 
 }  // namespace
 
+void lfsr::set_thread_error(const char* msg) { t_err = msg; }
+
 extern "C" {
 
 int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {

@@ -141,4 +141,7 @@ cudaError_t pair_from_canonical(const Geom& g, const float* can, float* pair, cu
 cudaError_t pair_to_canonical(const Geom& g, const float* pair, float* can, cudaStream_t s);
 cudaError_t scalars_reset(DevScalars* sc, cudaStream_t s);
 
+// Sets the thread-local message that lfsr_last_error(NULL) returns.
+void set_thread_error(const char* msg);
+
 }  // namespace lfsr

@@ -1,0 +1,226 @@
+// lfsr_apply_normal_noalloc: the x-step normal-matrix product q = M p and
+// <p, M p> without a handle and without any device allocation.
+//
+// The two kernels it runs (k_nltv<NL_APPLY>, k_operator<OP_NORMAL>) need
+// global scratch for their float64 block partials, last-block counters and
+// finished totals.  Here that scratch is a file-scope __device__ array of
+// fixed size, present on every GPU that loads the library until the process
+// exits.  Host code only holds a host-side stand-in for the array's name, so
+// the array's device address is looked up with cudaGetSymbolAddress once per
+// device (with that device current) and passed to the kernels.
+#include <cmath>
+#include <cstddef>
+#include <mutex>
+
+#include "lfsr.h"
+#include "lfsr_internal.cuh"
+
+using namespace lfsr;
+
+// The no-allocation scratch: block partials, counters and totals of the two
+// grid reductions.  Zero-initialised at module load; cleared again (the
+// scalars) at the start of every call.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LFSR_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxCtas = LFSR_NOALLOC_MAX_TILES;
+constexpr int kMaxDevices = 64;
+
+struct NoallocScratch {
+  DevScalars sc;
+  double partials[2][kMaxCtas];   // [0] NLTV part, [1] operator part
+};
+
+static_assert(sizeof(NoallocScratch) <= LFSR_NOALLOC_SCRATCH_BYTES, "scratch size");
+
+struct DeviceSetup {
+  bool ready = false;
+  unsigned zeta_ready = 0;   // bit z: operator kernels of scale z prepared
+  NoallocScratch* scratch = nullptr;
+  int sm_count = 0;
+  int optin = 0;
+};
+
+std::mutex g_mu;
+DeviceSetup g_dev[kMaxDevices];
+
+// Per-device set-up (first call on a device): device address of the scratch
+// array, SM count, shared-memory limits of the kernels.
+int setup_device(int dev, int zeta, DeviceSetup* out, const char** err) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceSetup& d = g_dev[dev];
+  if (!d.ready) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
+      *err = "cudaGetSymbolAddress of the no-allocation scratch failed";
+      return LFSR_ECUDA;
+    }
+    if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&d.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess ||
+        nl_prepare(d.optin) != cudaSuccess) {
+      *err = "device query / kernel attributes failed";
+      return LFSR_ECUDA;
+    }
+    d.scratch = static_cast<NoallocScratch*>(ptr);
+    d.ready = true;
+  }
+  if (!(d.zeta_ready & (1u << zeta))) {
+    if (op_prepare(zeta, d.optin) != cudaSuccess) {
+      *err = "kernel attributes failed";
+      return LFSR_ECUDA;
+    }
+    d.zeta_ready |= 1u << zeta;
+  }
+  *out = d;
+  return LFSR_OK;
+}
+
+// the message is readable with lfsr_last_error(NULL)
+int nfail(int code, const char* msg) {
+  set_thread_error(msg);
+  return code;
+}
+
+}  // namespace
+
+extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_disparity,
+                                         const float* d_xw, const float* d_p, float* d_q,
+                                         double* pMp, void* cuda_stream) {
+  if (!pr || pr->struct_size != sizeof(lfsr_params))
+    return nfail(LFSR_EINVAL, "params missing or struct_size mismatch");
+  if (!d_disparity || !d_xw || !d_p || !d_q)
+    return nfail(LFSR_EINVAL, "device pointers d_disparity, d_xw, d_p, d_q are required");
+  if (!pr->blur || !pr->disparity) return nfail(LFSR_EINVAL, "params blur and disparity are required");
+  if (pr->U < 1 || pr->V < 1 || !(pr->U & 1) || !(pr->V & 1) || pr->U * pr->V > LFSR_MAX_VIEWS)
+    return nfail(LFSR_EINVAL, "U and V must be odd, >= 1, with U*V <= 289");
+  if (pr->H < 1 || pr->W < 1 || pr->scale < 1 || pr->scale > 4 || pr->kb < 1 || !(pr->kb & 1) ||
+      pr->kb > LFSR_MAX_KB || pr->nltv_window < 3 || pr->nltv_window > 15 ||
+      !(pr->nltv_window & 1) || pr->nltv_patch < 1 || pr->nltv_patch > 7 ||
+      !(pr->nltv_patch & 1) || !(pr->nltv_h > 0.0) || !(pr->mu > 0.0) ||
+      !(pr->lambda1 >= 0.0) || !(pr->lambda2 >= 0.0))
+    return nfail(LFSR_EINVAL, "invalid size or parameter");
+  const long long Hh = (long long)pr->scale * pr->H, Wh = (long long)pr->scale * pr->W;
+  // the NLTV kernel runs one CTA per 32 x 32 HR tile; its partials must fit
+  const long long nl_tiles = ((Hh + 31) / 32) * ((Wh + 31) / 32);
+  if (nl_tiles > kMaxCtas)
+    return nfail(LFSR_EINVAL,
+                 "HR image too large for the no-allocation scratch (at most 4096 tiles of 32x32)");
+
+  Geom g{};
+  g.U = pr->U;
+  g.V = pr->V;
+  g.sk = pr->U * pr->V;
+  g.H = pr->H;
+  g.W = pr->W;
+  g.Hh = (int)Hh;
+  g.Wh = (int)Wh;
+  g.zeta = pr->scale;
+  g.kb = pr->kb;
+  g.r = (pr->kb - 1) / 2;
+  {
+    const int kb = pr->kb;
+    int am = 0, bm = 0;
+    double best = -1.0;
+    for (int i = 0; i < kb * kb; ++i) {
+      g.k2[i] = pr->blur[i];
+      if (std::fabs((double)pr->blur[i]) > best) {
+        best = std::fabs((double)pr->blur[i]);
+        am = i / kb;
+        bm = i % kb;
+      }
+    }
+    g.separable = 0;
+    if (best > 0.0) {
+      const double pivot = pr->blur[am * kb + bm];
+      double err = 0.0;
+      for (int a = 0; a < kb; ++a)
+        for (int b = 0; b < kb; ++b)
+          err = std::fmax(err, std::fabs((double)pr->blur[a * kb + bm] *
+                                             (double)pr->blur[am * kb + b] / pivot -
+                                         (double)pr->blur[a * kb + b]));
+      if (err <= 1e-7 * best) {
+        g.separable = 1;
+        for (int a = 0; a < kb; ++a) g.kv[a] = pr->blur[a * kb + bm];
+        for (int b = 0; b < kb; ++b) g.kh[b] = (float)((double)pr->blur[am * kb + b] / pivot);
+      }
+    }
+  }
+  double max_disp = 0.0;
+  for (long long i = 0; i < Hh * Wh; ++i)
+    max_disp = std::fmax(max_disp, std::fabs((double)pr->disparity[i]));
+  g.S = (int)std::ceil(max_disp * 0.5 * (double)((pr->U > pr->V ? pr->U : pr->V) - 1));
+  for (int k = 0; k < g.sk; ++k) {
+    g.tu[k] = (float)((k % pr->U) - 0.5 * (pr->U - 1));
+    g.tv[k] = (float)((k / pr->U) - 0.5 * (pr->V - 1));
+  }
+  g.win_r = (pr->nltv_window - 1) / 2;
+  g.patch_r = (pr->nltv_patch - 1) / 2;
+  g.sh = (pr->nltv_window * pr->nltv_window - 1) / 2;
+  for (int a = -g.win_r, n = 0; a <= g.win_r && n < g.sh; ++a)
+    for (int b = -g.win_r; b <= g.win_r && n < g.sh; ++b, ++n) {
+      g.di[n] = (int8_t)a;
+      g.dj[n] = (int8_t)b;
+    }
+  g.inv_h2 = (float)(1.0 / (pr->nltv_h * pr->nltv_h));
+  g.inv_np = (float)(1.0 / (double)(pr->nltv_patch * pr->nltv_patch));
+  g.lambda1 = (float)pr->lambda1;
+  g.lambda2 = (float)pr->lambda2;
+  g.mu = (float)pr->mu;
+  g.cA = (float)(pr->lambda2 + 0.5 * pr->mu * pr->lambda1 * pr->lambda1);
+  g.thr = (float)(1.0 / pr->mu);
+  g.tau = pr->cg_tol;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return nfail(LFSR_ECUDA, "no usable current device");
+  DeviceSetup ds;
+  const char* err = "no error";
+  const int rc = setup_device(dev, g.zeta, &ds, &err);
+  if (rc != LFSR_OK) return nfail(rc, err);
+
+  OpPlan op{};
+  NlPlan nl{};
+  const int smem_limit = ds.optin - 1024;
+  if (op_plan(g, &op, ds.sm_count, smem_limit) != cudaSuccess)
+    return nfail(LFSR_EUNSUPPORTED, "disparity * angular offset too large for the tile");
+  if (nl_plan(g, &nl, smem_limit) != cudaSuccess)
+    return nfail(LFSR_EUNSUPPORTED, "NLTV window / patch too large");
+  const int grid = op_grid(op, op.n_tiles * g.sk, ds.sm_count);
+  if (grid > kMaxCtas || nl.n_tiles > kMaxCtas)
+    return nfail(LFSR_EINVAL, "launch larger than the no-allocation scratch (4096 CTAs)");
+
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  NoallocScratch* scr = ds.scratch;
+  // counters and totals start at zero on every call
+  if (cudaMemsetAsync(&scr->sc, 0, sizeof(DevScalars), s) != cudaSuccess)
+    return nfail(LFSR_ECUDA, "clearing the scratch scalars failed");
+  NlArgs na{};
+  na.x = d_xw;
+  na.p_old = d_p;
+  na.out = d_q;
+  na.partials = scr->partials[0];
+  na.sc = &scr->sc;
+  if (nl_launch(NL_APPLY, g, nl, na, s) != cudaSuccess)
+    return nfail(LFSR_ECUDA, "NLTV kernel launch failed");
+  OpArgs on{};
+  on.src = d_p;
+  on.disp = d_disparity;
+  on.out = d_q;
+  on.scale = g.cA;
+  on.view0 = 0;
+  on.nviews = g.sk;
+  on.units = op.n_tiles * g.sk;
+  on.partials = scr->partials[1];
+  on.sc = &scr->sc;
+  if (op_launch(OP_NORMAL, g, op, on, grid, s) != cudaSuccess)
+    return nfail(LFSR_ECUDA, "operator kernel launch failed");
+  double pap = 0.0;
+  if (cudaMemcpyAsync(&pap, &scr->sc.pAp, sizeof(double), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return nfail(LFSR_ECUDA, "reading <p, M p> failed");
+  if (pMp) *pMp = pap;
+  return LFSR_OK;
+}

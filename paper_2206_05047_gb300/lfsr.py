@@ -31,7 +31,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblfsr.so
 EXPORTS = ("lfsr_create", "lfsr_solve", "lfsr_destroy", "lfsr_last_error", "lfsr_stats",
            "lfsr_load", "lfsr_iterate", "lfsr_get_x", "lfsr_set_state", "lfsr_get_state",
            "lfsr_apply_A", "lfsr_apply_AT", "lfsr_weights", "lfsr_apply_normal",
-           "lfsr_set_profiling")
+           "lfsr_set_profiling", "lfsr_apply_normal_noalloc")
 
 
 class lfsr_params(C.Structure):
@@ -85,6 +85,8 @@ def load_library(path: str = _LIB_PATH):
         "lfsr_weights": (C.c_int, [H, fp, fp, C.c_int]),
         "lfsr_apply_normal": (C.c_int, [H, fp, fp, fp, C.POINTER(C.c_double), C.c_int]),
         "lfsr_set_profiling": (C.c_int, [H, C.c_int]),
+        "lfsr_apply_normal_noalloc": (C.c_int, [C.POINTER(lfsr_params), fp, fp, fp, fp,
+                                                C.POINTER(C.c_double), C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -232,6 +234,36 @@ def stats(handle) -> dict:
                 dual_change_sq=st.dual_change_sq, cg_pi=st.cg_pi, state_bytes=st.state_bytes,
                 launches=st.launches, kernel_ms=list(st.kernel_ms),
                 kernel_launches=list(st.kernel_launches))
+
+
+def apply_normal_noalloc(U, V, H, W, scale, blur, disparity, d_disparity, xw, p, q,
+                         lambda1=1.0, lambda2=4.0, mu=1.0, nltv_window=5, nltv_patch=3,
+                         nltv_h=0.1, stream=None) -> float:
+    """lfsr_apply_normal_noalloc: q = M p and <p, M p> without a handle and
+    without device allocation.  For callers that cannot allocate device
+    memory (a host framework owns the device heap, a hard memory cap, or no
+    tolerance for the synchronisation cudaMalloc implies).  disparity is
+    the host map (for the shift bound); d_disparity, xw, p, q are CUDA
+    tensors of the current device."""
+    lib = load_library()
+    blur = np.ascontiguousarray(blur, dtype=np.float32)
+    disp = np.ascontiguousarray(disparity, dtype=np.float32)
+    prm = lfsr_params(C.sizeof(lfsr_params), U, V, H, W, scale, blur.shape[0],
+                      blur.ctypes.data_as(C.POINTER(C.c_float)),
+                      disp.ctypes.data_as(C.POINTER(C.c_float)),
+                      lambda1, lambda2, mu, nltv_window, nltv_patch, nltv_h, 0, 0.0, LFSR_FP32)
+    ptrs = [_ptr(t) for t in (d_disparity, xw, p, q)]
+    if any(k != LFSR_MEM_DEVICE for _, k in ptrs):
+        raise TypeError("d_disparity, xw, p and q must be CUDA tensors")
+    if stream is None:
+        import torch
+        s = torch.cuda.current_stream().cuda_stream
+    else:
+        s = stream if isinstance(stream, int) else stream.cuda_stream
+    out = C.c_double(0.0)
+    _check(lib.lfsr_apply_normal_noalloc(C.byref(prm), *[a for a, _ in ptrs], C.byref(out),
+                                         C.c_void_p(s)))
+    return out.value
 
 
 class Solver:
