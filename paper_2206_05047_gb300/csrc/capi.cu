@@ -45,6 +45,8 @@ struct lfsr_handle {
   float* R = nullptr;   // v, then the CG residual r
   float* P[2] = {nullptr, nullptr};
   float* Q = nullptr;
+  float* wt = nullptr;  // stored NLTV edge weights [s_d/2][p] (when supported)
+  bool nlf = false;
   float* io = nullptr;  // staging for host <-> device and layout conversion
   size_t io_floats = 0;
   double* partials = nullptr;
@@ -97,7 +99,7 @@ void free_all(lfsr_handle* h) {
     cudaEventDestroy(ev.b);
   }
   float* bufs[] = {h->disp, h->y, h->x[0], h->x[1], h->wA[0], h->wA[1], h->wS[0],
-                   h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io};
+                   h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt};
   for (float* b : bufs)
     if (b) cudaFree(b);
   if (h->partials) cudaFree(h->partials);
@@ -165,7 +167,9 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
   nbk.wS_new = h->wS[nb];
   nbk.partials = part_slot(h, RED_DW_S);
   nbk.sc = sc;
-  e = timed(h, s, 0, [&] { return nl_launch(NL_BLOCK, g, h->nl, nbk, s); });
+  e = timed(h, s, 0, [&] {
+    return h->nlf ? nlw_launch(1, g, h->nl, nbk, h->wt, s) : nl_launch(NL_BLOCK, g, h->nl, nbk, s);
+  });
   if (e != cudaSuccess) return e;
   // data rows: a = A x - b, z/w-step, v += A^T (l2 a + mu/2 l1 f)
   OpArgs od{};
@@ -200,7 +204,9 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
     na.sc = sc;
     na.use_beta = 1;
     na.check_done = 1;
-    e = timed(h, s, 3, [&] { return nl_launch(NL_APPLY, g, h->nl, na, s); });
+    e = timed(h, s, 3, [&] {
+      return h->nlf ? nla_launch(g, h->nl, na, h->wt, s) : nl_launch(NL_APPLY, g, h->nl, na, s);
+    });
     if (e != cudaSuccess) return e;
     OpArgs on{};
     on.src = h->P[pb];
@@ -378,7 +384,7 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
     delete h;
     return rc;
   }
-  e = op_prepare(g.zeta, optin);
+  e = op_prepare(g, optin);
   if (e == cudaSuccess) e = nl_prepare(optin);
   if (e != cudaSuccess) {
     rc = cuda_fail(nullptr, e, "kernel attributes");
@@ -416,6 +422,8 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   if (e == cudaSuccess) e = dalloc(h, &h->R, p);
   if (e == cudaSuccess) e = dalloc(h, &h->Q, p);
   if (e == cudaSuccess) e = dalloc(h, &h->io, h->io_floats);
+  h->nlf = nlf_supported(g);
+  if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->wt, (size_t)g.sh * p);
   if (e == cudaSuccess) e = dalloc(h, &h->partials, (size_t)RED_NUM * h->max_grid);
   if (e == cudaSuccess) e = dalloc(h, &h->sc, 2);
   if (e == cudaSuccess)
@@ -654,7 +662,12 @@ int lfsr_weights(lfsr_handle* h, const float* x, float* w, int mem) {
   a.x = xs;
   a.out = ws;
   a.sc = h->sc + 1;
-  CK(h, nl_launch(NL_WEIGHTS, h->g, h->nl, a, h->stream), "weights");
+  if (h->nlf) {
+    CK(h, nlw_launch(0, h->g, h->nl, a, h->wt, h->stream), "weights");
+    CK(h, weights_to_canonical(h->g, h->wt, ws, h->stream), "weights layout");
+  } else {
+    CK(h, nl_launch(NL_WEIGHTS, h->g, h->nl, a, h->stream), "weights");
+  }
   if (mem == LFSR_MEM_HOST) CK(h, from_dev(h, w, h->io, h->nS, mem), "download");
   CK(h, cudaStreamSynchronize(h->stream), "synchronize");
   return LFSR_OK;
@@ -682,7 +695,15 @@ int lfsr_apply_normal(lfsr_handle* h, const float* xw, const float* p, float* qo
   na.out = qs;
   na.partials = part_slot(h, RED_NLTV);
   na.sc = sc;
-  CK(h, nl_launch(NL_APPLY, h->g, h->nl, na, h->stream), "normal (NLTV part)");
+  if (h->nlf) {
+    NlArgs wa{};
+    wa.x = xs;
+    wa.sc = sc;
+    CK(h, nlw_launch(0, h->g, h->nl, wa, h->wt, h->stream), "normal (weights)");
+    CK(h, nla_launch(h->g, h->nl, na, h->wt, h->stream), "normal (NLTV part)");
+  } else {
+    CK(h, nl_launch(NL_APPLY, h->g, h->nl, na, h->stream), "normal (NLTV part)");
+  }
   OpArgs on{};
   on.src = ps;
   on.disp = h->disp;

@@ -70,6 +70,7 @@ struct OpPlan {
   size_t smem_bytes;
   int ctas_per_sm;
   int threads;
+  int fast;              // specialised compile-time kernel (op_fast.cu)
 };
 
 struct OpArgs {
@@ -121,7 +122,7 @@ inline cudaError_t set_max_dynamic_smem(K kernel, int smem_optin) {
 }
 
 // Host launchers (stream-ordered, no synchronisation).
-cudaError_t op_prepare(int zeta, int smem_optin);
+cudaError_t op_prepare(const Geom& g, int smem_optin);
 cudaError_t nl_prepare(int smem_optin);
 cudaError_t op_plan(const Geom& g, OpPlan* plan, int sm_count, int smem_limit);
 cudaError_t op_launch(int mode, const Geom& g, const OpPlan& plan, const OpArgs& a,
@@ -129,6 +130,21 @@ cudaError_t op_launch(int mode, const Geom& g, const OpPlan& plan, const OpArgs&
 int op_grid(const OpPlan& plan, int units, int sm_count);
 
 cudaError_t nl_plan(const Geom& g, NlPlan* plan, int smem_limit);
+
+// NLTV with stored edge weights (window radius 1-3, patch radius 0-2).
+bool nlf_supported(const Geom& g);
+cudaError_t nlw_launch(int block, const Geom& g, const NlPlan& P, const NlArgs& a, float* wt,
+                       cudaStream_t s);
+cudaError_t nla_launch(const Geom& g, const NlPlan& P, const NlArgs& a, const float* wt,
+                       cudaStream_t s);
+cudaError_t weights_to_canonical(const Geom& g, const float* wt, float* can, cudaStream_t s);
+
+// Specialised operator kernel for separable kernels of common (zeta, kb).
+bool fast_supported(const Geom& g);
+cudaError_t fast_prepare(const Geom& g, int smem_optin);
+cudaError_t fast_plan(const Geom& g, OpPlan* plan, int smem_limit);
+cudaError_t fast_launch(int mode, const Geom& g, const OpPlan& plan, const OpArgs& a, int grid,
+                        cudaStream_t s);
 cudaError_t nl_launch(int mode, const Geom& g, const NlPlan& plan, const NlArgs& a,
                       cudaStream_t s);
 

@@ -36,7 +36,7 @@ static_assert(sizeof(NoallocScratch) <= LFSR_NOALLOC_SCRATCH_BYTES, "scratch siz
 
 struct DeviceSetup {
   bool ready = false;
-  unsigned zeta_ready = 0;   // bit z: operator kernels of scale z prepared
+  uint64_t geom_ready = 0;   // bit 16 z + kb: operator kernels of (scale, kb) prepared
   NoallocScratch* scratch = nullptr;
   int sm_count = 0;
   int optin = 0;
@@ -47,7 +47,7 @@ DeviceSetup g_dev[kMaxDevices];
 
 // Per-device set-up (first call on a device): device address of the scratch
 // array, SM count, shared-memory limits of the kernels.
-int setup_device(int dev, int zeta, DeviceSetup* out, const char** err) {
+int setup_device(int dev, const Geom& g, DeviceSetup* out, const char** err) {
   std::lock_guard<std::mutex> lock(g_mu);
   DeviceSetup& d = g_dev[dev];
   if (!d.ready) {
@@ -66,12 +66,13 @@ int setup_device(int dev, int zeta, DeviceSetup* out, const char** err) {
     d.scratch = static_cast<NoallocScratch*>(ptr);
     d.ready = true;
   }
-  if (!(d.zeta_ready & (1u << zeta))) {
-    if (op_prepare(zeta, d.optin) != cudaSuccess) {
+  const uint64_t bit = 1ull << (16 * (g.zeta - 1) + g.kb);
+  if (!(d.geom_ready & bit)) {
+    if (op_prepare(g, d.optin) != cudaSuccess) {
       *err = "kernel attributes failed";
       return LFSR_ECUDA;
     }
-    d.zeta_ready |= 1u << zeta;
+    d.geom_ready |= bit;
   }
   *out = d;
   return LFSR_OK;
@@ -177,7 +178,7 @@ extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_d
     return nfail(LFSR_ECUDA, "no usable current device");
   DeviceSetup ds;
   const char* err = "no error";
-  const int rc = setup_device(dev, g.zeta, &ds, &err);
+  const int rc = setup_device(dev, g, &ds, &err);
   if (rc != LFSR_OK) return nfail(rc, err);
 
   OpPlan op{};

@@ -336,16 +336,18 @@ static cudaError_t op_prepare_z(int optin) {
   return e;
 }
 
-// Raises the dynamic shared-memory limit of every operator kernel of this
-// scale (the current device; called outside any stream capture).
-cudaError_t op_prepare(int zeta, int optin) {
-  switch (zeta) {
-    case 1: return op_prepare_z<1>(optin);
-    case 2: return op_prepare_z<2>(optin);
-    case 3: return op_prepare_z<3>(optin);
-    case 4: return op_prepare_z<4>(optin);
+// Raises the dynamic shared-memory limit of every operator kernel this
+// geometry can use (the current device; called outside any stream capture).
+cudaError_t op_prepare(const Geom& g, int optin) {
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (g.zeta) {
+    case 1: e = op_prepare_z<1>(optin); break;
+    case 2: e = op_prepare_z<2>(optin); break;
+    case 3: e = op_prepare_z<3>(optin); break;
+    case 4: e = op_prepare_z<4>(optin); break;
   }
-  return cudaErrorInvalidValue;
+  if (e == cudaSuccess && fast_supported(g)) e = fast_prepare(g, optin);
+  return e;
 }
 
 template <int MODE>
@@ -363,6 +365,7 @@ static cudaError_t op_launch_m(const Geom& g, const OpPlan& P, const OpArgs& a, 
 cudaError_t op_launch(int mode, const Geom& g, const OpPlan& P, const OpArgs& a, int grid,
                       cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
+  if (P.fast) return fast_launch(mode, g, P, a, grid, s);
   switch (mode) {
     case OP_NORMAL: return op_launch_m<OP_NORMAL>(g, P, a, grid, s);
     case OP_DATA: return op_launch_m<OP_DATA>(g, P, a, grid, s);
@@ -386,6 +389,9 @@ static int op_occupancy(size_t smem) {
 cudaError_t op_plan(const Geom& g, OpPlan* P, int sm_count, int smem_limit) {
   (void)sm_count;
   const size_t limit = (size_t)smem_limit;
+  P->fast = 0;
+  if (fast_supported(g) && fast_plan(g, P, smem_limit) == cudaSuccess) return cudaSuccess;
+  P->fast = 0;
   static const int shapes[][2] = {{64, 64}, {32, 64}, {32, 32}, {16, 32}, {16, 16}, {8, 16}, {8, 8}};
   for (auto& sh : shapes) {
     if (op_layout(g, sh[0], sh[1], P) <= limit) {
