@@ -46,6 +46,7 @@ struct lfsr_handle {
   float* P[2] = {nullptr, nullptr};
   float* Q = nullptr;
   float* wt = nullptr;  // stored NLTV edge weights [s_d/2][p] (when supported)
+  float* cb = nullptr;  // per-edge divergence terms of the z/w-step [s_d/2][p]
   bool nlf = false;
   float* io = nullptr;  // staging for host <-> device and layout conversion
   size_t io_floats = 0;
@@ -99,7 +100,7 @@ void free_all(lfsr_handle* h) {
     cudaEventDestroy(ev.b);
   }
   float* bufs[] = {h->disp, h->y, h->x[0], h->x[1], h->wA[0], h->wA[1], h->wS[0],
-                   h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt};
+                   h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt, h->cb};
   for (float* b : bufs)
     if (b) cudaFree(b);
   if (h->partials) cudaFree(h->partials);
@@ -168,7 +169,8 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
   nbk.partials = part_slot(h, RED_DW_S);
   nbk.sc = sc;
   e = timed(h, s, 0, [&] {
-    return h->nlf ? nlw_launch(1, g, h->nl, nbk, h->wt, s) : nl_launch(NL_BLOCK, g, h->nl, nbk, s);
+    return h->nlf ? nlw2_launch(1, g, h->nl, nbk, h->wt, h->cb, s)
+                  : nl_launch(NL_BLOCK, g, h->nl, nbk, s);
   });
   if (e != cudaSuccess) return e;
   // data rows: a = A x - b, z/w-step, v += A^T (l2 a + mu/2 l1 f)
@@ -189,7 +191,10 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   // x-step (Algorithm 2): r = -v, x' = x, pi = <r, r>
   e = timed(h, s, 2, [&] {
-    return cg_init_launch(g, h->R, h->x[b], h->x[nb], part_slot(h, RED_PI), sc, h->grid_vec, s);
+    return h->nlf ? cg_init_nltv_launch(g, h->R, h->cb, h->x[b], h->x[nb], part_slot(h, RED_PI),
+                                        sc, h->grid_vec, s)
+                  : cg_init_launch(g, h->R, h->x[b], h->x[nb], part_slot(h, RED_PI), sc,
+                                   h->grid_vec, s);
   });
   if (e != cudaSuccess) return e;
   for (int k = 0; k < h->prm.cg_iters; ++k) {
@@ -205,7 +210,7 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
     na.use_beta = 1;
     na.check_done = 1;
     e = timed(h, s, 3, [&] {
-      return h->nlf ? nla_launch(g, h->nl, na, h->wt, s) : nl_launch(NL_APPLY, g, h->nl, na, s);
+      return h->nlf ? nla2_launch(g, h->nl, na, h->wt, s) : nl_launch(NL_APPLY, g, h->nl, na, s);
     });
     if (e != cudaSuccess) return e;
     OpArgs on{};
@@ -424,6 +429,7 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   if (e == cudaSuccess) e = dalloc(h, &h->io, h->io_floats);
   h->nlf = nlf_supported(g);
   if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->wt, (size_t)g.sh * p);
+  if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->cb, (size_t)g.sh * p);
   if (e == cudaSuccess) e = dalloc(h, &h->partials, (size_t)RED_NUM * h->max_grid);
   if (e == cudaSuccess) e = dalloc(h, &h->sc, 2);
   if (e == cudaSuccess)
@@ -663,7 +669,7 @@ int lfsr_weights(lfsr_handle* h, const float* x, float* w, int mem) {
   a.out = ws;
   a.sc = h->sc + 1;
   if (h->nlf) {
-    CK(h, nlw_launch(0, h->g, h->nl, a, h->wt, h->stream), "weights");
+    CK(h, nlw2_launch(0, h->g, h->nl, a, h->wt, nullptr, h->stream), "weights");
     CK(h, weights_to_canonical(h->g, h->wt, ws, h->stream), "weights layout");
   } else {
     CK(h, nl_launch(NL_WEIGHTS, h->g, h->nl, a, h->stream), "weights");
@@ -699,8 +705,8 @@ int lfsr_apply_normal(lfsr_handle* h, const float* xw, const float* p, float* qo
     NlArgs wa{};
     wa.x = xs;
     wa.sc = sc;
-    CK(h, nlw_launch(0, h->g, h->nl, wa, h->wt, h->stream), "normal (weights)");
-    CK(h, nla_launch(h->g, h->nl, na, h->wt, h->stream), "normal (NLTV part)");
+    CK(h, nlw2_launch(0, h->g, h->nl, wa, h->wt, nullptr, h->stream), "normal (weights)");
+    CK(h, nla2_launch(h->g, h->nl, na, h->wt, h->stream), "normal (NLTV part)");
   } else {
     CK(h, nl_launch(NL_APPLY, h->g, h->nl, na, h->stream), "normal (NLTV part)");
   }

@@ -133,11 +133,14 @@ cudaError_t nl_plan(const Geom& g, NlPlan* plan, int smem_limit);
 
 // NLTV with stored edge weights (window radius 1-3, patch radius 0-2).
 bool nlf_supported(const Geom& g);
-cudaError_t nlw_launch(int block, const Geom& g, const NlPlan& P, const NlArgs& a, float* wt,
-                       cudaStream_t s);
-cudaError_t nla_launch(const Geom& g, const NlPlan& P, const NlArgs& a, const float* wt,
-                       cudaStream_t s);
 cudaError_t weights_to_canonical(const Geom& g, const float* wt, float* can, cudaStream_t s);
+cudaError_t nlw2_launch(int block, const Geom& g, const NlPlan& P, const NlArgs& a, float* wt,
+                        float* cb, cudaStream_t s);
+cudaError_t nla2_launch(const Geom& g, const NlPlan& P, const NlArgs& a, const float* wt,
+                        cudaStream_t s);
+cudaError_t cg_init_nltv_launch(const Geom& g, float* rv, const float* cb, const float* x,
+                                float* x_next, double* partials, DevScalars* sc, int grid,
+                                cudaStream_t s);
 
 // Specialised operator kernel for separable kernels of common (zeta, kb).
 bool fast_supported(const Geom& g);

@@ -23,10 +23,26 @@
 namespace lfsr {
 
 constexpr int FT_THREADS = 512;
+constexpr int FT_VB = 2;   // views processed together per pass through the stages
+
+// Outputs per task m in [4, 8] that needs the fewest 512-thread passes for
+// `rows` x ceil(n / m) tasks (ties: the smaller m, i.e. fewer registers).
+constexpr int pick_block(int rows, int n) {
+  int best = 4, best_passes = 1 << 30;
+  for (int m = 4; m <= 8; ++m) {
+    const int passes = (rows * ((n + m - 1) / m) + FT_THREADS - 1) / FT_THREADS;
+    if (passes < best_passes) {
+      best_passes = passes;
+      best = m;
+    }
+  }
+  return best;
+}
 
 template <int Z, int KB>
 struct FastShape {
   static constexpr int T = 64;                               // tile side (HR px)
+  static constexpr int VB = FT_VB;
   static constexpr int R = (KB - 1) / 2;                     // blur radius
   static constexpr int NL = (T + 2 * R + Z - 1) / Z;         // LR rows/cols touching a tile
   static constexpr int NE = Z * (NL - 1) + 2 * R + 1;        // warp samples per row/col
@@ -34,30 +50,38 @@ struct FastShape {
   static constexpr int NG = NL + 2 * MG;                     // LR grid with margins
   static constexpr int NGp = NG | 1;                         // its (odd) pitch
   // stage 2 (horizontal forward): MB2 LR columns per task
-  static constexpr int MB2 = (NL % 5 == 0) ? 5 : 4;
+  static constexpr int MB2 = pick_block(VB * NE, NL);
   static constexpr int NB2 = (NL + MB2 - 1) / MB2;
   static constexpr int W2 = Z * (MB2 - 1) + KB;              // window length
   static constexpr int NEp = ((Z * (NB2 * MB2 - 1) + KB) > NE ? (Z * (NB2 * MB2 - 1) + KB) : NE) | 1;
   // stage 3 (vertical forward): MB3 LR rows per task
-  static constexpr int MB3 = MB2;
-  static constexpr int NB3 = NB2;
-  static constexpr int W3 = W2;
+  static constexpr int MB3 = pick_block(VB * NL, NL);
+  static constexpr int NB3 = (NL + MB3 - 1) / MB3;
+  static constexpr int W3 = Z * (MB3 - 1) + KB;
   static constexpr int NEr = (Z * (NB3 * MB3 - 1) + KB) > NE ? (Z * (NB3 * MB3 - 1) + KB) : NE;
+  static constexpr int IT3 = (VB * NL * NB3 + FT_THREADS - 1) / FT_THREADS;
   static constexpr int NHp = NL | 1;                         // pitch of the forward H buffer
-  // stage 5 (adjoint rows): m = floor(hi / Z) over the tile, MB5 per task
-  static constexpr int NM = (T - 1) / Z + 2;                 // max m values per tile
-  static constexpr int MB5 = 4;
+  // stage 4 (adjoint rows): m = floor(hi / Z) over the tile, MB5 per task;
+  // tiles start at multiples of T, so when Z divides T every tile holds
+  // exactly T / Z values of m
+  static constexpr bool ALIGNED = (T % Z) == 0;
+  static constexpr int NM = ALIGNED ? T / Z : (T - 1) / Z + 2;  // m values per tile
+  static constexpr int MB5 = pick_block(VB * NG, NM);
   static constexpr int NB5 = (NM + MB5 - 1) / MB5;
   static constexpr int DMIN = -(R / Z) - 1;                  // safe delta bounds (all phases)
   static constexpr int DMAX = (Z - 1 + R) / Z;
   static constexpr int W5 = MB5 + DMAX - DMIN;
   static constexpr int NVp = NG | 1;                         // pitch of the adjoint V buffer
-  // stage 6 (adjoint columns + scatter): n = floor(hj / Z), MB6 per task
+  // stage 5 (adjoint columns + scatter): n = floor(hj / Z), MB6 per task
   static constexpr int NN = NM;
-  static constexpr int MB6 = (Z == 1) ? 8 : 4;
+  static constexpr int MB6 = pick_block(T, NN);
   static constexpr int NB6 = (NN + MB6 - 1) / MB6;
   static constexpr int W6 = MB6 + DMAX - DMIN;
-  static constexpr int HV = (NEr * NHp > T * NVp) ? NEr * NHp : T * NVp;  // shared H/V buffer
+  static constexpr int HV = (NEr * NHp > T * NVp) ? NEr * NHp : T * NVp;  // H/V buffer per view
+  static constexpr int GS = NG * NGp;                        // LR grid per view
+  static constexpr int WS = NE * NEp;                        // sample buffer per view
+  static constexpr int NS1 = NE * NE;                        // warp samples per view
+  static constexpr int IT1 = (NS1 + FT_THREADS - 1) / FT_THREADS;
 };
 
 __device__ __forceinline__ void split_shift(float t, int& ip, float& fr) {
@@ -72,46 +96,58 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
 k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
   using SH = FastShape<Z, KB>;
   constexpr int T = SH::T, R = SH::R, NL = SH::NL, NE = SH::NE, MG = SH::MG, NGp = SH::NGp;
-  constexpr int NEp = SH::NEp, NHp = SH::NHp, NVp = SH::NVp;
+  constexpr int NEp = SH::NEp, NHp = SH::NHp, NVp = SH::NVp, VB = SH::VB;
   extern __shared__ __align__(16) float smem[];
   if (a.check_done && a.sc->cg_done) return;
   float* sP = smem + P.off_P;   // source, (NE + 2S + 1) rows, pitch P.NPc
   float* sO = smem + P.off_W;   // disparity on the sample region, NE x NEp
-  float* sW = sO + NE * NEp;    // warped samples, NE x NEp
-  float* sHV = smem + P.off_H;  // forward H (NEr x NHp) / adjoint V (T x NVp)
-  float* sG = smem + P.off_G;   // LR grid with zero margins, NG x NGp
+  float* sW = sO + SH::WS;      // warped samples, VB x NE x NEp
+  float* sHV = smem + P.off_H;  // forward H (NEr x NHp) / adjoint V (T x NVp), VB copies
+  float* sG = smem + P.off_G;   // LR grid with zero margins, VB x NG x NGp
   float* sA = smem + P.off_A;   // scatter accumulator, NAr x NAc (pitch odd)
   const int tid = threadIdx.x;
   const int S = g.S;
   const float Sf = (float)S;
   const int NPc = P.NPc, NAc = P.NAc;
-  const int u_begin = (int)((long long)blockIdx.x * a.units / gridDim.x);
-  const int u_end = (int)((long long)(blockIdx.x + 1) * a.units / gridDim.x);
+  const int nvb = (a.nviews + VB - 1) / VB;
+  const int units = P.n_tiles * nvb;
+  const int u_begin = (int)((long long)blockIdx.x * units / gridDim.x);
+  const int u_end = (int)((long long)(blockIdx.x + 1) * units / gridDim.x);
   const size_t q_lr = (size_t)g.H * g.W;
   double part = 0.0;
 
+  static_assert(VB == 2, "the sample and scatter stages handle view pairs");
   int cur_tile = -1;
   int i0 = 0, j0 = 0, lr_lo = 0, lr_n = 0, lc_lo = 0, lc_n = 0, e_r0 = 0, e_c0 = 0;
   int NAr_t = 0, NAc_t = 0;
+  // this thread's warp-sample positions (fixed for all views of a tile):
+  // staged-source index of the (0, 0) tap before the shift, and disparity
+  int s1_base[SH::IT1];
+  float s1_om[SH::IT1];
 
-  for (int t = tid; t < SH::NG * NGp; t += FT_THREADS) sG[t] = 0.f;
+  for (int t = tid; t < VB * SH::GS; t += FT_THREADS) sG[t] = 0.f;
   if (MODE != OP_FWD)
     for (int t = tid; t < P.NAr * NAc; t += FT_THREADS) sA[t] = 0.f;
 
   auto flush = [&]() {
-    for (int t = tid; t < NAr_t * NAc_t; t += FT_THREADS) {
-      const int ar = t / NAc_t, ac = t - ar * NAc_t;
-      const int hi = i0 - S + ar, hj = j0 - S + ac;
-      const float v = sA[ar * NAc + ac];
-      if (hi >= 0 && hi < g.Hh && hj >= 0 && hj < g.Wh && v != 0.f)
-        atomicAdd(a.out + (size_t)hi * g.Wh + hj, a.scale * v);
-      sA[ar * NAc + ac] = 0.f;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int ar = warp; ar < NAr_t; ar += FT_THREADS / 32) {
+      const int hi = i0 - S + ar;
+      const bool row_in = hi >= 0 && hi < g.Hh;
+      for (int ac = lane; ac < NAc_t; ac += 32) {
+        const int hj = j0 - S + ac;
+        const float v = sA[ar * NAc + ac];
+        if (row_in && hj >= 0 && hj < g.Wh && v != 0.f)
+          atomicAdd(a.out + (size_t)hi * g.Wh + hj, a.scale * v);
+        sA[ar * NAc + ac] = 0.f;
+      }
     }
   };
 
   for (int u = u_begin; u < u_end; ++u) {
-    const int tile = u / a.nviews;
-    const int k = a.view0 + (u - tile * a.nviews);
+    const int tile = u / nvb;
+    const int kbase = a.view0 + VB * (u - tile * nvb);
+    const int nv = min(VB, a.view0 + a.nviews - kbase);   // views of this unit
     if (tile != cur_tile) {
       __syncthreads();
       if (cur_tile >= 0 && MODE != OP_FWD) {
@@ -131,46 +167,131 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
       e_c0 = Z * lc_lo - R;
       NAr_t = TRr + 2 * S + 1;
       NAc_t = TRc + 2 * S + 1;
-      // stage the source (zero outside the image) and the disparity
-      if (MODE != OP_ADJ) {
-        const int np = NE + 2 * S + 1;
-        for (int t = tid; t < np * np; t += FT_THREADS) {
-          const int pr = t / np, pc = t - pr * np;
-          const int hi = e_r0 - S + pr, hj = e_c0 - S + pc;
-          sP[pr * NPc + pc] = (hi >= 0 && hi < g.Hh && hj >= 0 && hj < g.Wh)
-                                  ? __ldg(a.src + (size_t)hi * g.Wh + hj) : 0.f;
+      // stage the source (zero outside the image) and the disparity: one
+      // warp per row, lanes along the row, loads batched before the stores
+      {
+        const int warp = tid >> 5, lane = tid & 31;
+        constexpr int NWARP = FT_THREADS / 32;
+        if (MODE != OP_ADJ) {
+          const int np = NE + 2 * S + 1;
+          for (int pr = warp; pr < np; pr += NWARP) {
+            const int hi = e_r0 - S + pr;
+            const bool row_in = hi >= 0 && hi < g.Hh;
+            const float* src_row = a.src + (size_t)(row_in ? hi : 0) * g.Wh;
+            for (int cb = 0; cb < np; cb += 128) {
+              float vals[4];
+#pragma unroll
+              for (int c4 = 0; c4 < 4; ++c4) {
+                const int pc = cb + lane + 32 * c4, hj = e_c0 - S + pc;
+                vals[c4] = (pc < np && row_in && hj >= 0 && hj < g.Wh) ? __ldg(src_row + hj) : 0.f;
+              }
+#pragma unroll
+              for (int c4 = 0; c4 < 4; ++c4) {
+                const int pc = cb + lane + 32 * c4;
+                if (pc < np) sP[pr * NPc + pc] = vals[c4];
+              }
+            }
+          }
+        }
+        for (int er = warp; er < NE; er += NWARP) {
+          const int hi = e_r0 + er;
+          const bool row_in = hi >= 0 && hi < g.Hh;
+          const float* d_row = a.disp + (size_t)(row_in ? hi : 0) * g.Wh;
+          float vals[(NE + 31) / 32];
+#pragma unroll
+          for (int c4 = 0; c4 < (NE + 31) / 32; ++c4) {
+            const int ec = lane + 32 * c4, hj = e_c0 + ec;
+            vals[c4] = (ec < NE && row_in && hj >= 0 && hj < g.Wh) ? __ldg(d_row + hj) : 0.f;
+          }
+#pragma unroll
+          for (int c4 = 0; c4 < (NE + 31) / 32; ++c4) {
+            const int ec = lane + 32 * c4;
+            if (ec < NE) sO[er * NEp + ec] = vals[c4];
+          }
         }
       }
-      for (int t = tid; t < NE * NE; t += FT_THREADS) {
-        const int er = t / NE, ec = t - er * NE;
-        const int hi = e_r0 + er, hj = e_c0 + ec;
-        sO[er * NEp + ec] = (hi >= 0 && hi < g.Hh && hj >= 0 && hj < g.Wh)
-                                ? __ldg(a.disp + (size_t)hi * g.Wh + hj) : 0.f;
-      }
       __syncthreads();
+      if (MODE != OP_ADJ) {
+#pragma unroll
+        for (int it = 0; it < SH::IT1; ++it) {
+          const int t = tid + it * FT_THREADS;
+          const int er = t / NE, ec = t - er * NE;
+          const bool ok = t < SH::NS1;
+          s1_base[it] = ok ? er * NPc + ec : 0;
+          s1_om[it] = ok ? sO[er * NEp + ec] : 0.f;
+        }
+      }
     }
-    const float tu = g.tu[k], tv = g.tv[k];
+
+    // data block: fetch the views' LR values and duals now, so the loads are
+    // in flight during the warp and blur stages
+    float pre_y[SH::IT3][SH::MB3], pre_w[SH::IT3][SH::MB3];
+    if (MODE == OP_DATA) {
+#pragma unroll
+      for (int it = 0; it < SH::IT3; ++it) {
+        const int t = tid + it * FT_THREADS;
+        const int v = t / (NL * SH::NB3), r3 = t - v * (NL * SH::NB3);
+        const int lc = r3 % NL, rb = r3 / NL;
+#pragma unroll
+        for (int o = 0; o < SH::MB3; ++o) {
+          const int lr = rb * SH::MB3 + o;
+          pre_y[it][o] = 0.f;
+          pre_w[it][o] = 0.f;
+          if (v < nv && lr < lr_n && lc < lc_n) {
+            const size_t gi = (size_t)(kbase + v) * q_lr + (size_t)(lr_lo + lr) * g.W + (lc_lo + lc);
+            pre_y[it][o] = __ldg(a.y + gi);
+            pre_w[it][o] = __ldg(a.wA_old + gi);
+          }
+        }
+      }
+    }
 
     if (MODE != OP_ADJ) {
       // 1. warped samples: outside the image the disparity is 0 and the
-      //    staged source is 0, so the sample is 0 without a branch
-      for (int t = tid; t < NE * NE; t += FT_THREADS) {
-        const int er = t / NE, ec = t - er * NE;
-        const float om = sO[er * NEp + ec];
-        int iy, ix;
-        float fy, fx;
-        split_shift(fmaf(tv, om, Sf), iy, fy);
-        split_shift(fmaf(tu, om, Sf), ix, fx);
-        const float* q = sP + (er + iy) * NPc + (ec + ix);
-        const float top = fmaf(fx, q[1] - q[0], q[0]);
-        const float bot = fmaf(fx, q[NPc + 1] - q[NPc], q[NPc]);
-        sW[er * NEp + ec] = fmaf(fy, bot - top, top);
+      //    staged source is 0, so the sample is 0 without a branch.  The
+      //    two views of the pass share the disparity read and, when they
+      //    lie in the same row of the angular grid, the vertical split.
+      {
+        const float tu0 = g.tu[kbase], tv0 = g.tv[kbase];
+        const int k1 = kbase + (nv > 1 ? 1 : 0);
+        const float tu1 = g.tu[k1], tv1 = g.tv[k1];
+        const bool two = nv > 1;
+        const bool same_row = tv1 == tv0;
+#pragma unroll
+        for (int it = 0; it < SH::IT1; ++it) {
+          const int t = tid + it * FT_THREADS;
+          if (it < SH::IT1 - 1 || t < SH::NS1) {
+            const int si = (NEp == NE) ? t : (t / NE) * NEp + (t % NE);
+            const float om = s1_om[it];
+            const float* qb = sP + s1_base[it];
+            int iy, ix;
+            float fy, fx;
+            split_shift(fmaf(tv0, om, Sf), iy, fy);
+            split_shift(fmaf(tu0, om, Sf), ix, fx);
+            {
+              const float* q = qb + iy * NPc + ix;
+              const float top = fmaf(fx, q[1] - q[0], q[0]);
+              const float bot = fmaf(fx, q[NPc + 1] - q[NPc], q[NPc]);
+              sW[si] = fmaf(fy, bot - top, top);
+            }
+            if (two) {
+              if (!same_row) split_shift(fmaf(tv1, om, Sf), iy, fy);
+              split_shift(fmaf(tu1, om, Sf), ix, fx);
+              const float* q = qb + iy * NPc + ix;
+              const float top = fmaf(fx, q[1] - q[0], q[0]);
+              const float bot = fmaf(fx, q[NPc + 1] - q[NPc], q[NPc]);
+              sW[SH::WS + si] = fmaf(fy, bot - top, top);
+            }
+          }
+        }
       }
       __syncthreads();
       // 2. horizontal blur at decimated columns; lanes along rows
-      for (int t = tid; t < NE * SH::NB2; t += FT_THREADS) {
-        const int er = t % NE, cb = t / NE;
-        const float* w = sW + er * NEp + Z * SH::MB2 * cb;
+      for (int t = tid; t < VB * NE * SH::NB2; t += FT_THREADS) {
+        const int v = t / (NE * SH::NB2), r2 = t - v * (NE * SH::NB2);
+        if (v >= nv) continue;
+        const int er = r2 % NE, cb = r2 / NE;
+        const float* w = sW + v * SH::WS + er * NEp + Z * SH::MB2 * cb;
         float win[SH::W2];
 #pragma unroll
         for (int c = 0; c < SH::W2; ++c) win[c] = w[c];
@@ -180,16 +301,21 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
 #pragma unroll
           for (int b = 0; b < KB; ++b) acc = fmaf(g.kh[b], win[Z * o + b], acc);
           const int lc = cb * SH::MB2 + o;
-          if (lc < NL) sHV[er * NHp + lc] = acc;
+          if (lc < NL) sHV[v * SH::HV + er * NHp + lc] = acc;
         }
       }
       __syncthreads();
       // 3. vertical blur at decimated rows, then the per-LR-pixel step;
       //    lanes along LR columns
       float psum = 0.f;
-      for (int t = tid; t < NL * SH::NB3; t += FT_THREADS) {
-        const int lc = t % NL, rb = t / NL;
-        const float* hcol = sHV + (Z * SH::MB3 * rb) * NHp + lc;
+#pragma unroll
+      for (int it = 0; it < SH::IT3; ++it) {
+        const int t = tid + it * FT_THREADS;
+        const int v = t / (NL * SH::NB3), r3 = t - v * (NL * SH::NB3);
+        if (v >= nv) break;
+        const int lc = r3 % NL, rb = r3 / NL;
+        const int k = kbase + v;
+        const float* hcol = sHV + v * SH::HV + (Z * SH::MB3 * rb) * NHp + lc;
         float win[SH::W3];
 #pragma unroll
         for (int c = 0; c < SH::W3; ++c) win[c] = hcol[c * NHp];
@@ -210,7 +336,7 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
               if (owned) psum = fmaf(acc, acc, psum);
             } else if (MODE == OP_DATA) {
               const size_t gi = (size_t)k * q_lr + (size_t)gr * g.W + gc;
-              const float yv = __ldg(a.y + gi), wa = __ldg(a.wA_old + gi);
+              const float yv = pre_y[it][o], wa = pre_w[it][o];
               const float res = acc - yv;
               const float uu = fmaf(g.lambda1, res, wa);
               const float wn = fminf(fmaxf(uu, -g.thr), g.thr);
@@ -225,17 +351,19 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
               if (owned) a.out[(size_t)k * q_lr + (size_t)gr * g.W + gc] = acc;
             }
           }
-          sG[(lr + MG) * NGp + (lc + MG)] = h;
+          sG[v * SH::GS + (lr + MG) * NGp + (lc + MG)] = h;
         }
       }
       part += (double)psum;
     } else {
-      for (int t = tid; t < NL * NL; t += FT_THREADS) {
-        const int lr = t / NL, lc = t - lr * NL;
-        float v = 0.f;
+      for (int t = tid; t < VB * NL * NL; t += FT_THREADS) {
+        const int v = t / (NL * NL), r0 = t - v * (NL * NL);
+        if (v >= nv) continue;
+        const int lr = r0 / NL, lc = r0 - lr * NL;
+        float val = 0.f;
         if (lr < lr_n && lc < lc_n)
-          v = __ldg(a.src + (size_t)k * q_lr + (size_t)(lr_lo + lr) * g.W + (lc_lo + lc));
-        sG[(lr + MG) * NGp + (lc + MG)] = v;
+          val = __ldg(a.src + (size_t)(kbase + v) * q_lr + (size_t)(lr_lo + lr) * g.W + (lc_lo + lc));
+        sG[v * SH::GS + (lr + MG) * NGp + (lc + MG)] = val;
       }
     }
     __syncthreads();
@@ -244,16 +372,19 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
     // 4. adjoint blur, rows (polyphase): V(hi, c) for hi in the tile and
     //    every column c of the LR grid (margins included, they are zero)
     const int m_lo = floor_div(i0, Z);
-    for (int t = tid; t < SH::NG * SH::NB5; t += FT_THREADS) {
-      const int c = t % SH::NG, mb = t / SH::NG;
+    for (int t = tid; t < VB * SH::NG * SH::NB5; t += FT_THREADS) {
+      const int v = t / (SH::NG * SH::NB5), r4 = t - v * (SH::NG * SH::NB5);
+      if (v >= nv) continue;
+      const int c = r4 % SH::NG, mb = r4 / SH::NG;
       const int m0 = m_lo + mb * SH::MB5;
+      const float* gv = sG + v * SH::GS;
       // window rows l = m0 + DMIN .. m0 + MB5 - 1 + DMAX (grid row l - lr_lo + MG)
       const int r0 = m0 + SH::DMIN - lr_lo + MG;
       float win[SH::W5];
 #pragma unroll
       for (int w = 0; w < SH::W5; ++w) {
         const int rr = r0 + w;
-        win[w] = (rr >= 0 && rr < SH::NG) ? sG[rr * NGp + c] : 0.f;
+        win[w] = (rr >= 0 && rr < SH::NG) ? gv[rr * NGp + c] : 0.f;
       }
 #pragma unroll
       for (int o = 0; o < SH::MB5; ++o) {
@@ -267,51 +398,110 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
             if (ai >= 0 && ai <= 2 * R) acc = fmaf(g.kv[ai], win[o + d - SH::DMIN], acc);
           }
           const int ri = hi - i0;
-          if (ri >= 0 && ri < T) sHV[ri * NVp + c] = acc;
+          if (ri >= 0 && ri < T) sHV[v * SH::HV + ri * NVp + c] = acc;
         }
       }
     }
     __syncthreads();
     // 5. adjoint blur, columns (polyphase), then the bilinear scatter W_k^T;
-    //    lanes along rows
+    //    lanes along rows; one task covers the same pixels in both views
     const int n_lo = floor_div(j0, Z);
     const int TRr = min(T, g.Hh - i0);
+    const bool full_cols = j0 + T <= g.Wh;
+    const float tu0 = g.tu[kbase], tv0 = g.tv[kbase];
+    const int k1 = kbase + (nv > 1 ? 1 : 0);
+    const float tu1 = g.tu[k1], tv1 = g.tv[k1];
+    const bool two = nv > 1;
+    const bool same_row = tv1 == tv0;
     for (int t = tid; t < T * SH::NB6; t += FT_THREADS) {
       const int i = t % T, nb = t / T;
       if (i >= TRr) continue;
       const int n0 = n_lo + nb * SH::MB6;
-      const int c0 = n0 + SH::DMIN - lc_lo + MG;
-      float win[SH::W6];
+      const int c0 = n0 + SH::DMIN - lc_lo + MG;     // in [0, NG - W6] for every tile
+      float win0[SH::W6], win1[SH::W6];
+      {
+        const float* v0 = sHV + i * NVp + c0;
+        const float* v1 = v0 + SH::HV;
 #pragma unroll
-      for (int w = 0; w < SH::W6; ++w) {
-        const int cc = c0 + w;
-        win[w] = (cc >= 0 && cc < SH::NG) ? sHV[i * NVp + cc] : 0.f;
+        for (int w = 0; w < SH::W6; ++w) {
+          win0[w] = v0[w];
+          win1[w] = two ? v1[w] : 0.f;
+        }
       }
       const int hi = i0 + i;
-#pragma unroll
-      for (int o = 0; o < SH::MB6; ++o) {
-#pragma unroll
-        for (int ph = 0; ph < Z; ++ph) {
-          const int hj = Z * (n0 + o) + ph;
-          if (hj < j0 || hj >= j0 + T || hj >= g.Wh) continue;
-          float tv_ = 0.f;
-#pragma unroll
-          for (int d = SH::DMIN; d <= SH::DMAX; ++d) {
-            const int ai = ph + R - Z * d;
-            if (ai >= 0 && ai <= 2 * R) tv_ = fmaf(g.kh[ai], win[o + d - SH::DMIN], tv_);
-          }
-          const float om = sO[(hi - e_r0) * NEp + (hj - e_c0)];
-          int iy, ix;
-          float fy, fx;
-          split_shift(fmaf(tv, om, Sf), iy, fy);
-          split_shift(fmaf(tu, om, Sf), ix, fx);
-          float* q = sA + (i + iy) * NAc + (hj - j0 + ix);
-          const float ty = fy * tv_, by = tv_ - ty;
-          atomicAdd(q, by - fx * by);
-          atomicAdd(q + 1, fx * by);
-          atomicAdd(q + NAc, ty - fx * ty);
-          atomicAdd(q + NAc + 1, fx * ty);
+      const float* orow = sO + (hi - e_r0) * NEp - e_c0;
+      // taps of consecutive pixels of this row segment: when a pixel's
+      // integer shift equals its left neighbour's, its left taps coincide
+      // with the neighbour's right taps and are added before one atomic
+      bool pend0 = false, pend1 = false;
+      int pr0 = 0, pc0 = 0, pr1 = 0, pc1 = 0;
+      float pt0 = 0.f, pb0 = 0.f, pt1 = 0.f, pb1 = 0.f;
+      auto scatter = [&](float tval, int r, int c, float fy, float fx, bool& pend, int& pr_,
+                         int& pc_, float& pt, float& pb) {
+        const float ty = fy * tval, by = tval - ty;
+        float tl = by - fx * by, bl = ty - fx * ty;
+        const float tr = fx * by, br = fx * ty;
+        const bool merged = pend && pr_ == r && pc_ == c;
+        if (merged) {
+          tl += pt;
+          bl += pb;
+        } else if (pend) {
+          atomicAdd(sA + pr_ * NAc + pc_, pt);
+          atomicAdd(sA + (pr_ + 1) * NAc + pc_, pb);
         }
+        atomicAdd(sA + r * NAc + c, tl);
+        atomicAdd(sA + (r + 1) * NAc + c, bl);
+        pend = true;
+        pr_ = r;
+        pc_ = c + 1;
+        pt = tr;
+        pb = br;
+      };
+      auto pixel = [&](int o, int ph) {
+        const int hj = Z * (n0 + o) + ph;
+        float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+        for (int d = SH::DMIN; d <= SH::DMAX; ++d) {
+          const int ai = ph + R - Z * d;
+          if (ai >= 0 && ai <= 2 * R) {
+            t0 = fmaf(g.kh[ai], win0[o + d - SH::DMIN], t0);
+            t1 = fmaf(g.kh[ai], win1[o + d - SH::DMIN], t1);
+          }
+        }
+        const float om = orow[hj];
+        const int cc = hj - j0;
+        int iy, ix;
+        float fy, fx;
+        split_shift(fmaf(tv0, om, Sf), iy, fy);
+        split_shift(fmaf(tu0, om, Sf), ix, fx);
+        scatter(t0, i + iy, cc + ix, fy, fx, pend0, pr0, pc0, pt0, pb0);
+        if (two) {
+          if (!same_row) split_shift(fmaf(tv1, om, Sf), iy, fy);
+          split_shift(fmaf(tu1, om, Sf), ix, fx);
+          scatter(t1, i + iy, cc + ix, fy, fx, pend1, pr1, pc1, pt1, pb1);
+        }
+      };
+      if (SH::ALIGNED && full_cols) {
+#pragma unroll
+        for (int o = 0; o < SH::MB6; ++o)
+#pragma unroll
+          for (int ph = 0; ph < Z; ++ph) pixel(o, ph);
+      } else {
+#pragma unroll
+        for (int o = 0; o < SH::MB6; ++o)
+#pragma unroll
+          for (int ph = 0; ph < Z; ++ph) {
+            const int hj = Z * (n0 + o) + ph;
+            if (hj >= j0 && hj < j0 + T && hj < g.Wh) pixel(o, ph);
+          }
+      }
+      if (pend0) {
+        atomicAdd(sA + pr0 * NAc + pc0, pt0);
+        atomicAdd(sA + (pr0 + 1) * NAc + pc0, pb0);
+      }
+      if (pend1) {
+        atomicAdd(sA + pr1 * NAc + pc1, pt1);
+        atomicAdd(sA + (pr1 + 1) * NAc + pc1, pb1);
       }
     }
     __syncthreads();
@@ -361,9 +551,9 @@ static size_t fast_layout(const Geom& g, OpPlan* P) {
   P->NAc = (SH::T + 2 * S + 2) | 1;
   size_t off = 0;
   P->off_P = (int)off; off += al((size_t)(P->NPr + 1) * P->NPc);
-  P->off_W = (int)off; off += al((size_t)2 * SH::NE * SH::NEp);
-  P->off_H = (int)off; off += al((size_t)SH::HV);
-  P->off_G = (int)off; off += al((size_t)SH::NG * SH::NGp);
+  P->off_W = (int)off; off += al((size_t)(1 + SH::VB) * SH::WS);
+  P->off_H = (int)off; off += al((size_t)SH::VB * SH::HV);
+  P->off_G = (int)off; off += al((size_t)SH::VB * SH::GS);
   P->off_A = (int)off; off += al((size_t)P->NAr * P->NAc);
   P->smem_bytes = off * sizeof(float);
   P->tiles_x = (g.Wh + SH::T - 1) / SH::T;
