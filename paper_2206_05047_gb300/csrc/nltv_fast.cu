@@ -67,7 +67,7 @@ k_nlw2(const Geom g, const NlPlan P, const NlArgs a, float* __restrict__ wt,
   // patch origin (u - PR) of the strip's first pixel, in sX coordinates
   const float* xs = sX + (iu0 + WR) * NXp + (ju + WR);
   // directions in chunks of DB: the chunk's dual loads are issued first
-  constexpr int DB = 6;
+  constexpr int DB = 3;
 #pragma unroll
   for (int i0d = 0; i0d < D::SH; i0d += DB) {
     float wa_[DB][NF_PIX], wb_[DB][NF_PIX];

@@ -77,12 +77,25 @@ struct FastShape {
   static constexpr int MB6 = pick_block(T, NN);
   static constexpr int NB6 = (NN + MB6 - 1) / MB6;
   static constexpr int W6 = MB6 + DMAX - DMIN;
-  static constexpr int HV = (NEr * NHp > T * NVp) ? NEr * NHp : T * NVp;  // H/V buffer per view
+  static constexpr int HS = NEr * NHp;                       // forward H buffer per view
+  static constexpr int VS = T * NVp;                         // adjoint V buffer per view
   static constexpr int GS = NG * NGp;                        // LR grid per view
   static constexpr int WS = NE * NEp;                        // sample buffer per view
   static constexpr int NS1 = NE * NE;                        // warp samples per view
   static constexpr int IT1 = (NS1 + FT_THREADS - 1) / FT_THREADS;
 };
+
+// 4-byte asynchronous global -> shared copy; valid == false writes 0 (no
+// bytes are read from src, which only has to be a valid address).
+__device__ __forceinline__ void cp_async_f32(float* sdst, const float* gsrc, bool valid) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(saddr), "l"(gsrc),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
 
 __device__ __forceinline__ void split_shift(float t, int& ip, float& fr) {
   // t in [0, 2^23): ip = floor(t), fr = t - floor(t), exactly, on the FP32 pipe
@@ -102,7 +115,9 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
   float* sP = smem + P.off_P;   // source, (NE + 2S + 1) rows, pitch P.NPc
   float* sO = smem + P.off_W;   // disparity on the sample region, NE x NEp
   float* sW = sO + SH::WS;      // warped samples, VB x NE x NEp
-  float* sHV = smem + P.off_H;  // forward H (NEr x NHp) / adjoint V (T x NVp), VB copies
+  float* sH = smem + P.off_H;   // forward H, VB x NEr x NHp
+  float* sV = sH + VB * SH::HS; // adjoint V, VB x T x NVp (separate from H, so one unit's
+                                // scatter may overlap the next unit's forward stages)
   float* sG = smem + P.off_G;   // LR grid with zero margins, VB x NG x NGp
   float* sA = smem + P.off_A;   // scatter accumulator, NAr x NAc (pitch odd)
   const int tid = threadIdx.x;
@@ -167,8 +182,8 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
       e_c0 = Z * lc_lo - R;
       NAr_t = TRr + 2 * S + 1;
       NAc_t = TRc + 2 * S + 1;
-      // stage the source (zero outside the image) and the disparity: one
-      // warp per row, lanes along the row, loads batched before the stores
+      // stage the source (zero outside the image) and the disparity with
+      // asynchronous copies: every copy of the tile is in flight at once
       {
         const int warp = tid >> 5, lane = tid & 31;
         constexpr int NWARP = FT_THREADS / 32;
@@ -178,18 +193,10 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
             const int hi = e_r0 - S + pr;
             const bool row_in = hi >= 0 && hi < g.Hh;
             const float* src_row = a.src + (size_t)(row_in ? hi : 0) * g.Wh;
-            for (int cb = 0; cb < np; cb += 128) {
-              float vals[4];
-#pragma unroll
-              for (int c4 = 0; c4 < 4; ++c4) {
-                const int pc = cb + lane + 32 * c4, hj = e_c0 - S + pc;
-                vals[c4] = (pc < np && row_in && hj >= 0 && hj < g.Wh) ? __ldg(src_row + hj) : 0.f;
-              }
-#pragma unroll
-              for (int c4 = 0; c4 < 4; ++c4) {
-                const int pc = cb + lane + 32 * c4;
-                if (pc < np) sP[pr * NPc + pc] = vals[c4];
-              }
+            for (int pc = lane; pc < np; pc += 32) {
+              const int hj = e_c0 - S + pc;
+              const bool ok = row_in && hj >= 0 && hj < g.Wh;
+              cp_async_f32(sP + pr * NPc + pc, ok ? src_row + hj : a.src, ok);
             }
           }
         }
@@ -197,18 +204,13 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
           const int hi = e_r0 + er;
           const bool row_in = hi >= 0 && hi < g.Hh;
           const float* d_row = a.disp + (size_t)(row_in ? hi : 0) * g.Wh;
-          float vals[(NE + 31) / 32];
-#pragma unroll
-          for (int c4 = 0; c4 < (NE + 31) / 32; ++c4) {
-            const int ec = lane + 32 * c4, hj = e_c0 + ec;
-            vals[c4] = (ec < NE && row_in && hj >= 0 && hj < g.Wh) ? __ldg(d_row + hj) : 0.f;
-          }
-#pragma unroll
-          for (int c4 = 0; c4 < (NE + 31) / 32; ++c4) {
-            const int ec = lane + 32 * c4;
-            if (ec < NE) sO[er * NEp + ec] = vals[c4];
+          for (int ec = lane; ec < NE; ec += 32) {
+            const int hj = e_c0 + ec;
+            const bool ok = row_in && hj >= 0 && hj < g.Wh;
+            cp_async_f32(sO + er * NEp + ec, ok ? d_row + hj : a.disp, ok);
           }
         }
+        cp_async_wait_all();
       }
       __syncthreads();
       if (MODE != OP_ADJ) {
@@ -301,7 +303,7 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
 #pragma unroll
           for (int b = 0; b < KB; ++b) acc = fmaf(g.kh[b], win[Z * o + b], acc);
           const int lc = cb * SH::MB2 + o;
-          if (lc < NL) sHV[v * SH::HV + er * NHp + lc] = acc;
+          if (lc < NL) sH[v * SH::HS + er * NHp + lc] = acc;
         }
       }
       __syncthreads();
@@ -315,7 +317,7 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
         if (v >= nv) break;
         const int lc = r3 % NL, rb = r3 / NL;
         const int k = kbase + v;
-        const float* hcol = sHV + v * SH::HV + (Z * SH::MB3 * rb) * NHp + lc;
+        const float* hcol = sH + v * SH::HS + (Z * SH::MB3 * rb) * NHp + lc;
         float win[SH::W3];
 #pragma unroll
         for (int c = 0; c < SH::W3; ++c) win[c] = hcol[c * NHp];
@@ -398,7 +400,7 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
             if (ai >= 0 && ai <= 2 * R) acc = fmaf(g.kv[ai], win[o + d - SH::DMIN], acc);
           }
           const int ri = hi - i0;
-          if (ri >= 0 && ri < T) sHV[v * SH::HV + ri * NVp + c] = acc;
+          if (ri >= 0 && ri < T) sV[v * SH::VS + ri * NVp + c] = acc;
         }
       }
     }
@@ -420,8 +422,8 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
       const int c0 = n0 + SH::DMIN - lc_lo + MG;     // in [0, NG - W6] for every tile
       float win0[SH::W6], win1[SH::W6];
       {
-        const float* v0 = sHV + i * NVp + c0;
-        const float* v1 = v0 + SH::HV;
+        const float* v0 = sV + i * NVp + c0;
+        const float* v1 = v0 + SH::VS;
 #pragma unroll
         for (int w = 0; w < SH::W6; ++w) {
           win0[w] = v0[w];
@@ -504,7 +506,9 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
         atomicAdd(sA + (pr1 + 1) * NAc + pc1, pb1);
       }
     }
-    __syncthreads();
+    // no barrier here: the next unit's stages 1-2 write sW and sH, which this
+    // stage does not read, and sG / sV are rewritten only after two barriers;
+    // a tile change starts with a barrier before the flush
   }
 
   if (MODE != OP_FWD && cur_tile >= 0) {
@@ -552,7 +556,7 @@ static size_t fast_layout(const Geom& g, OpPlan* P) {
   size_t off = 0;
   P->off_P = (int)off; off += al((size_t)(P->NPr + 1) * P->NPc);
   P->off_W = (int)off; off += al((size_t)(1 + SH::VB) * SH::WS);
-  P->off_H = (int)off; off += al((size_t)SH::VB * SH::HV);
+  P->off_H = (int)off; off += al((size_t)SH::VB * (SH::HS + SH::VS));
   P->off_G = (int)off; off += al((size_t)SH::VB * SH::GS);
   P->off_A = (int)off; off += al((size_t)P->NAr * P->NAc);
   P->smem_bytes = off * sizeof(float);
