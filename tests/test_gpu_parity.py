@@ -198,3 +198,35 @@ def test_invalid_parameters_are_rejected():
     bad[3, 3] = np.nan
     with pytest.raises(lfsr.LfsrError):
         lfsr.create(3, 3, 8, 8, 2, blur, bad)
+
+
+@pytest.mark.parametrize("kind", ["smooth", "constant"])
+def test_disparity_paths(kind):
+    """The operator kernel takes a shared-split path on row segments of
+    constant disparity and a per-pixel path elsewhere: a smoothly varying
+    map exercises only the latter, a constant map only the former."""
+    wl = synth.custom(U=5, V=5, H=70, W=66, scale=2, kb=7, blur_sigma=1.2, window=7)
+    hr = wl.HR
+    if kind == "smooth":
+        ii, jj = np.meshgrid(np.arange(hr[0]), np.arange(hr[1]), indexing="ij")
+        disp = 1.3 * np.sin(ii / 17.0) * np.cos(jj / 23.0) + 0.25
+    else:
+        disp = np.full(hr, -0.7)
+    c = Case(wl, seed=8, disparity=disp, h=0.3)
+    o = c.oracle
+    rng = np.random.default_rng(12)
+    x = f32(rng.random(o.hr))
+    out = c.empty(o.s_k, wl.H, wl.W)
+    lfsr.apply_A(c.h, -1, c.t(x), out)
+    ref = np.stack([o.A(k, x.astype(np.float64)) for k in range(o.s_k)])
+    assert max_err(c.np(out), ref) <= 2e-6
+    p = f32(rng.standard_normal(o.hr))
+    q = c.empty(*o.hr)
+    pMp = lfsr.apply_normal(c.h, c.t(c.x0), c.t(p), q)
+    qref = o.normal_apply(o.weights(c.x0.astype(np.float64)), p.astype(np.float64))
+    assert max_err(c.np(q), qref) <= 5e-6
+    assert abs(pMp - float(np.vdot(p, qref))) <= 2e-6 * abs(float(np.vdot(p, qref)))
+    x_out = c.empty(*o.hr)
+    lfsr.solve(c.h, c.t(c.y), 3, c.t(c.x0), x_out)
+    rx, _, _ = o.admm(c.y.astype(np.float64), c.x0.astype(np.float64), 3)
+    assert rel_err(c.np(x_out), rx) <= 2e-5
