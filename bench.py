@@ -158,17 +158,23 @@ def oracle_rate(prob, iters: int):
     return wl.s_k * wl.HR[0] * wl.HR[1] * iters / dt / 1e6, dt, om.num_threads()
 
 
+def kernel_source_digest() -> str:
+    """Digest of the operator-kernel sources (the kernel the roofline names)."""
+    h = hashlib.sha256()
+    for f in ("op_kernels.cu", "op_fast.cu", "lfsr_internal.cuh", "lfsr_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2206_05047_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profile(wl):
     """DRAM bytes per normal-operator launch from the committed ncu summary,
     if it was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "normal_apply_traffic.json")
-    src = os.path.join(ROOT, "paper_2206_05047_gb300", "csrc", "op_kernels.cu")
     try:
         with open(path) as f:
             rec = json.load(f)
-        with open(src, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()[:16]
-        if rec.get("source_sha256_16") != digest or rec.get("workload") != wl.name:
+        if rec.get("source_sha256_16") != kernel_source_digest() or rec.get("workload") != wl.name:
             return None
         return float(rec["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -321,7 +327,7 @@ def main():
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_clk * 1e6 / 1e12
     achieved = flops / (avg_ms / 1e3) / 1e12
     traffic = traffic_from_profile(wl)
-    roofline = {"bound": "alu", "kernel": "k_operator<OP_NORMAL> (sum_k A_k^T A_k p)",
+    roofline = {"bound": "alu", "kernel": "k_operator_fast<OP_NORMAL> (sum_k A_k^T A_k p)",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "avg_launch_ms": avg_ms, "flops_per_launch": flops,
