@@ -87,6 +87,25 @@ def normal_flops_per_launch(wl) -> float:
     return wl.s_k * p * (16.0 + 4.0 * wl.kb * (1.0 / z + 1.0 / z ** 2))
 
 
+def max_over_ranks(value: float) -> float:
+    """Max of a per-rank scalar over the process group (the identity when no
+    group is initialised).  Uses a CUDA tensor under NCCL, a CPU one else."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+        else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank solves its own light field (replicas, weak scaling)."""
+    return 1000 * 2 + rank
+
+
 # --------------------------------------------------------------------------
 # clocks
 # --------------------------------------------------------------------------
@@ -232,7 +251,7 @@ def main():
 
     from paper_2206_05047_gb300 import lfsr
 
-    prob = synth.make_problem(wl, seed=1000 * 2 + rank)
+    prob = synth.make_problem(wl, seed=replica_seed(rank))
     blur = prob.blur.astype(np.float32)
     disp = prob.disparity.astype(np.float32)
     y_h = torch.from_numpy(prob.y.astype(np.float32)).pin_memory()
@@ -274,11 +293,7 @@ def main():
         evs.append((e0, e1))
     barrier()
     clk = clocks.stop()
-    t_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
-    t_ms_t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_ms_t, op=dist.ReduceOp.MAX)
-    t_ms = float(t_ms_t.item())
+    t_ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in evs))
     p = wl.HR[0] * wl.HR[1]
     work = wl.s_k * p * n_iter * a.steps * world
     value = work / (t_ms / 1e3) / 1e6
@@ -302,10 +317,7 @@ def main():
             e1.record(stream)
             e1.synchronize()
             e2e_ms += e0.elapsed_time(e1)
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms)
         e2e = {"value": work / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(y_h.numel() * 4 + x0_h.numel() * 4),
                "d2h_bytes_per_step": int(x_h.numel() * 4)}
