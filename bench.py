@@ -54,6 +54,10 @@ def args():
     ap.add_argument("--iterations", type=int, default=None, help="ADMM iterations per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="fp32",
+                    choices=["fp32", "fp16", "bf16", "fp16-views32", "bf16-views32"],
+                    help="storage type of views, duals and NLTV weights (arithmetic is f32); "
+                         "-views32 keeps the views in f32")
     return ap.parse_args()
 
 
@@ -69,12 +73,14 @@ def workload_config(wl, n_iter, extra=None):
     return cfg
 
 
-def alg_bytes_per_iter(wl) -> float:
-    """FP32 streaming bytes of one ADMM iteration: duals read+write, views
-    read, x / omega / v, and 11 HR-vector passes per CG step."""
+def alg_bytes_per_iter(wl, esize=4, esize_y=4) -> float:
+    """Streaming bytes of one ADMM iteration: duals read+write (esize bytes
+    each: 4, or 2 with 16-bit storage), views read (esize_y), x / omega / v,
+    and 11 HR-vector passes per CG step (float32)."""
     p = wl.HR[0] * wl.HR[1]
     q = wl.H * wl.W
-    return 4.0 * (3 * wl.s_k * q + 2 * wl.s_d * p + 3 * p) + 4.0 * wl.cg_iters * 11 * p
+    return (esize * (2 * wl.s_k * q + 2 * wl.s_d * p) + esize_y * wl.s_k * q + 4.0 * 3 * p
+            + 4.0 * wl.cg_iters * 11 * p)
 
 
 def normal_flops_per_launch(wl) -> float:
@@ -261,7 +267,7 @@ def main():
     x0_d = x0_h.to(dev)
     x_d = torch.empty(wl.HR, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    solver = lfsr.Solver(prob, stream=stream)
+    solver = lfsr.Solver(prob, stream=stream, precision=a.precision)
     h = solver.handle
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
@@ -354,7 +360,9 @@ def main():
     except (OSError, KeyError, ValueError):
         hbm, hbm_note = 6800.0, "of fallback"
     step_s = t_ms / 1e3 / a.steps
-    hbm_frac = alg_bytes_per_iter(wl) * n_iter / step_s / (hbm * 1e9)
+    esize = 4 if a.precision == "fp32" else 2
+    esize_y = 4 if a.precision in ("fp32", "fp16-views32", "bf16-views32") else 2
+    hbm_frac = alg_bytes_per_iter(wl, esize, esize_y) * n_iter / step_s / (hbm * 1e9)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -371,9 +379,15 @@ def main():
                 "dtype": "f32", "data": "synthetic (seeded textured-plane light field)",
                 "config": workload_config(wl, n_iter, {
                     "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                    "storage": {"fp32": "f32", "fp16": "f16 (views, duals, NLTV weights)",
+                                "bf16": "bf16 (views, duals, NLTV weights)",
+                                "fp16-views32": "f16 (duals, NLTV weights), f32 views",
+                                "bf16-views32": "bf16 (duals, NLTV weights), f32 views"}[
+                                    a.precision],
                     "l2": "flushed between steps (256 MB write); per-step working set "
                           f"{st['state_bytes'] / 1e6:.0f} MB"}),
-                "hbm_roofline": {"frac": hbm_frac, "alg_bytes_per_iter": alg_bytes_per_iter(wl),
+                "hbm_roofline": {"frac": hbm_frac,
+                                 "alg_bytes_per_iter": alg_bytes_per_iter(wl, esize, esize_y),
                                  "peak_gbs": hbm, "note": hbm_note},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(a.steps * n_iter * (3 + 3 * wl.cg_iters)),

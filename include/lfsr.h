@@ -13,7 +13,8 @@
  * kernels on one GPU; there is no CPU fallback.
  *
  * Conventions
- *  - Images are row-major float32.  LR size H x W; HR size (scale*H) x
+ *  - Images passed through this interface are row-major float32 (the
+ *    solver may keep its state in 16 bits, see LFSR_FP16_STORAGE).  LR size H x W; HR size (scale*H) x
  *    (scale*W) = Hh x Wh; p = Hh*Wh, q = H*W.
  *  - View k = v*U + u has angular offset theta_k = (u-(U-1)/2, v-(V-1)/2);
  *    U and V are odd so the centre view is the reference (Sec. 3.1).
@@ -62,7 +63,37 @@ extern "C" {
 #define LFSR_MEM_HOST   0
 #define LFSR_MEM_DEVICE 1
 
-#define LFSR_FP32 0            /* all state and arithmetic in float32       */
+/* Precision of the solver state (lfsr_params.precision).
+ *
+ * LFSR_FP32: all state and arithmetic in float32.
+ *
+ * LFSR_FP16_STORAGE / LFSR_BF16_STORAGE: the large streams -- the LR views
+ * y, the data duals, the regulariser duals and the stored NLTV edge
+ * weights -- are kept in IEEE half or bfloat16 (round to nearest even on
+ * every store); every kernel widens them to float and computes in float32.
+ * The HR iterate x, the CG vectors (r, p, q, v), the disparity map and the
+ * per-edge divergence terms of the z/w-step (an intermediate) stay
+ * float32, and the inner products of the x-step and the residual norms
+ * accumulate in float64, as in LFSR_FP32.  The errors against the float64
+ * algorithm are stated per workload by the tests.
+ *
+ * LFSR_KEEP_VIEWS_FP32 may be or-ed into a 16-bit precision to keep the
+ * views y in float32 (rounding the views perturbs the data itself, the
+ * largest single error term of half storage; the views are read once per
+ * ADMM iteration, so keeping them costs little bandwidth).
+ *
+ * Range: a view value (or a data dual given to lfsr_set_state) that is not
+ * finite or exceeds the type's largest finite value (65504 for half) is
+ * stored saturated and makes the next blocking call return LFSR_EINVAL.
+ * The duals are bounded by 1/mu, so LFSR_FP16_STORAGE requires
+ * 1/mu <= LFSR_FP16_MAX_INV_MU (else lfsr_create returns
+ * LFSR_EUNSUPPORTED).  Values below half's smallest subnormal (about
+ * 6e-8), e.g. vanishing NLTV weights, store as 0. */
+#define LFSR_FP32 0
+#define LFSR_FP16_STORAGE 1
+#define LFSR_BF16_STORAGE 2
+#define LFSR_KEEP_VIEWS_FP32 256
+#define LFSR_FP16_MAX_INV_MU 8192.0
 
 /* Problem and solver parameters (copied by lfsr_create).  struct_size must
  * be sizeof(lfsr_params). */
@@ -82,7 +113,8 @@ typedef struct lfsr_params {
   double nltv_h;           /* > 0                                           */
   int32_t cg_iters;        /* K of Algorithm 2, >= 0                        */
   double cg_tol;           /* tau: CG stops once pi = |r|^2 <= tau          */
-  int32_t precision;       /* LFSR_FP32                                     */
+  int32_t precision;       /* LFSR_FP32, LFSR_FP16_STORAGE or
+                              LFSR_BF16_STORAGE [| LFSR_KEEP_VIEWS_FP32]      */
 } lfsr_params;
 
 typedef struct lfsr_handle lfsr_handle;
@@ -117,7 +149,8 @@ int lfsr_create(const lfsr_params *params, void *cuda_stream, lfsr_handle **out)
  * and running the K-step CG x-step of Algorithm 2.  lr_views holds s_k*q
  * floats ([k][i][j]), x0 and x_out p floats.  Blocks until x_out is
  * written.  Returns LFSR_ENUMERIC if the CG curvature became non-finite
- * or non-positive. */
+ * or non-positive, LFSR_EINVAL if a view value does not fit the storage
+ * type (16-bit precisions). */
 int lfsr_solve(lfsr_handle *h, const float *lr_views, int iterations,
                const float *x0, float *x_out, int mem_kind);
 
@@ -147,7 +180,9 @@ int lfsr_get_x(lfsr_handle *h, float *x_out, int mem_kind);
 
 /* Sets / reads the full ADMM state in the canonical layout: x (p floats),
  * data duals wA (s_k*q), regulariser duals wS (s_d*p).  Any pointer may be
- * NULL to skip that part.  lfsr_get_state blocks until done. */
+ * NULL to skip that part.  lfsr_get_state blocks until done.  With a
+ * 16-bit precision the duals are rounded to the storage type on set and
+ * widened exactly on get. */
 int lfsr_set_state(lfsr_handle *h, const float *x, const float *wA,
                    const float *wS, int mem_kind);
 int lfsr_get_state(lfsr_handle *h, float *x, float *wA, float *wS, int mem_kind);

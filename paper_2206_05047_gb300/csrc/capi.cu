@@ -38,15 +38,18 @@ struct lfsr_handle {
   int grid_op = 0, grid_vec = 0, max_grid = 0;
   // device buffers
   float* disp = nullptr;
-  float* y = nullptr;
   float* x[2] = {nullptr, nullptr};
-  float* wA[2] = {nullptr, nullptr};
-  float* wS[2] = {nullptr, nullptr};
   float* R = nullptr;   // v, then the CG residual r
   float* P[2] = {nullptr, nullptr};
   float* Q = nullptr;
-  float* wt = nullptr;  // stored NLTV edge weights [s_d/2][p] (when supported)
   float* cb = nullptr;  // per-edge divergence terms of the z/w-step [s_d/2][p]
+  // streams in the storage kind g.st (float, half or bfloat16), esize bytes
+  // each; the views in kind g.st_y (esize_y bytes)
+  size_t esize = 4, esize_y = 4;
+  void* y = nullptr;
+  void* wA[2] = {nullptr, nullptr};
+  void* wS[2] = {nullptr, nullptr};
+  void* wt = nullptr;   // stored NLTV edge weights [s_d/2][p] (when supported)
   bool nlf = false;
   float* io = nullptr;  // staging for host <-> device and layout conversion
   size_t io_floats = 0;
@@ -99,9 +102,9 @@ void free_all(lfsr_handle* h) {
     cudaEventDestroy(ev.a);
     cudaEventDestroy(ev.b);
   }
-  float* bufs[] = {h->disp, h->y, h->x[0], h->x[1], h->wA[0], h->wA[1], h->wS[0],
-                   h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt, h->cb};
-  for (float* b : bufs)
+  void* bufs[] = {h->disp, h->y, h->x[0], h->x[1], h->wA[0], h->wA[1], h->wS[0],
+                  h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt, h->cb};
+  for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->partials) cudaFree(h->partials);
   if (h->sc) cudaFree(h->sc);
@@ -112,6 +115,13 @@ template <class T>
 cudaError_t dalloc(lfsr_handle* h, T** p, size_t n) {
   cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
   if (e == cudaSuccess) h->state_bytes += (int64_t)(n * sizeof(T));
+  return e;
+}
+
+cudaError_t dalloc_st(lfsr_handle* h, void** p, size_t n, size_t esize) {
+  const size_t bytes = n * esize;
+  cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 16);
+  if (e == cudaSuccess) h->state_bytes += (int64_t)bytes;
   return e;
 }
 
@@ -305,7 +315,14 @@ int validate(const lfsr_params* pr) {
   if (!(pr->nltv_h > 0.0) || !std::isfinite(pr->nltv_h)) return fail(nullptr, LFSR_EINVAL, "nltv_h must be > 0");
   if (pr->cg_iters < 0 || pr->cg_iters > 10000) return fail(nullptr, LFSR_EINVAL, "cg_iters must be in [0, 10000]");
   if (!(pr->cg_tol >= 0.0) || !std::isfinite(pr->cg_tol)) return fail(nullptr, LFSR_EINVAL, "cg_tol must be >= 0");
-  if (pr->precision != LFSR_FP32) return fail(nullptr, LFSR_EUNSUPPORTED, "only LFSR_FP32 is implemented");
+  const int base = pr->precision & ~LFSR_KEEP_VIEWS_FP32;
+  if (base != LFSR_FP32 && base != LFSR_FP16_STORAGE && base != LFSR_BF16_STORAGE)
+    return fail(nullptr, LFSR_EINVAL,
+                "precision must be LFSR_FP32, LFSR_FP16_STORAGE or LFSR_BF16_STORAGE, "
+                "optionally | LFSR_KEEP_VIEWS_FP32");
+  if (base == LFSR_FP16_STORAGE && 1.0 / pr->mu > LFSR_FP16_MAX_INV_MU)
+    return fail(nullptr, LFSR_EUNSUPPORTED,
+                "LFSR_FP16_STORAGE needs 1/mu <= 8192 (duals are bounded by 1/mu)");
   return LFSR_OK;
 }
 
@@ -373,6 +390,13 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   g.cA = (float)(pr->lambda2 + 0.5 * pr->mu * pr->lambda1 * pr->lambda1);
   g.thr = (float)(1.0 / pr->mu);
   g.tau = pr->cg_tol;
+  {
+    const int base = pr->precision & ~LFSR_KEEP_VIEWS_FP32;
+    g.st = base == LFSR_FP16_STORAGE ? ST_F16 : base == LFSR_BF16_STORAGE ? ST_BF16 : ST_F32;
+    g.st_y = (pr->precision & LFSR_KEEP_VIEWS_FP32) ? ST_F32 : g.st;
+  }
+  h->esize = storage_bytes(g.st);
+  h->esize_y = storage_bytes(g.st_y);
   h->p = p;
   h->q = q;
   h->nA = (size_t)g.sk * q;
@@ -417,18 +441,18 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
 
   e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = dalloc(h, &h->disp, p);
-  if (e == cudaSuccess) e = dalloc(h, &h->y, h->nA);
+  if (e == cudaSuccess) e = dalloc_st(h, &h->y, h->nA, h->esize_y);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = dalloc(h, &h->x[i], p);
-    if (e == cudaSuccess) e = dalloc(h, &h->wA[i], h->nA);
-    if (e == cudaSuccess) e = dalloc(h, &h->wS[i], h->nSpair);
+    if (e == cudaSuccess) e = dalloc_st(h, &h->wA[i], h->nA, h->esize);
+    if (e == cudaSuccess) e = dalloc_st(h, &h->wS[i], h->nSpair, h->esize);
     if (e == cudaSuccess) e = dalloc(h, &h->P[i], p);
   }
   if (e == cudaSuccess) e = dalloc(h, &h->R, p);
   if (e == cudaSuccess) e = dalloc(h, &h->Q, p);
   if (e == cudaSuccess) e = dalloc(h, &h->io, h->io_floats);
   h->nlf = nlf_supported(g);
-  if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->wt, (size_t)g.sh * p);
+  if (e == cudaSuccess && h->nlf) e = dalloc_st(h, &h->wt, (size_t)g.sh * p, h->esize);
   if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->cb, (size_t)g.sh * p);
   if (e == cudaSuccess) e = dalloc(h, &h->partials, (size_t)RED_NUM * h->max_grid);
   if (e == cudaSuccess) e = dalloc(h, &h->sc, 2);
@@ -461,11 +485,20 @@ int lfsr_load(lfsr_handle* h, const float* lr_views, const float* x0, int mem) {
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
   if (!lr_views || !x0) return fail(h, LFSR_EINVAL, "lr_views and x0 are required");
   if (check_mem(h, mem)) return LFSR_EINVAL;
-  CK(h, to_dev(h, h->y, lr_views, h->nA, mem), "upload views");
-  CK(h, to_dev(h, h->x[0], x0, h->p, mem), "upload x0");
-  CK(h, cudaMemsetAsync(h->wA[0], 0, h->nA * sizeof(float), h->stream), "clear data duals");
-  CK(h, cudaMemsetAsync(h->wS[0], 0, h->nSpair * sizeof(float), h->stream), "clear NLTV duals");
   CK(h, scalars_reset(h->sc, h->stream), "reset scalars");
+  if (h->g.st_y == ST_F32) {
+    CK(h, to_dev(h, (float*)h->y, lr_views, h->nA, mem), "upload views");
+  } else {
+    const float* src = lr_views;
+    if (mem == LFSR_MEM_HOST) {
+      CK(h, to_dev(h, h->io, lr_views, h->nA, mem), "upload views");
+      src = h->io;
+    }
+    CK(h, to_storage(h->g.st_y, src, h->y, h->nA, h->sc, h->grid_vec, h->stream), "store views");
+  }
+  CK(h, to_dev(h, h->x[0], x0, h->p, mem), "upload x0");
+  CK(h, cudaMemsetAsync(h->wA[0], 0, h->nA * h->esize, h->stream), "clear data duals");
+  CK(h, cudaMemsetAsync(h->wS[0], 0, h->nSpair * h->esize, h->stream), "clear NLTV duals");
   h->parity = 0;
   h->iters = 0;
   h->launches = 0;
@@ -504,6 +537,8 @@ int lfsr_iterate(lfsr_handle* h, int iterations) {
 static int read_status(lfsr_handle* h, DevScalars* hs) {
   CK(h, cudaMemcpyAsync(hs, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream), "read scalars");
   CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  if (hs->status == LFSR_EINVAL)
+    return fail(h, LFSR_EINVAL, "a view or data-dual value given to the solver is not finite or outside the storage type's range");
   if (hs->status != 0)
     return fail(h, hs->status, "non-finite or non-positive curvature in the CG x-step");
   return LFSR_OK;
@@ -574,7 +609,15 @@ int lfsr_set_state(lfsr_handle* h, const float* x, const float* wA, const float*
   if (check_mem(h, mem)) return LFSR_EINVAL;
   const int b = h->parity;
   if (x) CK(h, to_dev(h, h->x[b], x, h->p, mem), "set x");
-  if (wA) CK(h, to_dev(h, h->wA[b], wA, h->nA, mem), "set data duals");
+  if (wA && h->g.st == ST_F32) CK(h, to_dev(h, (float*)h->wA[b], wA, h->nA, mem), "set data duals");
+  if (wA && h->g.st != ST_F32) {
+    const float* src = wA;
+    if (mem == LFSR_MEM_HOST) {
+      CK(h, to_dev(h, h->io, wA, h->nA, mem), "set data duals");
+      src = h->io;
+    }
+    CK(h, to_storage(h->g.st, src, h->wA[b], h->nA, h->sc, h->grid_vec, h->stream), "store duals");
+  }
   if (wS) {
     CK(h, to_dev(h, h->io, wS, h->nS, mem), "set NLTV duals");
     CK(h, pair_from_canonical(h->g, h->io, h->wS[b], h->stream), "dual layout");
@@ -587,7 +630,11 @@ int lfsr_get_state(lfsr_handle* h, float* x, float* wA, float* wS, int mem) {
   if (check_mem(h, mem)) return LFSR_EINVAL;
   const int b = h->parity;
   if (x) CK(h, from_dev(h, x, h->x[b], h->p, mem), "get x");
-  if (wA) CK(h, from_dev(h, wA, h->wA[b], h->nA, mem), "get data duals");
+  if (wA && h->g.st == ST_F32) CK(h, from_dev(h, wA, (const float*)h->wA[b], h->nA, mem), "get data duals");
+  if (wA && h->g.st != ST_F32) {
+    CK(h, from_storage(h->g.st, h->wA[b], h->io, h->nA, h->grid_vec, h->stream), "load duals");
+    CK(h, from_dev(h, wA, h->io, h->nA, mem), "get data duals");
+  }
   if (wS) {
     CK(h, pair_to_canonical(h->g, h->wS[b], h->io, h->stream), "dual layout");
     CK(h, from_dev(h, wS, h->io, h->nS, mem), "get NLTV duals");

@@ -1,9 +1,87 @@
 // Device helpers shared by the kernel translation units of liblfsr.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "lfsr_internal.cuh"
 
 namespace lfsr {
+
+// Element access of the streams kept in the storage type (LR views, data
+// and regulariser duals, stored NLTV weights): loads widen to float, stores
+// round to nearest even.  Arithmetic stays float.  The 16-bit loads are
+// plain (compiler-visible) unsigned-short loads, so they can be predicated
+// and batched like float loads; widening to float is exact for both types.
+__device__ __forceinline__ float ld_s(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_s(const __half* p) {
+  return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+}
+__device__ __forceinline__ float ld_s(const __nv_bfloat16* p) {
+  return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p))));
+}
+__device__ __forceinline__ void st_s(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_s(__half* p, float v) {
+  *reinterpret_cast<unsigned short*>(p) = __half_as_ushort(__float2half_rn(v));
+}
+__device__ __forceinline__ void st_s(__nv_bfloat16* p, float v) {
+  *reinterpret_cast<unsigned short*>(p) = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// Split load / widen for latency hiding: a kernel issues all raw loads of a
+// batch (predicated, 0 when masked) and widens each value only where it is
+// used, so no conversion waits on a load that the batch could overlap.
+template <class ST> struct SBits;
+template <> struct SBits<float> {
+  using R = float;
+  static __device__ __forceinline__ R ld(const float* p) { return __ldg(p); }
+  static __device__ __forceinline__ float f(R r) { return r; }
+};
+template <> struct SBits<__half> {
+  using R = unsigned short;
+  static __device__ __forceinline__ R ld(const __half* p) {
+    return __ldg(reinterpret_cast<const unsigned short*>(p));
+  }
+  static __device__ __forceinline__ float f(R r) { return __half2float(__ushort_as_half(r)); }
+};
+template <> struct SBits<__nv_bfloat16> {
+  using R = unsigned short;
+  static __device__ __forceinline__ R ld(const __nv_bfloat16* p) {
+    return __ldg(reinterpret_cast<const unsigned short*>(p));
+  }
+  static __device__ __forceinline__ float f(R r) { return __bfloat162float(__ushort_as_bfloat16(r)); }
+};
+
+// Run-time storage kind: raw 32-bit word (float bits or a zero-extended
+// 16-bit value) and its widening, for the per-LR-pixel accesses of the
+// operator kernels (warp-uniform kind).
+__device__ __forceinline__ unsigned int ld_raw_kind(const void* base, size_t i, int st) {
+  if (st == ST_F32) return __ldg(reinterpret_cast<const unsigned int*>(base) + i);
+  return __ldg(reinterpret_cast<const unsigned short*>(base) + i);
+}
+__device__ __forceinline__ float raw_to_float(unsigned int r, int st) {
+  if (st == ST_F16) return __half2float(__ushort_as_half((unsigned short)r));
+  if (st == ST_BF16) return __bfloat162float(__ushort_as_bfloat16((unsigned short)r));
+  return __uint_as_float(r);
+}
+
+// The same with the storage kind (ST_*) known only at run time; for the
+// few per-LR-pixel accesses of the operator kernels (warp-uniform branch).
+__device__ __forceinline__ float ld_kind(const void* base, size_t i, int st) {
+  if (st == ST_F16) return ld_s((const __half*)base + i);
+  if (st == ST_BF16) return ld_s((const __nv_bfloat16*)base + i);
+  return ld_s((const float*)base + i);
+}
+__device__ __forceinline__ void st_kind(void* base, size_t i, int st, float v) {
+  if (st == ST_F16) st_s((__half*)base + i, v);
+  else if (st == ST_BF16) st_s((__nv_bfloat16*)base + i, v);
+  else st_s((float*)base + i, v);
+}
+
+// Sticky device status: the first error recorded stays.
+__device__ __forceinline__ void set_status(DevScalars* sc, int code) {
+  atomicCAS(&sc->status, 0, code);
+}
 
 // Floor / ceil division for a possibly negative numerator and positive d.
 __host__ __device__ __forceinline__ int floor_div(int n, int d) {

@@ -10,6 +10,10 @@
 
 namespace lfsr {
 
+// Storage kinds of the large streams (values of lfsr_params.precision).
+enum { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
+inline size_t storage_bytes(int st) { return st == ST_F32 ? 4 : 2; }
+
 // Geometry and solver constants, passed by value to every kernel (lives in
 // the kernel-parameter constant bank; all reads are warp-uniform).
 struct Geom {
@@ -28,6 +32,8 @@ struct Geom {
   float cA;              // lambda2 + mu lambda1^2 / 2
   float thr;             // 1 / mu (prox threshold, Eq. sr_l1l2l1_prox)
   double tau;            // CG threshold
+  int st;                // storage kind of the duals and stored weights (ST_*)
+  int st_y;              // storage kind of the LR views
   float kv[LFSR_MAX_KB], kh[LFSR_MAX_KB];
   float k2[LFSR_MAX_KB * LFSR_MAX_KB];
   float tu[LFSR_MAX_VIEWS], tv[LFSR_MAX_VIEWS];
@@ -77,9 +83,9 @@ struct OpArgs {
   const float* src;      // HR source (x or p) for FWD/NORMAL/DATA; LR g for ADJ
   const float* disp;     // HR disparity
   float* out;            // HR accumulator target (atomics) or LR output (FWD)
-  const float* y;        // DATA: LR views
-  const float* wA_old;   // DATA: data duals (read)
-  float* wA_new;         // DATA: data duals (written)
+  const void* y;         // DATA: LR views (storage kind g.st_y)
+  const void* wA_old;    // DATA: data duals (read, g.st)
+  void* wA_new;          // DATA: data duals (written, g.st)
   float scale;           // multiplies the accumulator on flush
   int view0, nviews;     // views of this launch
   int units;             // n_tiles * nviews
@@ -94,8 +100,8 @@ struct NlArgs {
   const float* p_old;    // APPLY: previous direction
   float* p_new;          // APPLY: new direction (written)
   float* out;            // BLOCK: v (stored); APPLY: q (stored); WEIGHTS: w
-  const float* wS_old;   // BLOCK: pair-layout duals (read)
-  float* wS_new;         // BLOCK: pair-layout duals (written)
+  const void* wS_old;    // BLOCK: pair-layout duals (read, g.st)
+  void* wS_new;          // BLOCK: pair-layout duals (written, g.st)
   double* partials;
   DevScalars* sc;
   int use_beta;          // APPLY: p_new = r + beta p_old (else p_new = src p)
@@ -133,10 +139,11 @@ cudaError_t nl_plan(const Geom& g, NlPlan* plan, int smem_limit);
 
 // NLTV with stored edge weights (window radius 1-3, patch radius 0-2).
 bool nlf_supported(const Geom& g);
-cudaError_t weights_to_canonical(const Geom& g, const float* wt, float* can, cudaStream_t s);
-cudaError_t nlw2_launch(int block, const Geom& g, const NlPlan& P, const NlArgs& a, float* wt,
+// wt holds s_d/2 x p values of the storage kind g.st; cb s_d/2 x p floats.
+cudaError_t weights_to_canonical(const Geom& g, const void* wt, float* can, cudaStream_t s);
+cudaError_t nlw2_launch(int block, const Geom& g, const NlPlan& P, const NlArgs& a, void* wt,
                         float* cb, cudaStream_t s);
-cudaError_t nla2_launch(const Geom& g, const NlPlan& P, const NlArgs& a, const float* wt,
+cudaError_t nla2_launch(const Geom& g, const NlPlan& P, const NlArgs& a, const void* wt,
                         cudaStream_t s);
 cudaError_t cg_init_nltv_launch(const Geom& g, float* rv, const float* cb, const float* x,
                                 float* x_next, double* partials, DevScalars* sc, int grid,
@@ -156,8 +163,15 @@ cudaError_t cg_init_launch(const Geom& g, float* r_inout_v, const float* x, floa
 cudaError_t cg_update_launch(const Geom& g, const float* p, const float* q, float* x_next,
                              float* r, double* partials_pi, DevScalars* sc, int grid,
                              cudaStream_t s);
-cudaError_t pair_from_canonical(const Geom& g, const float* can, float* pair, cudaStream_t s);
-cudaError_t pair_to_canonical(const Geom& g, const float* pair, float* can, cudaStream_t s);
+// Regulariser duals: canonical float [d][u] <-> edge-pair layout of kind g.st.
+cudaError_t pair_from_canonical(const Geom& g, const float* can, void* pair, cudaStream_t s);
+cudaError_t pair_to_canonical(const Geom& g, const void* pair, float* can, cudaStream_t s);
+// n floats -> storage kind st (round to nearest even).  A value that is
+// not finite or outside the kind's finite range sets sc->status to
+// LFSR_EINVAL (sticky) and is stored saturated (0 for NaN).
+cudaError_t to_storage(int st, const float* src, void* dst, size_t n, DevScalars* sc, int grid,
+                       cudaStream_t s);
+cudaError_t from_storage(int st, const void* src, float* dst, size_t n, int grid, cudaStream_t s);
 cudaError_t scalars_reset(DevScalars* sc, cudaStream_t s);
 
 // Sets the thread-local message that lfsr_last_error(NULL) returns.

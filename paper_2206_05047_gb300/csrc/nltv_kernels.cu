@@ -127,8 +127,8 @@ k_nltv(const Geom g, const NlPlan P, const NlArgs a) {
         if (MODE == NL_BLOCK) {
           if (v_in) {
             const size_t gi = (size_t)vi * Wh + vj;
-            const float wa = __ldg(a.wS_old + (size_t)(2 * idx) * p + gi);
-            const float wb = __ldg(a.wS_old + (size_t)(2 * idx + 1) * p + gi);
+            const float wa = ld_kind(a.wS_old, (size_t)(2 * idx) * p + gi, g.st);
+            const float wb = ld_kind(a.wS_old, (size_t)(2 * idx + 1) * p + gi, g.st);
             const int xr = er0 + ea + hx, xc = ec0 + ec + hx;
             const float diff = valid ? (sX[xr * NXc + xc] - sX[(xr + di) * NXc + xc + dj]) : 0.f;
             const float ua = fmaf(w, diff, wa);          // (S_d x)(v) + w
@@ -138,8 +138,8 @@ k_nltv(const Geom g, const NlPlan P, const NlArgs a) {
             const float fa = 2.f * an - wa, fb = 2.f * bn - wb;
             cval = w * (fa - fb);
             if (own) {
-              a.wS_new[(size_t)(2 * idx) * p + gi] = an;
-              a.wS_new[(size_t)(2 * idx + 1) * p + gi] = bn;
+              st_kind(a.wS_new, (size_t)(2 * idx) * p + gi, g.st, an);
+              st_kind(a.wS_new, (size_t)(2 * idx + 1) * p + gi, g.st, bn);
               const double da = (double)an - wa, db = (double)bn - wb;
               part += da * da + db * db;
             }

@@ -227,7 +227,8 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
 
     // data block: fetch the views' LR values and duals now, so the loads are
     // in flight during the warp and blur stages
-    float pre_y[SH::IT3][SH::MB3], pre_w[SH::IT3][SH::MB3];
+    // (raw words of the storage kinds; widened at use)
+    unsigned int pre_y[SH::IT3][SH::MB3], pre_w[SH::IT3][SH::MB3];
     if (MODE == OP_DATA) {
 #pragma unroll
       for (int it = 0; it < SH::IT3; ++it) {
@@ -237,12 +238,12 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
 #pragma unroll
         for (int o = 0; o < SH::MB3; ++o) {
           const int lr = rb * SH::MB3 + o;
-          pre_y[it][o] = 0.f;
-          pre_w[it][o] = 0.f;
+          pre_y[it][o] = 0u;
+          pre_w[it][o] = 0u;
           if (v < nv && lr < lr_n && lc < lc_n) {
             const size_t gi = (size_t)(kbase + v) * q_lr + (size_t)(lr_lo + lr) * g.W + (lc_lo + lc);
-            pre_y[it][o] = __ldg(a.y + gi);
-            pre_w[it][o] = __ldg(a.wA_old + gi);
+            pre_y[it][o] = ld_raw_kind(a.y, gi, g.st_y);
+            pre_w[it][o] = ld_raw_kind(a.wA_old, gi, g.st);
           }
         }
       }
@@ -338,14 +339,15 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
               if (owned) psum = fmaf(acc, acc, psum);
             } else if (MODE == OP_DATA) {
               const size_t gi = (size_t)k * q_lr + (size_t)gr * g.W + gc;
-              const float yv = pre_y[it][o], wa = pre_w[it][o];
+              const float yv = raw_to_float(pre_y[it][o], g.st_y);
+              const float wa = raw_to_float(pre_w[it][o], g.st);
               const float res = acc - yv;
               const float uu = fmaf(g.lambda1, res, wa);
               const float wn = fminf(fmaxf(uu, -g.thr), g.thr);
               const float f = 2.f * wn - wa;
               h = fmaf(g.lambda2, res, 0.5f * g.mu * g.lambda1 * f);
               if (owned) {
-                a.wA_new[gi] = wn;
+                st_kind(a.wA_new, gi, g.st, wn);
                 const float dd = wn - wa;
                 psum = fmaf(dd, dd, psum);
               }
@@ -525,7 +527,7 @@ k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
         const double pAp = (double)g.cA * total + (double)g.mu * a.sc->red[RED_NLTV];
         a.sc->pAp = pAp;
         if (!(pAp > 0.0) || !isfinite(pAp)) {
-          a.sc->status = -4;  // LFSR_ENUMERIC
+          set_status(a.sc, -4);  // LFSR_ENUMERIC
           a.sc->cg_done = 1;
           a.sc->alpha = 0.0;
         } else {

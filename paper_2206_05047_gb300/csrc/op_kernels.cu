@@ -186,14 +186,14 @@ k_operator(const Geom g, const OpPlan P, const OpArgs a) {
             if (owned) part += (double)acc * (double)acc;
           } else if (MODE == OP_DATA) {
             const size_t gi = (size_t)k * q_lr + (size_t)gr * g.W + gc;
-            const float yv = __ldg(a.y + gi), wa = __ldg(a.wA_old + gi);
+            const float yv = ld_kind(a.y, gi, g.st_y), wa = ld_kind(a.wA_old, gi, g.st);
             const float res = acc - yv;                      // a = A x - b
             const float uu = fmaf(g.lambda1, res, wa);       // u = F x - b' + w
             const float wn = fminf(fmaxf(uu, -g.thr), g.thr);  // w = u - prox(u)
             const float f = 2.f * wn - wa;                   // f = 2 w_n - w_{n-1}
             h = fmaf(g.lambda2, res, 0.5f * g.mu * g.lambda1 * f);
             if (owned) {
-              a.wA_new[gi] = wn;
+              st_kind(a.wA_new, gi, g.st, wn);
               const double dd = (double)wn - (double)wa;
               part += dd * dd;
             }
@@ -277,7 +277,7 @@ k_operator(const Geom g, const OpPlan P, const OpArgs a) {
         const double pAp = (double)g.cA * total + (double)g.mu * a.sc->red[RED_NLTV];
         a.sc->pAp = pAp;
         if (!(pAp > 0.0) || !isfinite(pAp)) {
-          a.sc->status = -4;  // LFSR_ENUMERIC
+          set_status(a.sc, -4);  // LFSR_ENUMERIC
           a.sc->cg_done = 1;
           a.sc->alpha = 0.0;
         } else {

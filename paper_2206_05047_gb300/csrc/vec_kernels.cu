@@ -3,7 +3,10 @@
 // r -= alpha q, pi' = <r, r>, beta = pi'/pi.  Inner products accumulate in
 // float64 and finish with a last-block reduction, so the scalars never leave
 // the device.  Also the conversions between the canonical regulariser-dual
-// layout [d][u] and the kernels' edge-pair layout.
+// layout [d][u] and the kernels' edge-pair layout, and between float and the
+// storage type of the large streams.
+#include <cfloat>
+
 #include "lfsr_device.cuh"
 
 namespace lfsr {
@@ -30,7 +33,7 @@ k_cg_init(const Geom g, float* __restrict__ rv, const float* __restrict__ x,
     sc->cg_steps = 0;
     sc->beta = 0.0;
     sc->dw2 = sc->dwA + sc->dwS;
-    if (!isfinite(total)) sc->status = -4;
+    if (!isfinite(total)) set_status(sc, -4);  // LFSR_ENUMERIC
     sc->cg_done = (total > g.tau && isfinite(total)) ? 0 : 1;
   }
 }
@@ -58,7 +61,7 @@ k_cg_update(const Geom g, const float* __restrict__ p, const float* __restrict__
     sc->pi = total;
     sc->cg_first = 0;
     sc->cg_steps += 1;
-    if (!isfinite(total)) sc->status = -4;
+    if (!isfinite(total)) set_status(sc, -4);  // LFSR_ENUMERIC
     if (!(total > g.tau) || !isfinite(total)) sc->cg_done = 1;
   }
 }
@@ -79,8 +82,9 @@ cudaError_t cg_update_launch(const Geom& g, const float* p, const float* q, floa
 // canonical [d][u] (d over the full window minus the centre, raster order)
 // <-> pair layout [idx][0][u] = dual of d_idx at u,
 //                 [idx][1][u] = dual of -d_idx at u + d_idx   (idx < s_d/2)
+template <class ST>
 __global__ void k_pair_from_canonical(const Geom g, const float* __restrict__ can,
-                                      float* __restrict__ pair) {
+                                      ST* __restrict__ pair) {
   const size_t p = (size_t)g.Hh * g.Wh;
   const int sd = 2 * g.sh;
   const size_t total = (size_t)g.sh * p;
@@ -90,15 +94,16 @@ __global__ void k_pair_from_canonical(const Geom g, const float* __restrict__ ca
     const size_t u = t - (size_t)idx * p;
     const int ui = (int)(u / g.Wh), uj = (int)(u - (size_t)ui * g.Wh);
     const int vi = ui + g.di[idx], vj = uj + g.dj[idx];
-    pair[(size_t)(2 * idx) * p + u] = can[(size_t)idx * p + u];
+    st_s(pair + (size_t)(2 * idx) * p + u, can[(size_t)idx * p + u]);
     float b = 0.f;
     if (vi >= 0 && vi < g.Hh && vj >= 0 && vj < g.Wh)
       b = can[(size_t)(sd - 1 - idx) * p + (size_t)vi * g.Wh + vj];
-    pair[(size_t)(2 * idx + 1) * p + u] = b;
+    st_s(pair + (size_t)(2 * idx + 1) * p + u, b);
   }
 }
 
-__global__ void k_pair_to_canonical(const Geom g, const float* __restrict__ pair,
+template <class ST>
+__global__ void k_pair_to_canonical(const Geom g, const ST* __restrict__ pair,
                                     float* __restrict__ can) {
   const size_t p = (size_t)g.Hh * g.Wh;
   const int sd = 2 * g.sh;
@@ -109,26 +114,100 @@ __global__ void k_pair_to_canonical(const Geom g, const float* __restrict__ pair
     const size_t u = t - (size_t)d * p;
     float val = 0.f;
     if (d < g.sh) {
-      val = pair[(size_t)(2 * d) * p + u];
+      val = ld_s(pair + (size_t)(2 * d) * p + u);
     } else {
       // direction -d_idx at u is the second dual of edge (u - d_idx, u)
       const int idx = sd - 1 - d;
       const int ui = (int)(u / g.Wh), uj = (int)(u - (size_t)ui * g.Wh);
       const int vi = ui - g.di[idx], vj = uj - g.dj[idx];
       if (vi >= 0 && vi < g.Hh && vj >= 0 && vj < g.Wh)
-        val = pair[(size_t)(2 * idx + 1) * p + (size_t)vi * g.Wh + vj];
+        val = ld_s(pair + (size_t)(2 * idx + 1) * p + (size_t)vi * g.Wh + vj);
     }
     can[t] = val;
   }
 }
 
-cudaError_t pair_from_canonical(const Geom& g, const float* can, float* pair, cudaStream_t s) {
-  k_pair_from_canonical<<<1024, 256, 0, s>>>(g, can, pair);
+cudaError_t pair_from_canonical(const Geom& g, const float* can, void* pair, cudaStream_t s) {
+  switch (g.st) {
+    case ST_F32: k_pair_from_canonical<<<1024, 256, 0, s>>>(g, can, (float*)pair); break;
+    case ST_F16: k_pair_from_canonical<<<1024, 256, 0, s>>>(g, can, (__half*)pair); break;
+    case ST_BF16: k_pair_from_canonical<<<1024, 256, 0, s>>>(g, can, (__nv_bfloat16*)pair); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
-cudaError_t pair_to_canonical(const Geom& g, const float* pair, float* can, cudaStream_t s) {
-  k_pair_to_canonical<<<1024, 256, 0, s>>>(g, pair, can);
+cudaError_t pair_to_canonical(const Geom& g, const void* pair, float* can, cudaStream_t s) {
+  switch (g.st) {
+    case ST_F32: k_pair_to_canonical<<<1024, 256, 0, s>>>(g, (const float*)pair, can); break;
+    case ST_F16: k_pair_to_canonical<<<1024, 256, 0, s>>>(g, (const __half*)pair, can); break;
+    case ST_BF16:
+      k_pair_to_canonical<<<1024, 256, 0, s>>>(g, (const __nv_bfloat16*)pair, can);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Float -> storage kind with a range check: the largest finite value of
+// the kind (65504 for half; float's own range for bfloat16).  A value
+// outside it, or not finite, raises the sticky status and is stored
+// saturated (NaN as 0), so no infinity or NaN enters the solver state.
+template <class ST>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_to_storage(const float* __restrict__ src, ST* __restrict__ dst, size_t n, float vmax,
+             DevScalars* sc) {
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * VEC_THREADS) {
+    float v = src[i];
+    if (!(fabsf(v) <= vmax)) {
+      bad = true;
+      v = (v != v) ? 0.f : copysignf(vmax, v);
+    }
+    st_s(dst + i, v);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(sc, -1);  // LFSR_EINVAL
+}
+
+template <class ST>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_from_storage(const ST* __restrict__ src, float* __restrict__ dst, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * VEC_THREADS)
+    dst[i] = ld_s(src + i);
+}
+
+cudaError_t to_storage(int st, const float* src, void* dst, size_t n, DevScalars* sc, int grid,
+                       cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  switch (st) {
+    case ST_F32:
+      k_to_storage<<<grid, VEC_THREADS, 0, s>>>(src, (float*)dst, n, FLT_MAX, sc);
+      break;
+    case ST_F16:
+      k_to_storage<<<grid, VEC_THREADS, 0, s>>>(src, (__half*)dst, n, 65504.f, sc);
+      break;
+    case ST_BF16:
+      // the largest finite bfloat16 (0x7f7f); larger floats would round to infinity
+      k_to_storage<<<grid, VEC_THREADS, 0, s>>>(src, (__nv_bfloat16*)dst, n,
+                                                3.3895313892515355e38f, sc);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t from_storage(int st, const void* src, float* dst, size_t n, int grid, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  switch (st) {
+    case ST_F32: k_from_storage<<<grid, VEC_THREADS, 0, s>>>((const float*)src, dst, n); break;
+    case ST_F16: k_from_storage<<<grid, VEC_THREADS, 0, s>>>((const __half*)src, dst, n); break;
+    case ST_BF16:
+      k_from_storage<<<grid, VEC_THREADS, 0, s>>>((const __nv_bfloat16*)src, dst, n);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -24,6 +24,14 @@ LFSR_EUNSUPPORTED = -6
 LFSR_MEM_HOST = 0
 LFSR_MEM_DEVICE = 1
 LFSR_FP32 = 0
+LFSR_FP16_STORAGE = 1
+LFSR_BF16_STORAGE = 2
+LFSR_KEEP_VIEWS_FP32 = 256
+LFSR_FP16_MAX_INV_MU = 8192.0
+# precision names accepted by Solver(precision=...) and the benchmark
+PRECISIONS = {"fp32": LFSR_FP32, "fp16": LFSR_FP16_STORAGE, "bf16": LFSR_BF16_STORAGE,
+              "fp16-views32": LFSR_FP16_STORAGE | LFSR_KEEP_VIEWS_FP32,
+              "bf16-views32": LFSR_BF16_STORAGE | LFSR_KEEP_VIEWS_FP32}
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblfsr.so")
 
@@ -278,6 +286,8 @@ class Solver:
                         cg_iters=wl.cg_iters)
             base.update(kw)
             kw = base
+        if isinstance(kw.get("precision"), str):
+            kw = dict(kw, precision=PRECISIONS[kw["precision"]])
         self.kw = kw
         self.handle = create(**kw)
         self.s_k = kw["U"] * kw["V"]

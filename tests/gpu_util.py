@@ -15,6 +15,22 @@ def rel_err(a, ref):
     return float(np.linalg.norm(a - ref) / max(np.linalg.norm(ref), 1e-30))
 
 
+def round_f16(a):
+    """Round-to-nearest-even float32 -> IEEE half -> float32 (numpy's cast)."""
+    return np.asarray(a, np.float32).astype(np.float16).astype(np.float32)
+
+
+def round_bf16(a):
+    """Round-to-nearest-even float32 -> bfloat16 -> float32, on the bits
+    (finite inputs)."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+ROUND = {"fp32": lambda a: np.asarray(a, np.float32), "fp16": round_f16, "bf16": round_bf16}
+
+
 def max_err(a, ref):
     a = np.asarray(a, np.float64)
     ref = np.asarray(ref, np.float64)
@@ -25,7 +41,7 @@ class Case:
     """One problem: float32 arrays, an oracle on their float64 images and a
     GPU solver on the same float32 values."""
 
-    def __init__(self, wl, seed=0, blur=None, disparity=None, **overrides):
+    def __init__(self, wl, seed=0, blur=None, disparity=None, precision="fp32", **overrides):
         import torch
         from oracle import oracle as om
         from paper_2206_05047_gb300 import lfsr
@@ -44,7 +60,8 @@ class Case:
         self.solver = lfsr.Solver(U=wl.U, V=wl.V, H=wl.H, W=wl.W, scale=wl.scale, blur=self.blur,
                                   disparity=self.disp, lambda1=p["lambda1"], lambda2=p["lambda2"],
                                   mu=p["mu"], nltv_window=p["window"], nltv_patch=p["patch"],
-                                  nltv_h=p["h"], cg_iters=p["cg_iters"], cg_tol=p["cg_tol"])
+                                  nltv_h=p["h"], cg_iters=p["cg_iters"], cg_tol=p["cg_tol"],
+                                  precision=precision)
         self.h = self.solver.handle
         self.torch = torch
         self.dev = torch.device("cuda:0")

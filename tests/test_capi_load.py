@@ -42,3 +42,31 @@ def test_invalid_arguments_fail_without_gpu():
         lfsr.create(2, 3, 8, 8, 2, blur, np.zeros((16, 16), np.float32))
     assert e.value.code == lfsr.LFSR_EINVAL
     assert "odd" in lfsr.last_error(None)
+
+
+def test_header_constants_match_binding():
+    src = open(os.path.join(ROOT, "include", "lfsr.h")).read()
+    defs = dict(re.findall(r"^#define\s+(LFSR_\w+)\s+\(?(-?[0-9.]+)\)?", src, re.M))
+    for name, val in defs.items():
+        if hasattr(lfsr, name):
+            assert float(getattr(lfsr, name)) == float(val), name
+    for name in ("LFSR_FP32", "LFSR_FP16_STORAGE", "LFSR_BF16_STORAGE", "LFSR_FP16_MAX_INV_MU",
+                 "LFSR_KEEP_VIEWS_FP32",
+                 "LFSR_EINVAL", "LFSR_EUNSUPPORTED", "LFSR_MEM_DEVICE"):
+        assert name in defs and hasattr(lfsr, name), name
+
+
+def test_precision_is_validated_without_gpu():
+    import numpy as np
+    import pytest
+    blur = np.ones((3, 3), np.float32) / 9
+    disp = np.zeros((16, 16), np.float32)
+    for bad in (3, lfsr.LFSR_KEEP_VIEWS_FP32 | 3, 512):
+        with pytest.raises(lfsr.LfsrError) as e:
+            lfsr.create(3, 3, 8, 8, 2, blur, disp, precision=bad)
+        assert e.value.code == lfsr.LFSR_EINVAL
+    # half storage cannot hold duals bounded by 1/mu = 1e4
+    with pytest.raises(lfsr.LfsrError) as e:
+        lfsr.create(3, 3, 8, 8, 2, blur, disp, mu=1e-4, precision=lfsr.LFSR_FP16_STORAGE)
+    assert e.value.code == lfsr.LFSR_EUNSUPPORTED
+    assert "8192" in lfsr.last_error(None)
