@@ -39,6 +39,7 @@ import numpy as np  # noqa: E402
 from paper_2206_05047_gb300 import synth  # noqa: E402
 
 METRIC = "HR LF Mpix*ADMM-iter/s"
+BATCH_WORKLOAD = "batch_uneven"
 UNIT = "Mpix*iter/s"
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
@@ -50,7 +51,9 @@ def args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lf9x9_256_x2", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="lf9x9_256_x2",
+                    choices=sorted(synth.WORKLOADS) + [BATCH_WORKLOAD])
+    ap.add_argument("--batch", type=int, default=64, help="light fields of the batch workload")
     ap.add_argument("--iterations", type=int, default=None, help="ADMM iterations per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -186,7 +189,8 @@ def oracle_rate(prob, iters: int):
 def kernel_source_digest() -> str:
     """Digest of the operator-kernel sources (the kernel the roofline names)."""
     h = hashlib.sha256()
-    for f in ("op_kernels.cu", "op_fast.cu", "lfsr_internal.cuh", "lfsr_device.cuh"):
+    for f in ("op_kernels.cu", "op_fast.cu", "op_fast.cuh", "lfsr_internal.cuh",
+              "lfsr_device.cuh"):
         with open(os.path.join(ROOT, "paper_2206_05047_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -236,8 +240,213 @@ def run_reference(a, wl, n_iter):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# batched uneven light fields: one launch per phase for all of them, against
+# the same light fields solved one after another by the plain path
+# --------------------------------------------------------------------------
+def _make_problem_args(wl_seed):
+    wl, seed = wl_seed
+    pr = synth.make_problem(wl, seed=seed)
+    return (pr.y.astype(np.float32), pr.x0.astype(np.float32), pr.blur.astype(np.float32),
+            pr.disparity.astype(np.float32), pr.gt)
+
+
+def batch_problems(n: int, seed: int = 4000):
+    """The batched configuration's light fields, generated in a process pool
+    (spawned: no CUDA state is forked)."""
+    import multiprocessing as mp
+    wls = synth.batch_workloads(n, seed)
+    jobs = [(w, seed + 1 + i) for i, w in enumerate(wls)]
+    procs = min(len(jobs), os.cpu_count() or 1, 16)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        out = pool.map(_make_problem_args, jobs, chunksize=1)
+    return wls, out
+
+
+def run_batch(a):
+    import torch
+    from paper_2206_05047_gb300 import lfsr
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit("the batch workload runs on one GPU")
+    t_gen = time.perf_counter()
+    wls, probs = batch_problems(a.batch)
+    t_gen = time.perf_counter() - t_gen
+    n_iter = a.iterations if a.iterations is not None else wls[0].iterations
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    kws = []
+    for wl, (y, x0, blur, disp, gt) in zip(wls, probs):
+        kws.append(dict(U=wl.U, V=wl.V, H=wl.H, W=wl.W, scale=wl.scale, blur=blur,
+                        disparity=disp, lambda1=wl.lambda1, lambda2=wl.lambda2, mu=wl.mu,
+                        nltv_window=wl.window, nltv_patch=wl.patch, nltv_h=wl.h,
+                        cg_iters=wl.cg_iters, cg_tol=0.0, precision=a.precision))
+    y_d = [torch.from_numpy(p[0]).to(dev) for p in probs]
+    x0_d = [torch.from_numpy(p[1]).to(dev) for p in probs]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    work = sum(w.s_k * w.HR[0] * w.HR[1] for w in wls) * n_iter     # HR LF pixel-iterations
+
+    def timed(step, steps):
+        torch.cuda.synchronize(dev)
+        total = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        return total
+
+    # the batch: one launch per phase (per operator group) for all light fields
+    batch = lfsr.Batch(kws, stream=stream)
+
+    def batch_step():
+        for j in range(len(wls)):
+            batch.load(j, y_d[j], x0_d[j])
+        batch.iterate(n_iter)
+
+    for _ in range(a.warmup):
+        batch_step()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.25)
+    t_batch = timed(batch_step, a.steps)
+    clk = clocks.stop()
+    value = work * a.steps / (t_batch / 1e3) / 1e6
+    xb = []
+    for j, wl in enumerate(wls):
+        x = torch.empty(wl.HR, dtype=torch.float32, device=dev)
+        batch.get_x(j, x)
+        xb.append(x.cpu().numpy().astype(np.float64))
+
+    # e2e: pinned host views and x0 in, x out, inside the timing
+    e2e = None
+    if not a.no_e2e:
+        y_h = [torch.from_numpy(p[0]).pin_memory() for p in probs]
+        x0_h = [torch.from_numpy(p[1]).pin_memory() for p in probs]
+        x_h = [torch.empty(w.HR, dtype=torch.float32).pin_memory() for w in wls]
+
+        def e2e_step():
+            for j in range(len(wls)):
+                batch.load(j, y_h[j], x0_h[j])
+            batch.iterate(n_iter)
+            for j in range(len(wls)):
+                batch.get_x(j, x_h[j])
+        t_e2e = timed(e2e_step, a.steps)
+        e2e = {"value": work * a.steps / (t_e2e / 1e3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(t.numel() * 4 for t in y_h + x0_h)),
+               "d2h_bytes_per_step": int(sum(t.numel() * 4 for t in x_h))}
+
+    # per-kernel times of one batched iteration (profiling mode)
+    batch.set_profiling(True)
+    batch_step()
+    ms, nl = batch.kernel_times()
+    batch.set_profiling(False)
+    names = ["nltv_block", "data_block", "cg_init", "nltv_apply", "normal_apply", "cg_update"]
+    per_class = {names[i]: {"ms": ms[i], "launches": nl[i]} for i in range(6)}
+    flops = sum(normal_flops_per_launch(w) for w in wls)         # one CG step, all light fields
+    normal_ms_per_step = per_class["normal_apply"]["ms"] / max(n_iter * wls[0].cg_iters, 1)
+    sm_clk = (clk.get("sm_max_mhz") or 2070.0)
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_clk * 1e6 / 1e12
+    achieved = flops / (normal_ms_per_step / 1e3) / 1e12
+    launches = batch.launches_per_iteration()
+    roofline = {"bound": "alu",
+                "kernel": "k_operator_fast<OP_NORMAL> (table: all light fields of a group)",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "normal_ms_per_cg_step": normal_ms_per_step, "flops_per_cg_step": flops,
+                "peak_note": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                             f"{sm_clk:.0f} MHz",
+                "per_kernel_ms_per_step": {k: v["ms"] for k, v in per_class.items()}}
+    batch.close()
+
+    # the plain path: the same light fields solved one after another
+    solvers = [lfsr.Solver(stream=stream, **kw) for kw in kws]
+
+    def plain_step():
+        for j, sv in enumerate(solvers):
+            lfsr.load(sv.handle, y_d[j], x0_d[j])
+            lfsr.iterate(sv.handle, n_iter)
+
+    def plain_x():
+        out = []
+        for sv, wl in zip(solvers, wls):
+            x = torch.empty(wl.HR, dtype=torch.float32, device=dev)
+            lfsr.get_x(sv.handle, x)
+            out.append(x.cpu().numpy().astype(np.float64))
+        return out
+
+    for _ in range(a.warmup - 1):
+        plain_step()
+    xp0 = plain_x() if a.warmup >= 1 else None
+    if a.warmup >= 1:
+        plain_step()
+    t_plain = timed(plain_step, a.steps)
+    value_plain = work * a.steps / (t_plain / 1e3) / 1e6
+    xp = plain_x()
+    gts = [p[4] for p in probs]
+    dpsnr = [synth.psnr(xb[j], gts[j]) - synth.psnr(xp[j], gts[j]) for j in range(len(wls))]
+    # two runs of the plain path differ as much: float atomics reorder sums and
+    # the reweighted iteration at this h amplifies the difference
+    dpsnr_plain = ([synth.psnr(xp0[j], gts[j]) - synth.psnr(xp[j], gts[j])
+                    for j in range(len(wls))] if xp0 is not None else [float("nan")])
+    assert all(np.isfinite(x).all() for x in xb)
+    for sv in solvers:
+        sv.close()
+
+    cpu = None
+    if not a.no_cpu_baseline:
+        small = min(range(len(wls)), key=lambda j: wls[j].s_k * wls[j].HR[0] * wls[j].HR[1])
+        y, x0, blur, disp, gt = probs[small]
+        prob = synth.Problem(wls[small], 0, blur.astype(np.float64), disp.astype(np.float64),
+                             y.astype(np.float64), x0.astype(np.float64), gt, None)
+        rate, dt, cores = oracle_rate(prob, 3)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"3 ADMM iterations of the smallest light field of the batch "
+                         f"({wls[small].name}), {dt:.1f} s"}
+    groups = sorted({(w.scale, w.kb) for w in wls})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t_batch / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded textured-plane light fields)",
+            "config": {"workload": BATCH_WORKLOAD, "light_fields": len(wls),
+                       "iterations": n_iter, "cg_iters": wls[0].cg_iters,
+                       "views": sorted({f"{w.U}x{w.V}" for w in wls}),
+                       "lr_side": [min(w.H for w in wls), max(w.H for w in wls)],
+                       "scales": sorted({w.scale for w in wls}),
+                       "operator_groups": [f"x{z} blur {k}x{k}" for z, k in groups],
+                       "hr_lf_mpix_per_iteration": work / n_iter / 1e6, "seed": 4000,
+                       "storage": a.precision, "parallelism": "single GPU",
+                       "l2": "flushed between steps (256 MB write); working set >> L2",
+                       "generation_s": round(t_gen, 1)},
+            "plain_serial": {"value": value_plain, "unit": UNIT,
+                             "ms_per_step": t_plain / a.steps,
+                             "launches_per_iteration": len(wls) * (3 + 3 * wls[0].cg_iters)},
+            "batch_vs_plain": value / value_plain,
+            "equal_psnr": {"batch_vs_plain": {"max_abs_db": max(abs(d) for d in dpsnr),
+                                              "mean_db": float(np.mean(dpsnr)),
+                                              "mean_psnr_batch_db": float(np.mean(
+                                                  [synth.psnr(xb[j], gts[j])
+                                                   for j in range(len(wls))]))},
+                           "plain_vs_plain": {"max_abs_db": max(abs(d) for d in dpsnr_plain),
+                                              "mean_db": float(np.mean(dpsnr_plain))}},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(a.steps * n_iter * launches),
+            "launches_per_iteration": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = args()
+    if a.workload == BATCH_WORKLOAD:
+        if a.impl == "reference":
+            run_reference(a, synth.batch_workloads(1)[0], 1)
+        else:
+            run_batch(a)
+        return
     wl = synth.WORKLOADS[a.workload]
     n_iter = a.iterations if a.iterations is not None else wl.iterations
     if a.impl == "reference":

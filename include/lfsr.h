@@ -210,6 +210,67 @@ int lfsr_apply_normal(lfsr_handle *h, const float *xw, const float *p, float *q,
  * kernel time.  Off by default. */
 int lfsr_set_profiling(lfsr_handle *h, int on);
 
+/* ---- batches of light fields ------------------------------------------
+ *
+ * A batch steps many light fields -- of different angular grids, LR sizes,
+ * scales and blurs -- through the ADMM iteration together (Algorithm 1 with
+ * the CG x-step of Algorithm 2, exactly as lfsr_iterate does for each of
+ * them).  Each phase of an iteration is one launch over a work list that
+ * spans every light field of the batch (NLTV tiles, (tile, view pair)
+ * operator units, chunks of HR pixels); the operator phases take one launch
+ * per group of light fields that share the scale and the blur kernel.  Two
+ * iterations are captured as one CUDA graph and replayed.  The CG scalars
+ * stay per light field; every light field's result equals its result alone
+ * up to the order of float atomic additions.
+ *
+ * Requirements: the light fields share lambda1, lambda2, mu, the NLTV
+ * window, patch and h, cg_iters, cg_tol and precision (else LFSR_EINVAL),
+ * and each takes the specialised kernels -- a separable blur with (scale,
+ * kb) in {(1,3) (1,5) (1,7) (2,3) (2,5) (2,7) (2,9) (3,5) (3,7) (3,9) (4,7)
+ * (4,9)} and an NLTV window of 3, 5 or 7 with a patch of 1, 3 or 5 (else
+ * LFSR_EUNSUPPORTED).  Each light field's state is allocated as by
+ * lfsr_create.  All calls are ordered on cuda_stream.  Not thread-safe. */
+#define LFSR_BATCH_MAX 4096
+
+typedef struct lfsr_batch lfsr_batch;
+
+/* Creates a batch of n light fields, params[j] describing light field j
+ * (copied).  *out is NULL on failure. */
+int lfsr_batch_create(const lfsr_params *params, int n, void *cuda_stream, lfsr_batch **out);
+
+/* Frees the batch and all its device memory.  NULL is a no-op. */
+void lfsr_batch_destroy(lfsr_batch *b);
+
+/* Message of the last failing call on b (NULL: of this thread's last
+ * failing batch call).  Never NULL. */
+const char *lfsr_batch_last_error(const lfsr_batch *b);
+
+/* Number of light fields (0 for NULL). */
+int lfsr_batch_size(const lfsr_batch *b);
+
+/* As lfsr_load for light field `job`: views and x0 in, duals := 0. */
+int lfsr_batch_load(lfsr_batch *b, int job, const float *lr_views, const float *x0,
+                    int mem_kind);
+
+/* Enqueues `iterations` ADMM iterations of every light field (no host
+ * synchronisation). */
+int lfsr_batch_iterate(lfsr_batch *b, int iterations);
+
+/* As lfsr_get_x / lfsr_stats for light field `job` (blocking). */
+int lfsr_batch_get_x(lfsr_batch *b, int job, float *x_out, int mem_kind);
+int lfsr_batch_stats(const lfsr_batch *b, int job, lfsr_stats_t *out);
+
+/* Kernel launches per ADMM iteration of the whole batch. */
+int lfsr_batch_launches_per_iteration(const lfsr_batch *b);
+
+/* Profiling mode (as lfsr_set_profiling): lfsr_batch_iterate launches one by
+ * one with CUDA events around each launch; lfsr_batch_kernel_times
+ * synchronises and returns the summed milliseconds and launch counts by
+ * class (the classes of lfsr_stats_t; 8 entries each) since profiling was
+ * switched on. */
+int lfsr_batch_set_profiling(lfsr_batch *b, int on);
+int lfsr_batch_kernel_times(lfsr_batch *b, double *ms, int64_t *launches);
+
 /* ---- no-allocation variant ------------------------------------------
  *
  * Some callers cannot allocate device memory: code that runs inside a host

@@ -8,8 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "lfsr.h"
-#include "lfsr_internal.cuh"
+#include "handle.cuh"
 
 using namespace lfsr;
 
@@ -17,57 +16,10 @@ namespace {
 
 thread_local std::string t_err = "no error";
 
-constexpr int NUM_CLASSES = 6;  // profiling classes, see lfsr_stats_t
-
-struct ProfEvent {
-  int cls;
-  cudaEvent_t a, b;
-};
+constexpr int NUM_CLASSES = KD_NUM;  // profiling classes, see lfsr_stats_t
 
 }  // namespace
 
-struct lfsr_handle {
-  lfsr_params prm{};
-  Geom g{};
-  OpPlan op{};
-  NlPlan nl{};
-  cudaStream_t stream = nullptr;      // caller's stream
-  cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
-  int device = 0, sm_count = 0;
-  size_t p = 0, q = 0, nA = 0, nS = 0, nSpair = 0;
-  int grid_op = 0, grid_vec = 0, max_grid = 0;
-  // device buffers
-  float* disp = nullptr;
-  float* x[2] = {nullptr, nullptr};
-  float* R = nullptr;   // v, then the CG residual r
-  float* P[2] = {nullptr, nullptr};
-  float* Q = nullptr;
-  float* cb = nullptr;  // per-edge divergence terms of the z/w-step [s_d/2][p]
-  // streams in the storage kind g.st (float, half or bfloat16), esize bytes
-  // each; the views in kind g.st_y (esize_y bytes)
-  size_t esize = 4, esize_y = 4;
-  void* y = nullptr;
-  void* wA[2] = {nullptr, nullptr};
-  void* wS[2] = {nullptr, nullptr};
-  void* wt = nullptr;   // stored NLTV edge weights [s_d/2][p] (when supported)
-  bool nlf = false;
-  float* io = nullptr;  // staging for host <-> device and layout conversion
-  size_t io_floats = 0;
-  double* partials = nullptr;
-  DevScalars* sc = nullptr;  // [0] solver, [1] standalone operator calls
-  int64_t state_bytes = 0;
-  // schedule state
-  int parity = 0;
-  int iters = 0;
-  int64_t launches = 0;
-  cudaGraphExec_t graph_pair = nullptr;     // iterations at parity 0 then 1
-  cudaGraphExec_t graph_single[2] = {nullptr, nullptr};
-  bool profiling = false;
-  std::vector<ProfEvent> prof;
-  double prof_ms[8] = {0};
-  int64_t prof_n[8] = {0};
-  std::string err = "no error";
-};
 
 namespace {
 
@@ -108,6 +60,9 @@ void free_all(lfsr_handle* h) {
     if (b) cudaFree(b);
   if (h->partials) cudaFree(h->partials);
   if (h->sc) cudaFree(h->sc);
+  if (h->jobs_dev) cudaFree(h->jobs_dev);
+  if (h->jobs_scratch) cudaFree(h->jobs_scratch);
+  if (h->counters) cudaFree(h->counters);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
@@ -163,83 +118,104 @@ cudaError_t timed(lfsr_handle* h, cudaStream_t s, int cls, F&& launch) {
   return e;
 }
 
+// Table of one entry for launch `kind` at (b, pb) of this handle.
+TableArgs handle_table(lfsr_handle* h, int kind, int b, int pb) {
+  TableArgs t{};
+  t.jobs = h->jobs_dev + (2 * b + pb) * KD_NUM + kind;
+  t.unit_job = nullptr;
+  t.n_jobs = 1;
+  t.total_units = kind_units(h, kind);
+  t.check_done = (kind == KD_NLA || kind == KD_NORMAL) ? 1 : 0;
+  t.partials = part_slot(h, kind_slot(kind));
+  t.counter = h->counters + kind;
+  return t;
+}
+
 // One ADMM iteration (Algorithm 1) on parity b: reads x[b], w*[b], writes
-// x[1-b], w*[1-b].
+// x[1-b], w*[1-b].  The specialised kernels run from this handle's job
+// tables; geometries they do not cover take the generic kernels.
 cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
   const int nb = 1 - b;
   const Geom& g = h->g;
   DevScalars* sc = h->sc;
   cudaError_t e;
   // regulariser rows: weights from x^(n-1), z/w-step, v := mu/2 S^T f
-  NlArgs nbk{};
-  nbk.x = h->x[b];
-  nbk.out = h->R;
-  nbk.wS_old = h->wS[b];
-  nbk.wS_new = h->wS[nb];
-  nbk.partials = part_slot(h, RED_DW_S);
-  nbk.sc = sc;
-  e = timed(h, s, 0, [&] {
-    return h->nlf ? nlw2_launch(1, g, h->nl, nbk, h->wt, h->cb, s)
-                  : nl_launch(NL_BLOCK, g, h->nl, nbk, s);
+  e = timed(h, s, KD_NLW, [&] {
+    if (h->nlf) return nlw2_launch(1, g, handle_table(h, KD_NLW, b, 0), s);
+    NlArgs nbk{};
+    nbk.x = h->x[b];
+    nbk.out = h->R;
+    nbk.wS_old = h->wS[b];
+    nbk.wS_new = h->wS[nb];
+    nbk.partials = part_slot(h, RED_DW_S);
+    nbk.sc = sc;
+    return nl_launch(NL_BLOCK, g, h->nl, nbk, s);
   });
   if (e != cudaSuccess) return e;
   // data rows: a = A x - b, z/w-step, v += A^T (l2 a + mu/2 l1 f)
-  OpArgs od{};
-  od.src = h->x[b];
-  od.disp = h->disp;
-  od.out = h->R;
-  od.y = h->y;
-  od.wA_old = h->wA[b];
-  od.wA_new = h->wA[nb];
-  od.scale = 1.f;
-  od.view0 = 0;
-  od.nviews = g.sk;
-  od.units = h->op.n_tiles * g.sk;
-  od.partials = part_slot(h, RED_DW_A);
-  od.sc = sc;
-  e = timed(h, s, 1, [&] { return op_launch(OP_DATA, g, h->op, od, h->grid_op, s); });
+  e = timed(h, s, KD_DATA, [&] {
+    if (h->op.fast)
+      return fast_launch(OP_DATA, g, h->op, handle_table(h, KD_DATA, b, 0), h->grid_op, s,
+                         &h->jobs_host[(2 * b) * KD_NUM + KD_DATA]);
+    OpArgs od{};
+    od.src = h->x[b];
+    od.disp = h->disp;
+    od.out = h->R;
+    od.y = h->y;
+    od.wA_old = h->wA[b];
+    od.wA_new = h->wA[nb];
+    od.scale = 1.f;
+    od.view0 = 0;
+    od.nviews = g.sk;
+    od.units = h->op.n_tiles * g.sk;
+    od.partials = part_slot(h, RED_DW_A);
+    od.sc = sc;
+    return op_launch(OP_DATA, g, h->op, od, h->grid_op, s);
+  });
   if (e != cudaSuccess) return e;
   // x-step (Algorithm 2): r = -v, x' = x, pi = <r, r>
-  e = timed(h, s, 2, [&] {
-    return h->nlf ? cg_init_nltv_launch(g, h->R, h->cb, h->x[b], h->x[nb], part_slot(h, RED_PI),
-                                        sc, h->grid_vec, s)
-                  : cg_init_launch(g, h->R, h->x[b], h->x[nb], part_slot(h, RED_PI), sc,
-                                   h->grid_vec, s);
+  e = timed(h, s, KD_INIT, [&] {
+    const TableArgs t = handle_table(h, KD_INIT, b, 0);
+    return h->nlf ? cg_init_nltv_launch(g, t, s) : cg_init_launch(g, t, s);
   });
   if (e != cudaSuccess) return e;
   for (int k = 0; k < h->prm.cg_iters; ++k) {
     const int pb = k & 1;
-    NlArgs na{};
-    na.x = h->x[b];
-    na.r = h->R;
-    na.p_old = h->P[1 - pb];
-    na.p_new = h->P[pb];
-    na.out = h->Q;
-    na.partials = part_slot(h, RED_NLTV);
-    na.sc = sc;
-    na.use_beta = 1;
-    na.check_done = 1;
-    e = timed(h, s, 3, [&] {
-      return h->nlf ? nla2_launch(g, h->nl, na, h->wt, s) : nl_launch(NL_APPLY, g, h->nl, na, s);
+    e = timed(h, s, KD_NLA, [&] {
+      if (h->nlf) return nla2_launch(g, handle_table(h, KD_NLA, b, pb), s);
+      NlArgs na{};
+      na.x = h->x[b];
+      na.r = h->R;
+      na.p_old = h->P[1 - pb];
+      na.p_new = h->P[pb];
+      na.out = h->Q;
+      na.partials = part_slot(h, RED_NLTV);
+      na.sc = sc;
+      na.use_beta = 1;
+      na.check_done = 1;
+      return nl_launch(NL_APPLY, g, h->nl, na, s);
     });
     if (e != cudaSuccess) return e;
-    OpArgs on{};
-    on.src = h->P[pb];
-    on.disp = h->disp;
-    on.out = h->Q;
-    on.scale = g.cA;
-    on.view0 = 0;
-    on.nviews = g.sk;
-    on.units = h->op.n_tiles * g.sk;
-    on.partials = part_slot(h, RED_OP);
-    on.sc = sc;
-    on.check_done = 1;
-    e = timed(h, s, 4, [&] { return op_launch(OP_NORMAL, g, h->op, on, h->grid_op, s); });
-    if (e != cudaSuccess) return e;
-    e = timed(h, s, 5, [&] {
-      return cg_update_launch(g, h->P[pb], h->Q, h->x[nb], h->R, part_slot(h, RED_PI), sc,
-                              h->grid_vec, s);
+    e = timed(h, s, KD_NORMAL, [&] {
+      if (h->op.fast)
+        return fast_launch(OP_NORMAL, g, h->op, handle_table(h, KD_NORMAL, b, pb), h->grid_op, s,
+                           &h->jobs_host[(2 * b + pb) * KD_NUM + KD_NORMAL]);
+      OpArgs on{};
+      on.src = h->P[pb];
+      on.disp = h->disp;
+      on.out = h->Q;
+      on.scale = g.cA;
+      on.view0 = 0;
+      on.nviews = g.sk;
+      on.units = h->op.n_tiles * g.sk;
+      on.partials = part_slot(h, RED_OP);
+      on.sc = sc;
+      on.check_done = 1;
+      return op_launch(OP_NORMAL, g, h->op, on, h->grid_op, s);
     });
+    if (e != cudaSuccess) return e;
+    e = timed(h, s, KD_UPDATE,
+              [&] { return cg_update_launch(g, handle_table(h, KD_UPDATE, b, pb), s); });
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -328,7 +304,137 @@ int validate(const lfsr_params* pr) {
 
 }  // namespace
 
+namespace {
+
+// One-entry table in the handle's scratch slot `slot` for a standalone
+// operator call (the host entry is copied at once; calls on the handle are
+// stream-ordered).
+cudaError_t scratch_table(lfsr_handle* h, int slot, const JobArgs& j, int red_slot, TableArgs* t) {
+  cudaError_t e = cudaMemcpyAsync(h->jobs_scratch + slot, &j, sizeof(JobArgs),
+                                  cudaMemcpyHostToDevice, h->stream);
+  *t = TableArgs{};
+  t->jobs = h->jobs_scratch + slot;
+  t->unit_job = nullptr;
+  t->n_jobs = 1;
+  t->total_units = j.units;
+  t->check_done = 0;
+  t->partials = part_slot(h, red_slot);
+  t->counter = h->counters + KD_NUM + slot;
+  return e;
+}
+
+// Common fields of a standalone operator-call entry.
+JobArgs standalone_job(const lfsr_handle* h) {
+  JobArgs j{};
+  j.H = h->g.H;
+  j.W = h->g.W;
+  j.Hh = h->g.Hh;
+  j.Wh = h->g.Wh;
+  j.U = h->g.U;
+  j.V = h->g.V;
+  j.disp = h->disp;
+  j.sc = h->sc + 1;
+  return j;
+}
+
+}  // namespace
+
 void lfsr::set_thread_error(const char* msg) { t_err = msg; }
+
+int lfsr::handle_fail(lfsr_handle* h, int code, const std::string& msg) { return fail(h, code, msg); }
+int lfsr::handle_cuda_fail(lfsr_handle* h, cudaError_t e, const char* what) {
+  return cuda_fail(h, e, what);
+}
+
+int lfsr::kind_slot(int kind) {
+  switch (kind) {
+    case KD_NLW: return RED_DW_S;
+    case KD_DATA: return RED_DW_A;
+    case KD_NLA: return RED_NLTV;
+    case KD_NORMAL: return RED_OP;
+    default: return RED_PI;   // KD_INIT, KD_UPDATE
+  }
+}
+
+int lfsr::kind_units(const lfsr_handle* h, int kind) {
+  switch (kind) {
+    case KD_NLW:
+    case KD_NLA: return h->nl_units;
+    case KD_DATA:
+    case KD_NORMAL: return h->op_units;
+    default: return h->vec_units;
+  }
+}
+
+JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0) {
+  const Geom& g = h->g;
+  const int nb = 1 - b;
+  JobArgs j{};
+  j.H = g.H;
+  j.W = g.W;
+  j.Hh = g.Hh;
+  j.Wh = g.Wh;
+  j.U = g.U;
+  j.V = g.V;
+  j.unit0 = unit0;
+  j.units = kind_units(h, kind);
+  j.disp = h->disp;
+  j.sc = h->sc;
+  switch (kind) {
+    case KD_NLW:   // weights from x^(n-1), regulariser z/w-step, v := 0
+      j.tiles_x = h->nl_tiles_x;
+      j.src = h->x[b];
+      j.out = h->R;
+      j.wS_old = h->wS[b];
+      j.wS_new = h->wS[nb];
+      j.wt = h->wt;
+      j.cb = h->cb;
+      break;
+    case KD_DATA:  // data rows, v += A^T (...)
+      j.tiles_x = h->op.tiles_x;
+      j.view0 = 0;
+      j.nviews = g.sk;
+      j.scale = 1.f;
+      j.src = h->x[b];
+      j.out = h->R;
+      j.y = h->y;
+      j.wA_old = h->wA[b];
+      j.wA_new = h->wA[nb];
+      break;
+    case KD_INIT:  // r = -(v + regulariser divergence), x' = x
+      j.chunk = h->vec_chunk;
+      j.out = h->R;
+      j.cb = h->cb;
+      j.src = h->x[b];
+      j.x_next = h->x[nb];
+      break;
+    case KD_NLA:   // p = r + beta p_old, q = mu S^T W^2 S p
+      j.tiles_x = h->nl_tiles_x;
+      j.use_beta = 1;
+      j.r = h->R;
+      j.p_old = h->P[1 - pb];
+      j.p_new = h->P[pb];
+      j.out = h->Q;
+      j.wt = h->wt;
+      break;
+    case KD_NORMAL:  // q += cA sum_k A_k^T A_k p
+      j.tiles_x = h->op.tiles_x;
+      j.view0 = 0;
+      j.nviews = g.sk;
+      j.scale = g.cA;
+      j.src = h->P[pb];
+      j.out = h->Q;
+      break;
+    default:       // KD_UPDATE: x += alpha p, r -= alpha q
+      j.chunk = h->vec_chunk;
+      j.p_old = h->P[pb];
+      j.q = h->Q;
+      j.rr = h->R;
+      j.x_next = h->x[nb];
+      break;
+  }
+  return j;
+}
 
 extern "C" {
 
@@ -431,11 +537,25 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
     delete h;
     return fail(nullptr, LFSR_EUNSUPPORTED, "NLTV window / patch too large");
   }
-  h->grid_op = op_grid(h->op, h->op.n_tiles * g.sk, h->sm_count);
+  h->op_units = h->op.n_tiles * ((g.sk + FAST_VIEWS - 1) / FAST_VIEWS);
+  h->grid_op = op_grid(h->op, h->op.fast ? h->op_units : h->op.n_tiles * g.sk, h->sm_count);
   h->grid_vec = h->sm_count * 2;
+  h->nl_tiles_x = (Wh + NLF_TILE - 1) / NLF_TILE;
+  h->nl_units = h->nl_tiles_x * ((Hh + NLF_TILE - 1) / NLF_TILE);
+  {
+    // vector kernels: two CTAs per SM (a whole number of waves), chunks of
+    // a multiple of 32 pixels, at least 256
+    size_t chunk = (p + (size_t)h->grid_vec - 1) / (size_t)h->grid_vec;
+    chunk = (chunk + 31) / 32 * 32;
+    if (chunk < 256) chunk = 256;
+    h->vec_chunk = (int)chunk;
+    h->vec_units = (int)((p + chunk - 1) / chunk);
+  }
   h->max_grid = h->grid_op;
   if (h->nl.n_tiles > h->max_grid) h->max_grid = h->nl.n_tiles;
+  if (h->nl_units > h->max_grid) h->max_grid = h->nl_units;
   if (h->grid_vec > h->max_grid) h->max_grid = h->grid_vec;
+  if (h->vec_units > h->max_grid) h->max_grid = h->vec_units;
   h->io_floats = h->nA > h->nS ? h->nA : h->nS;
   if (h->io_floats < p) h->io_floats = p;
 
@@ -456,6 +576,18 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->cb, (size_t)g.sh * p);
   if (e == cudaSuccess) e = dalloc(h, &h->partials, (size_t)RED_NUM * h->max_grid);
   if (e == cudaSuccess) e = dalloc(h, &h->sc, 2);
+  if (e == cudaSuccess) e = dalloc(h, &h->jobs_dev, (size_t)4 * KD_NUM);
+  if (e == cudaSuccess) e = dalloc(h, &h->jobs_scratch, 4);
+  if (e == cudaSuccess) e = dalloc(h, &h->counters, (size_t)KD_NUM + 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->counters, 0, (KD_NUM + 4) * sizeof(unsigned int), h->stream);
+  h->jobs_host.resize(4 * KD_NUM);
+  for (int b = 0; b < 2; ++b)
+    for (int pb = 0; pb < 2; ++pb)
+      for (int kd = 0; kd < KD_NUM; ++kd)
+        h->jobs_host[(2 * b + pb) * KD_NUM + kd] = make_job(h, kd, b, pb, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->jobs_dev, h->jobs_host.data(), h->jobs_host.size() * sizeof(JobArgs),
+                        cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->disp, pr->disparity, p * sizeof(float), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->sc, 0, 2 * sizeof(DevScalars), h->stream);
@@ -482,9 +614,16 @@ void lfsr_destroy(lfsr_handle* h) {
 const char* lfsr_last_error(const lfsr_handle* h) { return h ? h->err.c_str() : t_err.c_str(); }
 
 int lfsr_load(lfsr_handle* h, const float* lr_views, const float* x0, int mem) {
+  return load_state(h, lr_views, x0, mem, 0);
+}
+
+}  // extern "C"
+
+int lfsr::load_state(lfsr_handle* h, const float* lr_views, const float* x0, int mem, int parity) {
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
   if (!lr_views || !x0) return fail(h, LFSR_EINVAL, "lr_views and x0 are required");
   if (check_mem(h, mem)) return LFSR_EINVAL;
+  const int b = parity & 1;
   CK(h, scalars_reset(h->sc, h->stream), "reset scalars");
   if (h->g.st_y == ST_F32) {
     CK(h, to_dev(h, (float*)h->y, lr_views, h->nA, mem), "upload views");
@@ -496,14 +635,16 @@ int lfsr_load(lfsr_handle* h, const float* lr_views, const float* x0, int mem) {
     }
     CK(h, to_storage(h->g.st_y, src, h->y, h->nA, h->sc, h->grid_vec, h->stream), "store views");
   }
-  CK(h, to_dev(h, h->x[0], x0, h->p, mem), "upload x0");
-  CK(h, cudaMemsetAsync(h->wA[0], 0, h->nA * h->esize, h->stream), "clear data duals");
-  CK(h, cudaMemsetAsync(h->wS[0], 0, h->nSpair * h->esize, h->stream), "clear NLTV duals");
-  h->parity = 0;
+  CK(h, to_dev(h, h->x[b], x0, h->p, mem), "upload x0");
+  CK(h, cudaMemsetAsync(h->wA[b], 0, h->nA * h->esize, h->stream), "clear data duals");
+  CK(h, cudaMemsetAsync(h->wS[b], 0, h->nSpair * h->esize, h->stream), "clear NLTV duals");
+  h->parity = b;
   h->iters = 0;
   h->launches = 0;
   return LFSR_OK;
 }
+
+extern "C" {
 
 int lfsr_iterate(lfsr_handle* h, int iterations) {
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
@@ -656,15 +797,30 @@ int lfsr_apply_A(lfsr_handle* h, int view, const float* x, float* out, int mem) 
     xs = h->Q;
     os = h->io;
   }
-  OpArgs a{};
-  a.src = xs;
-  a.disp = h->disp;
-  a.out = os - (size_t)(view < 0 ? 0 : view) * h->q;  // kernel indexes out by view
-  a.view0 = view < 0 ? 0 : view;
-  a.nviews = nv;
-  a.units = h->op.n_tiles * nv;
-  a.sc = h->sc + 1;
-  CK(h, op_launch(OP_FWD, h->g, h->op, a, op_grid(h->op, a.units, h->sm_count), h->stream), "apply A");
+  if (h->op.fast) {
+    JobArgs j = standalone_job(h);
+    j.tiles_x = h->op.tiles_x;
+    j.view0 = view < 0 ? 0 : view;
+    j.nviews = nv;
+    j.units = h->op.n_tiles * ((nv + FAST_VIEWS - 1) / FAST_VIEWS);
+    j.src = xs;
+    j.out = os - (size_t)j.view0 * h->q;   // the kernel indexes out by view
+    TableArgs t;
+    CK(h, scratch_table(h, 0, j, RED_OP, &t), "operator table");
+    CK(h, fast_launch(OP_FWD, h->g, h->op, t, op_grid(h->op, j.units, h->sm_count), h->stream, &j),
+       "apply A");
+  } else {
+    OpArgs a{};
+    a.src = xs;
+    a.disp = h->disp;
+    a.out = os - (size_t)(view < 0 ? 0 : view) * h->q;  // kernel indexes out by view
+    a.view0 = view < 0 ? 0 : view;
+    a.nviews = nv;
+    a.units = h->op.n_tiles * nv;
+    a.sc = h->sc + 1;
+    CK(h, op_launch(OP_FWD, h->g, h->op, a, op_grid(h->op, a.units, h->sm_count), h->stream),
+       "apply A");
+  }
   if (mem == LFSR_MEM_HOST) CK(h, from_dev(h, out, h->io, (size_t)nv * h->q, mem), "download");
   CK(h, cudaStreamSynchronize(h->stream), "synchronize");
   return LFSR_OK;
@@ -684,16 +840,32 @@ int lfsr_apply_AT(lfsr_handle* h, int view, const float* gin, float* out, int me
     os = h->Q;
   }
   CK(h, cudaMemsetAsync(os, 0, h->p * sizeof(float), h->stream), "clear out");
-  OpArgs a{};
-  a.src = gs - (size_t)(view < 0 ? 0 : view) * h->q;
-  a.disp = h->disp;
-  a.out = os;
-  a.scale = 1.f;
-  a.view0 = view < 0 ? 0 : view;
-  a.nviews = nv;
-  a.units = h->op.n_tiles * nv;
-  a.sc = h->sc + 1;
-  CK(h, op_launch(OP_ADJ, h->g, h->op, a, op_grid(h->op, a.units, h->sm_count), h->stream), "apply A^T");
+  if (h->op.fast) {
+    JobArgs j = standalone_job(h);
+    j.tiles_x = h->op.tiles_x;
+    j.view0 = view < 0 ? 0 : view;
+    j.nviews = nv;
+    j.units = h->op.n_tiles * ((nv + FAST_VIEWS - 1) / FAST_VIEWS);
+    j.scale = 1.f;
+    j.src = gs - (size_t)j.view0 * h->q;
+    j.out = os;
+    TableArgs t;
+    CK(h, scratch_table(h, 0, j, RED_OP, &t), "operator table");
+    CK(h, fast_launch(OP_ADJ, h->g, h->op, t, op_grid(h->op, j.units, h->sm_count), h->stream, &j),
+       "apply A^T");
+  } else {
+    OpArgs a{};
+    a.src = gs - (size_t)(view < 0 ? 0 : view) * h->q;
+    a.disp = h->disp;
+    a.out = os;
+    a.scale = 1.f;
+    a.view0 = view < 0 ? 0 : view;
+    a.nviews = nv;
+    a.units = h->op.n_tiles * nv;
+    a.sc = h->sc + 1;
+    CK(h, op_launch(OP_ADJ, h->g, h->op, a, op_grid(h->op, a.units, h->sm_count), h->stream),
+       "apply A^T");
+  }
   if (mem == LFSR_MEM_HOST) CK(h, from_dev(h, out, h->Q, h->p, mem), "download");
   CK(h, cudaStreamSynchronize(h->stream), "synchronize");
   return LFSR_OK;
@@ -711,14 +883,21 @@ int lfsr_weights(lfsr_handle* h, const float* x, float* w, int mem) {
     ws = h->io;
   }
   CK(h, cudaMemsetAsync(ws, 0, h->nS * sizeof(float), h->stream), "clear w");
-  NlArgs a{};
-  a.x = xs;
-  a.out = ws;
-  a.sc = h->sc + 1;
   if (h->nlf) {
-    CK(h, nlw2_launch(0, h->g, h->nl, a, h->wt, nullptr, h->stream), "weights");
+    JobArgs j = standalone_job(h);
+    j.tiles_x = h->nl_tiles_x;
+    j.units = h->nl_units;
+    j.src = xs;
+    j.wt = h->wt;
+    TableArgs t;
+    CK(h, scratch_table(h, 0, j, RED_NLTV, &t), "NLTV table");
+    CK(h, nlw2_launch(0, h->g, t, h->stream), "weights");
     CK(h, weights_to_canonical(h->g, h->wt, ws, h->stream), "weights layout");
   } else {
+    NlArgs a{};
+    a.x = xs;
+    a.out = ws;
+    a.sc = h->sc + 1;
     CK(h, nl_launch(NL_WEIGHTS, h->g, h->nl, a, h->stream), "weights");
   }
   if (mem == LFSR_MEM_HOST) CK(h, from_dev(h, w, h->io, h->nS, mem), "download");
@@ -742,32 +921,57 @@ int lfsr_apply_normal(lfsr_handle* h, const float* xw, const float* p, float* qo
     qs = h->io + 2 * h->p;
   }
   DevScalars* sc = h->sc + 1;
-  NlArgs na{};
-  na.x = xs;
-  na.p_old = ps;
-  na.out = qs;
-  na.partials = part_slot(h, RED_NLTV);
-  na.sc = sc;
   if (h->nlf) {
-    NlArgs wa{};
-    wa.x = xs;
-    wa.sc = sc;
-    CK(h, nlw2_launch(0, h->g, h->nl, wa, h->wt, nullptr, h->stream), "normal (weights)");
-    CK(h, nla2_launch(h->g, h->nl, na, h->wt, h->stream), "normal (NLTV part)");
+    JobArgs jw = standalone_job(h);   // weights of xw
+    jw.tiles_x = h->nl_tiles_x;
+    jw.units = h->nl_units;
+    jw.src = xs;
+    jw.wt = h->wt;
+    JobArgs ja = jw;                  // q := mu S^T W^2 S p
+    ja.src = nullptr;
+    ja.use_beta = 0;
+    ja.p_old = ps;
+    ja.out = qs;
+    TableArgs tw, ta;
+    CK(h, scratch_table(h, 0, jw, RED_NLTV, &tw), "NLTV table");
+    CK(h, scratch_table(h, 1, ja, RED_NLTV, &ta), "NLTV table");
+    CK(h, nlw2_launch(0, h->g, tw, h->stream), "normal (weights)");
+    CK(h, nla2_launch(h->g, ta, h->stream), "normal (NLTV part)");
   } else {
+    NlArgs na{};
+    na.x = xs;
+    na.p_old = ps;
+    na.out = qs;
+    na.partials = part_slot(h, RED_NLTV);
+    na.sc = sc;
     CK(h, nl_launch(NL_APPLY, h->g, h->nl, na, h->stream), "normal (NLTV part)");
   }
-  OpArgs on{};
-  on.src = ps;
-  on.disp = h->disp;
-  on.out = qs;
-  on.scale = h->g.cA;
-  on.view0 = 0;
-  on.nviews = h->g.sk;
-  on.units = h->op.n_tiles * h->g.sk;
-  on.partials = part_slot(h, RED_OP);
-  on.sc = sc;
-  CK(h, op_launch(OP_NORMAL, h->g, h->op, on, h->grid_op, h->stream), "normal (operator part)");
+  if (h->op.fast) {
+    JobArgs j = standalone_job(h);
+    j.tiles_x = h->op.tiles_x;
+    j.view0 = 0;
+    j.nviews = h->g.sk;
+    j.units = h->op_units;
+    j.scale = h->g.cA;
+    j.src = ps;
+    j.out = qs;
+    TableArgs t;
+    CK(h, scratch_table(h, 2, j, RED_OP, &t), "operator table");
+    CK(h, fast_launch(OP_NORMAL, h->g, h->op, t, h->grid_op, h->stream, &j),
+       "normal (operator part)");
+  } else {
+    OpArgs on{};
+    on.src = ps;
+    on.disp = h->disp;
+    on.out = qs;
+    on.scale = h->g.cA;
+    on.view0 = 0;
+    on.nviews = h->g.sk;
+    on.units = h->op.n_tiles * h->g.sk;
+    on.partials = part_slot(h, RED_OP);
+    on.sc = sc;
+    CK(h, op_launch(OP_NORMAL, h->g, h->op, on, h->grid_op, h->stream), "normal (operator part)");
+  }
   if (mem == LFSR_MEM_HOST) CK(h, from_dev(h, qo, qs, h->p, mem), "download q");
   DevScalars hs;
   CK(h, cudaMemcpyAsync(&hs, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream), "read");

@@ -1,0 +1,95 @@
+// Private to liblfsr: the solver state of one light field (lfsr_handle) and
+// the helpers that the batch entry points share with the single-light-field
+// ones.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "lfsr.h"
+#include "lfsr_internal.cuh"
+
+namespace lfsr {
+
+struct ProfEvent {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+// Launch kinds of one ADMM iteration, in schedule order (also the profiling
+// classes of lfsr_stats_t): NLTV block, data block, x-step init, then per CG
+// step NLTV apply, normal-matrix operator, CG update.
+enum { KD_NLW = 0, KD_DATA = 1, KD_INIT = 2, KD_NLA = 3, KD_NORMAL = 4, KD_UPDATE = 5, KD_NUM = 6 };
+
+}  // namespace lfsr
+
+struct lfsr_handle {
+  lfsr_params prm{};
+  lfsr::Geom g{};
+  lfsr::OpPlan op{};
+  lfsr::NlPlan nl{};
+  cudaStream_t stream = nullptr;      // caller's stream
+  cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+  int device = 0, sm_count = 0;
+  size_t p = 0, q = 0, nA = 0, nS = 0, nSpair = 0;
+  int grid_op = 0, grid_vec = 0, max_grid = 0;
+  // device buffers
+  float* disp = nullptr;
+  float* x[2] = {nullptr, nullptr};
+  float* R = nullptr;   // v, then the CG residual r
+  float* P[2] = {nullptr, nullptr};
+  float* Q = nullptr;
+  float* cb = nullptr;  // per-edge divergence terms of the z/w-step [s_d/2][p]
+  // streams in the storage kind g.st (float, half or bfloat16), esize bytes
+  // each; the views in kind g.st_y (esize_y bytes)
+  size_t esize = 4, esize_y = 4;
+  void* y = nullptr;
+  void* wA[2] = {nullptr, nullptr};
+  void* wS[2] = {nullptr, nullptr};
+  void* wt = nullptr;   // stored NLTV edge weights [s_d/2][p] (when supported)
+  bool nlf = false;
+  float* io = nullptr;  // staging for host <-> device and layout conversion
+  size_t io_floats = 0;
+  double* partials = nullptr;
+  lfsr::DevScalars* sc = nullptr;  // [0] solver, [1] standalone operator calls
+  int64_t state_bytes = 0;
+  // schedule state
+  int parity = 0;
+  int iters = 0;
+  int64_t launches = 0;
+  cudaGraphExec_t graph_pair = nullptr;     // iterations at parity 0 then 1
+  cudaGraphExec_t graph_single[2] = {nullptr, nullptr};
+  // table-driven launches (specialised operator, stored-weight NLTV, CG
+  // vector kernels): one JobArgs per (iteration parity b, CG direction
+  // parity pb, kind), entry (2 b + pb) KD_NUM + kind
+  std::vector<lfsr::JobArgs> jobs_host;     // host copies (by-value operator launches)
+  lfsr::JobArgs* jobs_dev = nullptr;
+  lfsr::JobArgs* jobs_scratch = nullptr;    // standalone operator calls: 4 entries
+  unsigned int* counters = nullptr;         // arrival counters: KD_NUM + 4
+  int nl_tiles_x = 0, nl_units = 0;         // 32 x 32 NLTV tiles
+  int op_units = 0;                         // (64 x 64 tile, view pair) units
+  int vec_chunk = 0, vec_units = 0;         // HR pixels per vector-kernel CTA, CTAs
+  bool profiling = false;
+  std::vector<lfsr::ProfEvent> prof;
+  double prof_ms[8] = {0};
+  int64_t prof_n[8] = {0};
+  std::string err = "no error";
+};
+
+namespace lfsr {
+
+// JobArgs of launch `kind` of an iteration at parity b (reads state b,
+// writes state 1 - b) and CG direction parity pb, for a table whose first
+// unit of this light field is unit0.
+JobArgs make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0);
+// Work units of a launch kind for this light field.
+int kind_units(const lfsr_handle* h, int kind);
+// Reduction slot (RED_*) of a launch kind.
+int kind_slot(int kind);
+// lfsr_load into state `parity` (x[parity] := x0, duals[parity] := 0).
+int load_state(lfsr_handle* h, const float* lr_views, const float* x0, int mem, int parity);
+// Records an error on h (and the thread) and returns code.
+int handle_fail(lfsr_handle* h, int code, const std::string& msg);
+int handle_cuda_fail(lfsr_handle* h, cudaError_t e, const char* what);
+
+}  // namespace lfsr

@@ -147,4 +147,57 @@ __device__ __forceinline__ bool grid_sum_last(double part, double* partials, uns
   return true;
 }
 
+// Reductions of the table-driven kernels.  Every CTA writes its partial
+// slot(s) and then arrives here; the CTA that arrives last gets true and may
+// then read every slot (fenced).  The counter is re-armed for the next launch.
+__device__ __forceinline__ bool table_arrive_last(unsigned int* counter) {
+  __shared__ int am_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(counter, 1u);
+    am_last = (t == gridDim.x - 1);
+    if (am_last) *counter = 0u;   // every CTA has arrived
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  return true;
+}
+
+// Sum of n slots by one warp in a fixed order; the total in every lane.
+__device__ __forceinline__ double warp_sum_slots(const double* slots, int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += ((const volatile double*)slots)[i];
+  s = warp_sum(s);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+
+// x-step initialisation totals (Algorithm 2), per light field of the table:
+// pi = <r, r> from the unit slots and a fresh CG state.  Run by the last CTA.
+template <int NT>
+__device__ __forceinline__ void cg_init_finalize(const Geom& g, const TableArgs& tb) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = warp; j < tb.n_jobs; j += NT / 32) {
+    const JobArgs* jj = tb.jobs + j;
+    const double total = warp_sum_slots(tb.partials + jj->unit0, jj->units);
+    if (lane == 0) {
+      DevScalars* sc = jj->sc;
+      sc->pi = total;
+      sc->cg_first = 1;
+      sc->cg_steps = 0;
+      sc->beta = 0.0;
+      sc->dw2 = sc->dwA + sc->dwS;
+      if (!isfinite(total)) set_status(sc, -4);  // LFSR_ENUMERIC
+      sc->cg_done = (total > g.tau && isfinite(total)) ? 0 : 1;
+    }
+  }
+}
+
+// Table entry of work unit u.
+__device__ __forceinline__ int table_job(const TableArgs& t, int u) {
+  return t.unit_job ? __ldg(t.unit_job + u) : 0;
+}
+
 }  // namespace lfsr

@@ -108,6 +108,52 @@ struct NlArgs {
   int check_done;
 };
 
+// One light field's share of a launch of a table-driven kernel (the
+// specialised operator kernel, the stored-weight NLTV kernels and the CG
+// vector kernels).  Each launch reads a device table of these, one entry per
+// light field, so one launch covers many light fields of different sizes;
+// a single solve is a table of one.  Pointers are this light field's
+// buffers in the roles of this launch.
+struct JobArgs {
+  int H, W, Hh, Wh, U, V;     // geometry
+  int unit0, units;           // work units of this light field: [unit0, unit0 + units)
+  int tiles_x;                // tile columns (operator: 64 x 64, NLTV: 32 x 32 HR pixels)
+  int chunk;                  // vector kernels: HR pixels per unit
+  int view0, nviews;          // operator: views of this launch
+  float scale;                // operator: factor of the flushed accumulator
+  int use_beta;               // NLTV apply: p_new = r + beta p_old (else p_old is the direction)
+  const float* disp;          // HR disparity
+  const float* src;           // operator: x or p (HR), g (LR, adjoint); NLTV: weights source x;
+                              // vector init: x
+  float* out;                 // operator: HR accumulator or LR output; NLTV block: v;
+                              // NLTV apply: q; vector init: v, replaced by r = -v
+  const void* y;              // operator DATA: views (kind g.st_y)
+  const void* wA_old;         // operator DATA: data duals (kind g.st)
+  void* wA_new;
+  const void* wS_old;         // NLTV block: regulariser duals, pair layout (kind g.st)
+  void* wS_new;
+  void* wt;                   // NLTV: stored edge weights (kind g.st)
+  float* cb;                  // NLTV block -> vector init: per-edge divergence terms
+  const float* r;             // NLTV apply: CG residual
+  const float* p_old;         // NLTV apply: previous direction; vector update: p
+  float* p_new;               // NLTV apply: new direction
+  const float* q;             // vector update: M p
+  float* rr;                  // vector update: residual r, updated in place
+  float* x_next;              // vector: iterate of the x-step
+  DevScalars* sc;             // this light field's device scalars
+};
+
+// Launch-wide arguments of a table-driven kernel.
+struct TableArgs {
+  const JobArgs* jobs;        // device table
+  const int* unit_job;        // unit -> table index (NULL: every unit is entry 0)
+  int n_jobs;
+  int total_units;
+  int check_done;             // CG steps: skip light fields whose x-step has finished
+  double* partials;           // reduction slots
+  unsigned int* counter;      // arrival counter of the grid reduction (re-armed by the kernel)
+};
+
 struct NlPlan {
   int TH, TW, tiles_x, tiles_y, n_tiles;
   int NXr, NXc;          // staged x region
@@ -139,30 +185,36 @@ cudaError_t nl_plan(const Geom& g, NlPlan* plan, int smem_limit);
 
 // NLTV with stored edge weights (window radius 1-3, patch radius 0-2).
 bool nlf_supported(const Geom& g);
-// wt holds s_d/2 x p values of the storage kind g.st; cb s_d/2 x p floats.
+// Table-driven: one CTA per 32 x 32 tile (t.total_units tiles); wt holds
+// s_d/2 x p values of the storage kind g.st, cb s_d/2 x p floats.
+constexpr int NLF_TILE = 32;
 cudaError_t weights_to_canonical(const Geom& g, const void* wt, float* can, cudaStream_t s);
-cudaError_t nlw2_launch(int block, const Geom& g, const NlPlan& P, const NlArgs& a, void* wt,
-                        float* cb, cudaStream_t s);
-cudaError_t nla2_launch(const Geom& g, const NlPlan& P, const NlArgs& a, const void* wt,
-                        cudaStream_t s);
-cudaError_t cg_init_nltv_launch(const Geom& g, float* rv, const float* cb, const float* x,
-                                float* x_next, double* partials, DevScalars* sc, int grid,
-                                cudaStream_t s);
+cudaError_t nlw2_launch(int block, const Geom& g, const TableArgs& t, cudaStream_t s);
+cudaError_t nla2_launch(const Geom& g, const TableArgs& t, cudaStream_t s);
+cudaError_t cg_init_nltv_launch(const Geom& g, const TableArgs& t, cudaStream_t s);
 
 // Specialised operator kernel for separable kernels of common (zeta, kb).
 bool fast_supported(const Geom& g);
 cudaError_t fast_prepare(const Geom& g, int smem_optin);
 cudaError_t fast_plan(const Geom& g, OpPlan* plan, int smem_limit);
-cudaError_t fast_launch(int mode, const Geom& g, const OpPlan& plan, const OpArgs& a, int grid,
-                        cudaStream_t s);
+// Table-driven: t.total_units (64 x 64 tile, view pair) units over `grid`
+// CTAs; the partial slots are t.n_jobs x grid.
+constexpr int FAST_TILE = 64;
+constexpr int FAST_VIEWS = 2;
+// single != NULL: one light field, its fields by value (t.jobs unused);
+// else the table t (data block and normal-matrix modes).
+cudaError_t fast_launch(int mode, const Geom& g, const OpPlan& plan, const TableArgs& t, int grid,
+                        cudaStream_t s, const JobArgs* single);
+cudaError_t fast_launch_table(int mode, const Geom& g, const OpPlan& plan, const TableArgs& t,
+                              int grid, cudaStream_t s);
+cudaError_t fast_prepare_table(int zeta, int kb, int smem_optin);
 cudaError_t nl_launch(int mode, const Geom& g, const NlPlan& plan, const NlArgs& a,
                       cudaStream_t s);
 
-cudaError_t cg_init_launch(const Geom& g, float* r_inout_v, const float* x, float* x_next,
-                           double* partials_pi, DevScalars* sc, int grid, cudaStream_t s);
-cudaError_t cg_update_launch(const Geom& g, const float* p, const float* q, float* x_next,
-                             float* r, double* partials_pi, DevScalars* sc, int grid,
-                             cudaStream_t s);
+// Table-driven vector kernels: one CTA per chunk of HR pixels.
+constexpr int VEC_THREADS = 512;
+cudaError_t cg_init_launch(const Geom& g, const TableArgs& t, cudaStream_t s);
+cudaError_t cg_update_launch(const Geom& g, const TableArgs& t, cudaStream_t s);
 // Regulariser duals: canonical float [d][u] <-> edge-pair layout of kind g.st.
 cudaError_t pair_from_canonical(const Geom& g, const float* can, void* pair, cudaStream_t s);
 cudaError_t pair_to_canonical(const Geom& g, const void* pair, float* can, cudaStream_t s);

@@ -19,22 +19,30 @@ namespace lfsr {
 // k_nlw2<ONLY>: the weights alone.
 template <int MODE, int WR, int PR, class ST>
 __global__ void __launch_bounds__(NF_THREADS)
-k_nlw2(const Geom g, const NlPlan P, const NlArgs a, ST* __restrict__ wt, float* __restrict__ cb) {
+k_nlw2(const Geom g, const TableArgs tb) {
   using D = HalfDirs<WR>;
-  const ST* __restrict__ wS_old = (const ST*)a.wS_old;
-  ST* __restrict__ wS_new = (ST*)a.wS_new;
   constexpr int T = NF_T, HX = WR + PR, NX = T + 2 * HX, NXp = NX | 1;
   constexpr int PW = 2 * PR + 1, NS = NF_PIX + 2 * PR;
   __shared__ float sX[NX * NXp];
+  __shared__ double s_red[NF_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int Hh = g.Hh, Wh = g.Wh;
+  // this CTA's tile: unit blockIdx.x of the table
+  const JobArgs* jp = tb.jobs + table_job(tb, blockIdx.x);
+  const int Hh = jp->Hh, Wh = jp->Wh;
+  const float* __restrict__ x = jp->src;
+  float* __restrict__ vout = jp->out;
+  const ST* __restrict__ wS_old = (const ST*)jp->wS_old;
+  ST* __restrict__ wS_new = (ST*)jp->wS_new;
+  ST* __restrict__ wt = (ST*)jp->wt;
+  float* __restrict__ cb = jp->cb;
   const size_t p = (size_t)Hh * Wh;
-  const int ty = blockIdx.x / P.tiles_x, tx = blockIdx.x - ty * P.tiles_x;
+  const int tile = blockIdx.x - jp->unit0;
+  const int ty = tile / jp->tiles_x, tx = tile - ty * jp->tiles_x;
   const int i0 = ty * T, j0 = tx * T;
   for (int t = tid; t < NX * NX; t += NF_THREADS) {
     const int rr = t / NX, cc = t - rr * NX;
     const int hi = clampi(i0 - HX + rr, 0, Hh - 1), hj = clampi(j0 - HX + cc, 0, Wh - 1);
-    sX[rr * NXp + cc] = __ldg(a.x + (size_t)hi * Wh + hj);
+    sX[rr * NXp + cc] = __ldg(x + (size_t)hi * Wh + hj);
   }
   __syncthreads();
   const int ju = lane, uj = j0 + ju;
@@ -44,7 +52,7 @@ k_nlw2(const Geom g, const NlPlan P, const NlArgs a, ST* __restrict__ wt, float*
 #pragma unroll
     for (int m = 0; m < NF_PIX; ++m) {
       const int ui = i0 + iu0 + m;
-      if (ui < Hh) a.out[(size_t)ui * Wh + uj] = 0.f;
+      if (ui < Hh) vout[(size_t)ui * Wh + uj] = 0.f;
     }
   }
   float psum = 0.f;
@@ -114,21 +122,27 @@ k_nlw2(const Geom g, const NlPlan P, const NlArgs a, ST* __restrict__ wt, float*
     }
   }
   if (MODE == NLW_BLOCK) {
-    double total = 0.0;
-    if (grid_sum_last<NF_THREADS>((double)psum, a.partials, &a.sc->counter[RED_DW_S], &total) &&
-        threadIdx.x == 0) {
-      a.sc->red[RED_DW_S] = total;
-      a.sc->dwS = total;
+    // |w_S' - w_S|^2 per light field: one slot per tile, summed by the last CTA
+    const double bs = block_sum<NF_THREADS>((double)psum, s_red);
+    if (tid == 0) tb.partials[blockIdx.x] = bs;
+    if (table_arrive_last(tb.counter)) {
+      for (int j = warp; j < tb.n_jobs; j += NF_THREADS / 32) {
+        const JobArgs* jj = tb.jobs + j;
+        const double total = warp_sum_slots(tb.partials + jj->unit0, jj->units);
+        if (lane == 0) {
+          jj->sc->red[RED_DW_S] = total;
+          jj->sc->dwS = total;
+        }
+      }
     }
   }
 }
 
 template <int MODE, class ST>
-static cudaError_t nlw2_dispatch(const Geom& g, const NlPlan& P, const NlArgs& a, ST* wt,
-                                 float* cb, cudaStream_t s) {
+static cudaError_t nlw2_dispatch(const Geom& g, const TableArgs& t, cudaStream_t s) {
 #define NLW2_CASE(wr, pr)                                                          \
   if (g.win_r == wr && g.patch_r == pr) {                                          \
-    k_nlw2<MODE, wr, pr, ST><<<P.n_tiles, NF_THREADS, 0, s>>>(g, P, a, wt, cb);    \
+    k_nlw2<MODE, wr, pr, ST><<<t.total_units, NF_THREADS, 0, s>>>(g, t);           \
     return cudaGetLastError();                                                     \
   }
   NLW2_CASE(1, 0) NLW2_CASE(1, 1) NLW2_CASE(1, 2)
@@ -139,18 +153,16 @@ static cudaError_t nlw2_dispatch(const Geom& g, const NlPlan& P, const NlArgs& a
 }
 
 template <class ST>
-static cudaError_t nlw2_st(int block, const Geom& g, const NlPlan& P, const NlArgs& a, void* wt,
-                           float* cb, cudaStream_t s) {
-  return block ? nlw2_dispatch<NLW_BLOCK, ST>(g, P, a, (ST*)wt, cb, s)
-               : nlw2_dispatch<NLW_ONLY, ST>(g, P, a, (ST*)wt, cb, s);
+static cudaError_t nlw2_st(int block, const Geom& g, const TableArgs& t, cudaStream_t s) {
+  return block ? nlw2_dispatch<NLW_BLOCK, ST>(g, t, s) : nlw2_dispatch<NLW_ONLY, ST>(g, t, s);
 }
 
-cudaError_t nlw2_launch(int block, const Geom& g, const NlPlan& P, const NlArgs& a, void* wt,
-                        float* cb, cudaStream_t s) {
+cudaError_t nlw2_launch(int block, const Geom& g, const TableArgs& t, cudaStream_t s) {
+  if (t.total_units < 1) return cudaErrorInvalidValue;
   switch (g.st) {
-    case ST_F32: return nlw2_st<float>(block, g, P, a, wt, cb, s);
-    case ST_F16: return nlw2_st<__half>(block, g, P, a, wt, cb, s);
-    case ST_BF16: return nlw2_st<__nv_bfloat16>(block, g, P, a, wt, cb, s);
+    case ST_F32: return nlw2_st<float>(block, g, t, s);
+    case ST_F16: return nlw2_st<__half>(block, g, t, s);
+    case ST_BF16: return nlw2_st<__nv_bfloat16>(block, g, t, s);
     default: return cudaErrorInvalidValue;
   }
 }

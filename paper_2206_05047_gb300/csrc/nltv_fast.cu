@@ -12,31 +12,39 @@ namespace lfsr {
 // with <p, q>'s NLTV part sum_d w(u,u+d)^2 (p(u) - p(u+d))^2 (each edge once).
 template <int WR, class ST>
 __global__ void __launch_bounds__(NF_THREADS)
-k_nla2(const Geom g, const NlPlan P, const NlArgs a, const ST* __restrict__ wt) {
+k_nla2(const Geom g, const TableArgs tb) {
   using D = HalfDirs<WR>;
   constexpr int T = NF_T, NP = T + 2 * WR, NPp = NP | 1;
   __shared__ float sP[NP * NPp];
-  if (a.check_done && a.sc->cg_done) return;
+  __shared__ double s_red[NF_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int Hh = g.Hh, Wh = g.Wh;
+  // this CTA's tile: unit blockIdx.x of the table
+  const JobArgs* jp = tb.jobs + table_job(tb, blockIdx.x);
+  DevScalars* sc = jp->sc;
+  const bool skip = tb.check_done && ((volatile int*)&sc->cg_done)[0];
+  float psum = 0.f;
+  if (!skip) {
+  const int Hh = jp->Hh, Wh = jp->Wh;
   const size_t p = (size_t)Hh * Wh;
-  const int ty = blockIdx.x / P.tiles_x, tx = blockIdx.x - ty * P.tiles_x;
+  const ST* __restrict__ wt = (const ST*)jp->wt;
+  const int tile = blockIdx.x - jp->unit0;
+  const int ty = tile / jp->tiles_x, tx = tile - ty * jp->tiles_x;
   const int i0 = ty * T, j0 = tx * T;
   const int TRr = min(T, Hh - i0), TRc = min(T, Wh - j0);
-  const int first = a.sc->cg_first;
-  const float beta = (float)a.sc->beta;
+  const int first = sc->cg_first;
+  const float beta = (float)sc->beta;
   for (int t = tid; t < NP * NP; t += NF_THREADS) {
     const int rr = t / NP, cc = t - rr * NP;
     const int hi = i0 - WR + rr, hj = j0 - WR + cc;
     float v = 0.f;
     if (hi >= 0 && hi < Hh && hj >= 0 && hj < Wh) {
       const size_t gi = (size_t)hi * Wh + hj;
-      if (a.use_beta) {
-        v = __ldg(a.r + gi);
-        if (!first) v = fmaf(beta, __ldg(a.p_old + gi), v);
-        if (rr >= WR && rr < WR + TRr && cc >= WR && cc < WR + TRc) a.p_new[gi] = v;
+      if (jp->use_beta) {
+        v = __ldg(jp->r + gi);
+        if (!first) v = fmaf(beta, __ldg(jp->p_old + gi), v);
+        if (rr >= WR && rr < WR + TRr && cc >= WR && cc < WR + TRc) jp->p_new[gi] = v;
       } else {
-        v = __ldg(a.p_old + gi);
+        v = __ldg(jp->p_old + gi);
       }
     }
     sP[rr * NPp + cc] = v;
@@ -48,7 +56,6 @@ k_nla2(const Geom g, const NlPlan P, const NlArgs a, const ST* __restrict__ wt) 
   float acc[NF_PIX];
 #pragma unroll
   for (int m = 0; m < NF_PIX; ++m) acc[m] = 0.f;
-  float psum = 0.f;
   // directions in chunks of DB: all weight loads of a chunk are issued
   // before any is used (memory-level parallelism)
   constexpr int DB = 6;
@@ -93,28 +100,42 @@ k_nla2(const Geom g, const NlPlan P, const NlArgs a, const ST* __restrict__ wt) 
 #pragma unroll
   for (int m = 0; m < NF_PIX; ++m) {
     const int ui = i0 + iu0 + m;
-    if (ui < Hh && col_in) a.out[(size_t)ui * Wh + uj] = g.mu * acc[m];
+    if (ui < Hh && col_in) jp->out[(size_t)ui * Wh + uj] = g.mu * acc[m];
   }
-  double total = 0.0;
-  if (grid_sum_last<NF_THREADS>((double)psum, a.partials, &a.sc->counter[RED_NLTV], &total) &&
-      threadIdx.x == 0)
-    a.sc->red[RED_NLTV] = total;
+  }  // !skip
+  // NLTV part of <p, M p> per light field: one slot per tile
+  const double bs = block_sum<NF_THREADS>((double)psum, s_red);
+  if (tid == 0) tb.partials[blockIdx.x] = bs;
+  if (table_arrive_last(tb.counter)) {
+    for (int j = warp; j < tb.n_jobs; j += NF_THREADS / 32) {
+      const JobArgs* jj = tb.jobs + j;
+      const double total = warp_sum_slots(tb.partials + jj->unit0, jj->units);
+      if (lane == 0) jj->sc->red[RED_NLTV] = total;
+    }
+  }
 }
 
 // x-step initialisation (Algorithm 2) with the regulariser divergence of
 // the z/w-step folded in: v = v_data + mu/2 sum_d (c(u,d) - c(u-d,d));
 // r = -v; x' = x; pi = <r, r>.
 template <int WR>
-__global__ void __launch_bounds__(512)
-k_cg_init_nltv(const Geom g, float* __restrict__ rv, const float* __restrict__ cb,
-               const float* __restrict__ x, float* __restrict__ x_next, double* partials,
-               DevScalars* sc) {
+__global__ void __launch_bounds__(VEC_THREADS)
+k_cg_init_nltv(const Geom g, const TableArgs tb) {
   using D = HalfDirs<WR>;
-  const int Hh = g.Hh, Wh = g.Wh;
+  __shared__ double s_red[VEC_THREADS / 32];
+  // this CTA's chunk of HR pixels: unit blockIdx.x of the table
+  const JobArgs* jp = tb.jobs + table_job(tb, blockIdx.x);
+  const int Hh = jp->Hh, Wh = jp->Wh;
   const size_t n = (size_t)Hh * Wh;
+  float* __restrict__ rv = jp->out;
+  const float* __restrict__ cb = jp->cb;
+  const float* __restrict__ x = jp->src;
+  float* __restrict__ x_next = jp->x_next;
+  const size_t c0 = (size_t)(blockIdx.x - jp->unit0) * jp->chunk;
+  const size_t c1 = min(n, c0 + (size_t)jp->chunk);
   const float half_mu = 0.5f * g.mu;
   double part = 0.0;
-  for (size_t i = (size_t)blockIdx.x * 512 + threadIdx.x; i < n; i += (size_t)gridDim.x * 512) {
+  for (size_t i = c0 + threadIdx.x; i < c1; i += VEC_THREADS) {
     const int ui = (int)(i / Wh), uj = (int)(i - (size_t)ui * Wh);
     float div = 0.f;
     constexpr int DB = 8;
@@ -139,16 +160,9 @@ k_cg_init_nltv(const Geom g, float* __restrict__ rv, const float* __restrict__ c
     x_next[i] = x[i];
     part += (double)r * (double)r;
   }
-  double total = 0.0;
-  if (grid_sum_last<512>(part, partials, &sc->counter[RED_PI], &total) && threadIdx.x == 0) {
-    sc->pi = total;
-    sc->cg_first = 1;
-    sc->cg_steps = 0;
-    sc->beta = 0.0;
-    sc->dw2 = sc->dwA + sc->dwS;
-    if (!isfinite(total)) set_status(sc, -4);  // LFSR_ENUMERIC
-    sc->cg_done = (total > g.tau && isfinite(total)) ? 0 : 1;
-  }
+  const double bs = block_sum<VEC_THREADS>(part, s_red);
+  if (threadIdx.x == 0) tb.partials[blockIdx.x] = bs;
+  if (table_arrive_last(tb.counter)) cg_init_finalize<VEC_THREADS>(g, tb);
 }
 
 // canonical weights [d][u] from the stored edge weights wt[idx][u]
@@ -181,34 +195,32 @@ bool nlf_supported(const Geom& g) {
 }
 
 template <class ST>
-static cudaError_t nla2_st(const Geom& g, const NlPlan& P, const NlArgs& a, const ST* wt,
-                           cudaStream_t s) {
+static cudaError_t nla2_st(const Geom& g, const TableArgs& t, cudaStream_t s) {
   switch (g.win_r) {
-    case 1: k_nla2<1, ST><<<P.n_tiles, NF_THREADS, 0, s>>>(g, P, a, wt); break;
-    case 2: k_nla2<2, ST><<<P.n_tiles, NF_THREADS, 0, s>>>(g, P, a, wt); break;
-    case 3: k_nla2<3, ST><<<P.n_tiles, NF_THREADS, 0, s>>>(g, P, a, wt); break;
+    case 1: k_nla2<1, ST><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
+    case 2: k_nla2<2, ST><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
+    case 3: k_nla2<3, ST><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t nla2_launch(const Geom& g, const NlPlan& P, const NlArgs& a, const void* wt,
-                        cudaStream_t s) {
+cudaError_t nla2_launch(const Geom& g, const TableArgs& t, cudaStream_t s) {
+  if (t.total_units < 1) return cudaErrorInvalidValue;
   switch (g.st) {
-    case ST_F32: return nla2_st(g, P, a, (const float*)wt, s);
-    case ST_F16: return nla2_st(g, P, a, (const __half*)wt, s);
-    case ST_BF16: return nla2_st(g, P, a, (const __nv_bfloat16*)wt, s);
+    case ST_F32: return nla2_st<float>(g, t, s);
+    case ST_F16: return nla2_st<__half>(g, t, s);
+    case ST_BF16: return nla2_st<__nv_bfloat16>(g, t, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t cg_init_nltv_launch(const Geom& g, float* rv, const float* cb, const float* x,
-                                float* x_next, double* partials, DevScalars* sc, int grid,
-                                cudaStream_t s) {
+cudaError_t cg_init_nltv_launch(const Geom& g, const TableArgs& t, cudaStream_t s) {
+  if (t.total_units < 1) return cudaErrorInvalidValue;
   switch (g.win_r) {
-    case 1: k_cg_init_nltv<1><<<grid, 512, 0, s>>>(g, rv, cb, x, x_next, partials, sc); break;
-    case 2: k_cg_init_nltv<2><<<grid, 512, 0, s>>>(g, rv, cb, x, x_next, partials, sc); break;
-    case 3: k_cg_init_nltv<3><<<grid, 512, 0, s>>>(g, rv, cb, x, x_next, partials, sc); break;
+    case 1: k_cg_init_nltv<1><<<t.total_units, VEC_THREADS, 0, s>>>(g, t); break;
+    case 2: k_cg_init_nltv<2><<<t.total_units, VEC_THREADS, 0, s>>>(g, t); break;
+    case 3: k_cg_init_nltv<3><<<t.total_units, VEC_THREADS, 0, s>>>(g, t); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

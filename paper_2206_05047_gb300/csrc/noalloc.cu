@@ -1,9 +1,10 @@
 // lfsr_apply_normal_noalloc: the x-step normal-matrix product q = M p and
 // <p, M p> without a handle and without any device allocation.
 //
-// The two kernels it runs (k_nltv<NL_APPLY>, k_operator<OP_NORMAL>) need
-// global scratch for their float64 block partials, last-block counters and
-// finished totals.  Here that scratch is a file-scope __device__ array of
+// The two kernels it runs (the generic NLTV kernel in NL_APPLY mode and the
+// operator kernel, specialised or generic, in OP_NORMAL mode) need global
+// scratch for their float64 block partials, last-block counters, finished
+// totals.  Here that scratch is a file-scope __device__ array of
 // fixed size, present on every GPU that loads the library until the process
 // exits.  Host code only holds a host-side stand-in for the array's name, so
 // the array's device address is looked up with cudaGetSymbolAddress once per
@@ -27,9 +28,13 @@ namespace {
 constexpr int kMaxCtas = LFSR_NOALLOC_MAX_TILES;
 constexpr int kMaxDevices = 64;
 
+constexpr int kMaxOpCtas = 1024;
+
 struct NoallocScratch {
   DevScalars sc;
-  double partials[2][kMaxCtas];   // [0] NLTV part, [1] operator part
+  unsigned int counter;            // the specialised operator kernel's arrival counter
+  double nl_partials[kMaxCtas];    // NLTV part, one per 32 x 32 tile
+  double op_partials[kMaxOpCtas];  // operator part, one per CTA
 };
 
 static_assert(sizeof(NoallocScratch) <= LFSR_NOALLOC_SCRATCH_BYTES, "scratch size");
@@ -188,35 +193,67 @@ extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_d
     return nfail(LFSR_EUNSUPPORTED, "disparity * angular offset too large for the tile");
   if (nl_plan(g, &nl, smem_limit) != cudaSuccess)
     return nfail(LFSR_EUNSUPPORTED, "NLTV window / patch too large");
-  const int grid = op_grid(op, op.n_tiles * g.sk, ds.sm_count);
-  if (grid > kMaxCtas || nl.n_tiles > kMaxCtas)
-    return nfail(LFSR_EINVAL, "launch larger than the no-allocation scratch (4096 CTAs)");
+  const int op_units = op.fast ? op.n_tiles * ((g.sk + FAST_VIEWS - 1) / FAST_VIEWS)
+                              : op.n_tiles * g.sk;
+  const int grid = op_grid(op, op_units, ds.sm_count);
+  if (grid > kMaxOpCtas || nl.n_tiles > kMaxCtas)
+    return nfail(LFSR_EINVAL, "launch larger than the no-allocation scratch");
 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   NoallocScratch* scr = ds.scratch;
   // counters and totals start at zero on every call
-  if (cudaMemsetAsync(&scr->sc, 0, sizeof(DevScalars), s) != cudaSuccess)
+  if (cudaMemsetAsync(&scr->sc, 0, sizeof(DevScalars), s) != cudaSuccess ||
+      cudaMemsetAsync(&scr->counter, 0, sizeof(unsigned int), s) != cudaSuccess)
     return nfail(LFSR_ECUDA, "clearing the scratch scalars failed");
   NlArgs na{};
   na.x = d_xw;
   na.p_old = d_p;
   na.out = d_q;
-  na.partials = scr->partials[0];
+  na.partials = scr->nl_partials;
   na.sc = &scr->sc;
   if (nl_launch(NL_APPLY, g, nl, na, s) != cudaSuccess)
     return nfail(LFSR_ECUDA, "NLTV kernel launch failed");
-  OpArgs on{};
-  on.src = d_p;
-  on.disp = d_disparity;
-  on.out = d_q;
-  on.scale = g.cA;
-  on.view0 = 0;
-  on.nviews = g.sk;
-  on.units = op.n_tiles * g.sk;
-  on.partials = scr->partials[1];
-  on.sc = &scr->sc;
-  if (op_launch(OP_NORMAL, g, op, on, grid, s) != cudaSuccess)
-    return nfail(LFSR_ECUDA, "operator kernel launch failed");
+  cudaError_t le;
+  if (op.fast) {
+    JobArgs j{};
+    j.H = g.H;
+    j.W = g.W;
+    j.Hh = g.Hh;
+    j.Wh = g.Wh;
+    j.U = g.U;
+    j.V = g.V;
+    j.unit0 = 0;
+    j.units = op_units;
+    j.tiles_x = op.tiles_x;
+    j.view0 = 0;
+    j.nviews = g.sk;
+    j.scale = g.cA;
+    j.disp = d_disparity;
+    j.src = d_p;
+    j.out = d_q;
+    j.sc = &scr->sc;
+    TableArgs t{};   // the light field itself goes by value
+    t.jobs = nullptr;
+    t.unit_job = nullptr;
+    t.n_jobs = 1;
+    t.total_units = op_units;
+    t.partials = scr->op_partials;
+    t.counter = &scr->counter;
+    le = fast_launch(OP_NORMAL, g, op, t, grid, s, &j);
+  } else {
+    OpArgs on{};
+    on.src = d_p;
+    on.disp = d_disparity;
+    on.out = d_q;
+    on.scale = g.cA;
+    on.view0 = 0;
+    on.nviews = g.sk;
+    on.units = op_units;
+    on.partials = scr->op_partials;
+    on.sc = &scr->sc;
+    le = op_launch(OP_NORMAL, g, op, on, grid, s);
+  }
+  if (le != cudaSuccess) return nfail(LFSR_ECUDA, "operator kernel launch failed");
   double pap = 0.0;
   if (cudaMemcpyAsync(&pap, &scr->sc.pAp, sizeof(double), cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||

@@ -1,548 +1,10 @@
-// Specialised fused operator kernel for separable blur kernels of size
-// KB in {3,5,7,9} and scale Z in {1,2,3,4}: the same per-(tile, view)
-// pipeline as k_operator (warped samples -> decimated separable blur ->
-// per-LR-pixel step -> adjoint blur -> bilinear scatter), with every size of
-// the 64 x 64 tile known at compile time:
-//   * blur taps are compile-time-indexed kernel parameters (no dynamic
-//     constant-bank indexing), all tap loops unrolled;
-//   * each thread computes several outputs from a register sliding window
-//     (a row or column segment), so one shared-memory load feeds several FMAs;
-//   * the adjoint of "zero-fill then blur" runs in polyphase form: output
-//     row Z m + ph takes LR rows m + delta with compile-time deltas and
-//     coefficients kv[ph + R - Z delta] -- no division, no zero taps;
-//   * the disparity tile is staged once per tile and reused by all views;
-//   * lanes run along the dimension whose shared-memory pitch is odd, so
-//     loads, stores and the scatter atomics are free of bank conflicts;
-//   * floor / fraction of the sub-pixel shift use an FP32 add with round-down
-//     against 2^23 (exact for 0 <= t < 2^23) instead of conversions;
-//   * the <p, M p> partial sums in FP32 within a (tile, view) unit and in
-//     FP64 across units.
-// Algorithmic definitions: Eq. sr_model_vec (A_k = D B W_k) and Sec. 4.1.
-#include "lfsr_device.cuh"
+// Host side of the specialised operator kernel (op_fast.cuh): shared-memory
+// layout, occupancy, kernel attributes and the single-light-field launches.
+// The table (batch) instantiations live in op_fast_batch.cu.
+#include "op_fast.cuh"
 
 namespace lfsr {
 
-constexpr int FT_THREADS = 512;
-constexpr int FT_VB = 2;   // views processed together per pass through the stages
-
-// Outputs per task m in [4, 8] that needs the fewest 512-thread passes for
-// `rows` x ceil(n / m) tasks (ties: the smaller m, i.e. fewer registers).
-constexpr int pick_block(int rows, int n) {
-  int best = 4, best_passes = 1 << 30;
-  for (int m = 4; m <= 8; ++m) {
-    const int passes = (rows * ((n + m - 1) / m) + FT_THREADS - 1) / FT_THREADS;
-    if (passes < best_passes) {
-      best_passes = passes;
-      best = m;
-    }
-  }
-  return best;
-}
-
-template <int Z, int KB>
-struct FastShape {
-  static constexpr int T = 64;                               // tile side (HR px)
-  static constexpr int VB = FT_VB;
-  static constexpr int R = (KB - 1) / 2;                     // blur radius
-  static constexpr int NL = (T + 2 * R + Z - 1) / Z;         // LR rows/cols touching a tile
-  static constexpr int NE = Z * (NL - 1) + 2 * R + 1;        // warp samples per row/col
-  static constexpr int MG = (R + Z - 1) / Z + 1;             // zero margin of the LR grid
-  static constexpr int NG = NL + 2 * MG;                     // LR grid with margins
-  static constexpr int NGp = NG | 1;                         // its (odd) pitch
-  // stage 2 (horizontal forward): MB2 LR columns per task
-  static constexpr int MB2 = pick_block(VB * NE, NL);
-  static constexpr int NB2 = (NL + MB2 - 1) / MB2;
-  static constexpr int W2 = Z * (MB2 - 1) + KB;              // window length
-  static constexpr int NEp = ((Z * (NB2 * MB2 - 1) + KB) > NE ? (Z * (NB2 * MB2 - 1) + KB) : NE) | 1;
-  // stage 3 (vertical forward): MB3 LR rows per task
-  static constexpr int MB3 = pick_block(VB * NL, NL);
-  static constexpr int NB3 = (NL + MB3 - 1) / MB3;
-  static constexpr int W3 = Z * (MB3 - 1) + KB;
-  static constexpr int NEr = (Z * (NB3 * MB3 - 1) + KB) > NE ? (Z * (NB3 * MB3 - 1) + KB) : NE;
-  static constexpr int IT3 = (VB * NL * NB3 + FT_THREADS - 1) / FT_THREADS;
-  static constexpr int NHp = NL | 1;                         // pitch of the forward H buffer
-  // stage 4 (adjoint rows): m = floor(hi / Z) over the tile, MB5 per task;
-  // tiles start at multiples of T, so when Z divides T every tile holds
-  // exactly T / Z values of m
-  static constexpr bool ALIGNED = (T % Z) == 0;
-  static constexpr int NM = ALIGNED ? T / Z : (T - 1) / Z + 2;  // m values per tile
-  static constexpr int MB5 = pick_block(VB * NG, NM);
-  static constexpr int NB5 = (NM + MB5 - 1) / MB5;
-  static constexpr int DMIN = -(R / Z) - 1;                  // safe delta bounds (all phases)
-  static constexpr int DMAX = (Z - 1 + R) / Z;
-  static constexpr int W5 = MB5 + DMAX - DMIN;
-  static constexpr int NVp = NG | 1;                         // pitch of the adjoint V buffer
-  // stage 5 (adjoint columns + scatter): n = floor(hj / Z), MB6 per task
-  static constexpr int NN = NM;
-  static constexpr int MB6 = pick_block(T, NN);
-  static constexpr int NB6 = (NN + MB6 - 1) / MB6;
-  static constexpr int W6 = MB6 + DMAX - DMIN;
-  static constexpr int HS = NEr * NHp;                       // forward H buffer per view
-  static constexpr int VS = T * NVp;                         // adjoint V buffer per view
-  static constexpr int GS = NG * NGp;                        // LR grid per view
-  static constexpr int WS = NE * NEp;                        // sample buffer per view
-  static constexpr int NS1 = NE * NE;                        // warp samples per view
-  static constexpr int IT1 = (NS1 + FT_THREADS - 1) / FT_THREADS;
-};
-
-// 4-byte asynchronous global -> shared copy; valid == false writes 0 (no
-// bytes are read from src, which only has to be a valid address).
-__device__ __forceinline__ void cp_async_f32(float* sdst, const float* gsrc, bool valid) {
-  const unsigned saddr = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(saddr), "l"(gsrc),
-               "r"(valid ? 4 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void split_shift(float t, int& ip, float& fr) {
-  // t in [0, 2^23): ip = floor(t), fr = t - floor(t), exactly, on the FP32 pipe
-  const float f = __fadd_rd(t, 8388608.0f);
-  ip = __float_as_int(f) - 0x4B000000;
-  fr = t - (f - 8388608.0f);
-}
-
-template <int MODE, int Z, int KB>
-__global__ void __launch_bounds__(FT_THREADS, 1)
-k_operator_fast(const Geom g, const OpPlan P, const OpArgs a) {
-  using SH = FastShape<Z, KB>;
-  constexpr int T = SH::T, R = SH::R, NL = SH::NL, NE = SH::NE, MG = SH::MG, NGp = SH::NGp;
-  constexpr int NEp = SH::NEp, NHp = SH::NHp, NVp = SH::NVp, VB = SH::VB;
-  extern __shared__ __align__(16) float smem[];
-  if (a.check_done && a.sc->cg_done) return;
-  float* sP = smem + P.off_P;   // source, (NE + 2S + 1) rows, pitch P.NPc
-  float* sO = smem + P.off_W;   // disparity on the sample region, NE x NEp
-  float* sW = sO + SH::WS;      // warped samples, VB x NE x NEp
-  float* sH = smem + P.off_H;   // forward H, VB x NEr x NHp
-  float* sV = sH + VB * SH::HS; // adjoint V, VB x T x NVp (separate from H, so one unit's
-                                // scatter may overlap the next unit's forward stages)
-  float* sG = smem + P.off_G;   // LR grid with zero margins, VB x NG x NGp
-  float* sA = smem + P.off_A;   // scatter accumulator, NAr x NAc (pitch odd)
-  const int tid = threadIdx.x;
-  const int S = g.S;
-  const float Sf = (float)S;
-  const int NPc = P.NPc, NAc = P.NAc;
-  const int nvb = (a.nviews + VB - 1) / VB;
-  const int units = P.n_tiles * nvb;
-  const int u_begin = (int)((long long)blockIdx.x * units / gridDim.x);
-  const int u_end = (int)((long long)(blockIdx.x + 1) * units / gridDim.x);
-  const size_t q_lr = (size_t)g.H * g.W;
-  double part = 0.0;
-
-  static_assert(VB == 2, "the sample and scatter stages handle view pairs");
-  int cur_tile = -1;
-  int i0 = 0, j0 = 0, lr_lo = 0, lr_n = 0, lc_lo = 0, lc_n = 0, e_r0 = 0, e_c0 = 0;
-  int NAr_t = 0, NAc_t = 0;
-  // this thread's warp-sample positions (fixed for all views of a tile):
-  // staged-source index of the (0, 0) tap before the shift, and disparity
-  int s1_base[SH::IT1];
-  float s1_om[SH::IT1];
-
-  for (int t = tid; t < VB * SH::GS; t += FT_THREADS) sG[t] = 0.f;
-  if (MODE != OP_FWD)
-    for (int t = tid; t < P.NAr * NAc; t += FT_THREADS) sA[t] = 0.f;
-
-  auto flush = [&]() {
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int ar = warp; ar < NAr_t; ar += FT_THREADS / 32) {
-      const int hi = i0 - S + ar;
-      const bool row_in = hi >= 0 && hi < g.Hh;
-      for (int ac = lane; ac < NAc_t; ac += 32) {
-        const int hj = j0 - S + ac;
-        const float v = sA[ar * NAc + ac];
-        if (row_in && hj >= 0 && hj < g.Wh && v != 0.f)
-          atomicAdd(a.out + (size_t)hi * g.Wh + hj, a.scale * v);
-        sA[ar * NAc + ac] = 0.f;
-      }
-    }
-  };
-
-  for (int u = u_begin; u < u_end; ++u) {
-    const int tile = u / nvb;
-    const int kbase = a.view0 + VB * (u - tile * nvb);
-    const int nv = min(VB, a.view0 + a.nviews - kbase);   // views of this unit
-    if (tile != cur_tile) {
-      __syncthreads();
-      if (cur_tile >= 0 && MODE != OP_FWD) {
-        flush();
-        __syncthreads();
-      }
-      cur_tile = tile;
-      const int ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
-      i0 = ty * T;
-      j0 = tx * T;
-      const int TRr = min(T, g.Hh - i0), TRc = min(T, g.Wh - j0);
-      lr_lo = max(0, ceil_div(i0 - R, Z));
-      lr_n = min(g.H - 1, floor_div(i0 + TRr - 1 + R, Z)) - lr_lo + 1;
-      lc_lo = max(0, ceil_div(j0 - R, Z));
-      lc_n = min(g.W - 1, floor_div(j0 + TRc - 1 + R, Z)) - lc_lo + 1;
-      e_r0 = Z * lr_lo - R;
-      e_c0 = Z * lc_lo - R;
-      NAr_t = TRr + 2 * S + 1;
-      NAc_t = TRc + 2 * S + 1;
-      // stage the source (zero outside the image) and the disparity with
-      // asynchronous copies: every copy of the tile is in flight at once
-      {
-        const int warp = tid >> 5, lane = tid & 31;
-        constexpr int NWARP = FT_THREADS / 32;
-        if (MODE != OP_ADJ) {
-          const int np = NE + 2 * S + 1;
-          for (int pr = warp; pr < np; pr += NWARP) {
-            const int hi = e_r0 - S + pr;
-            const bool row_in = hi >= 0 && hi < g.Hh;
-            const float* src_row = a.src + (size_t)(row_in ? hi : 0) * g.Wh;
-            for (int pc = lane; pc < np; pc += 32) {
-              const int hj = e_c0 - S + pc;
-              const bool ok = row_in && hj >= 0 && hj < g.Wh;
-              cp_async_f32(sP + pr * NPc + pc, ok ? src_row + hj : a.src, ok);
-            }
-          }
-        }
-        for (int er = warp; er < NE; er += NWARP) {
-          const int hi = e_r0 + er;
-          const bool row_in = hi >= 0 && hi < g.Hh;
-          const float* d_row = a.disp + (size_t)(row_in ? hi : 0) * g.Wh;
-          for (int ec = lane; ec < NE; ec += 32) {
-            const int hj = e_c0 + ec;
-            const bool ok = row_in && hj >= 0 && hj < g.Wh;
-            cp_async_f32(sO + er * NEp + ec, ok ? d_row + hj : a.disp, ok);
-          }
-        }
-        cp_async_wait_all();
-      }
-      __syncthreads();
-      if (MODE != OP_ADJ) {
-#pragma unroll
-        for (int it = 0; it < SH::IT1; ++it) {
-          const int t = tid + it * FT_THREADS;
-          const int er = t / NE, ec = t - er * NE;
-          const bool ok = t < SH::NS1;
-          s1_base[it] = ok ? er * NPc + ec : 0;
-          s1_om[it] = ok ? sO[er * NEp + ec] : 0.f;
-        }
-      }
-    }
-
-    // data block: fetch the views' LR values and duals now, so the loads are
-    // in flight during the warp and blur stages
-    // (raw words of the storage kinds; widened at use)
-    unsigned int pre_y[SH::IT3][SH::MB3], pre_w[SH::IT3][SH::MB3];
-    if (MODE == OP_DATA) {
-#pragma unroll
-      for (int it = 0; it < SH::IT3; ++it) {
-        const int t = tid + it * FT_THREADS;
-        const int v = t / (NL * SH::NB3), r3 = t - v * (NL * SH::NB3);
-        const int lc = r3 % NL, rb = r3 / NL;
-#pragma unroll
-        for (int o = 0; o < SH::MB3; ++o) {
-          const int lr = rb * SH::MB3 + o;
-          pre_y[it][o] = 0u;
-          pre_w[it][o] = 0u;
-          if (v < nv && lr < lr_n && lc < lc_n) {
-            const size_t gi = (size_t)(kbase + v) * q_lr + (size_t)(lr_lo + lr) * g.W + (lc_lo + lc);
-            pre_y[it][o] = ld_raw_kind(a.y, gi, g.st_y);
-            pre_w[it][o] = ld_raw_kind(a.wA_old, gi, g.st);
-          }
-        }
-      }
-    }
-
-    if (MODE != OP_ADJ) {
-      // 1. warped samples: outside the image the disparity is 0 and the
-      //    staged source is 0, so the sample is 0 without a branch.  The
-      //    two views of the pass share the disparity read and, when they
-      //    lie in the same row of the angular grid, the vertical split.
-      {
-        const float tu0 = g.tu[kbase], tv0 = g.tv[kbase];
-        const int k1 = kbase + (nv > 1 ? 1 : 0);
-        const float tu1 = g.tu[k1], tv1 = g.tv[k1];
-        const bool two = nv > 1;
-        const bool same_row = tv1 == tv0;
-#pragma unroll
-        for (int it = 0; it < SH::IT1; ++it) {
-          const int t = tid + it * FT_THREADS;
-          if (it < SH::IT1 - 1 || t < SH::NS1) {
-            const int si = (NEp == NE) ? t : (t / NE) * NEp + (t % NE);
-            const float om = s1_om[it];
-            const float* qb = sP + s1_base[it];
-            int iy, ix;
-            float fy, fx;
-            split_shift(fmaf(tv0, om, Sf), iy, fy);
-            split_shift(fmaf(tu0, om, Sf), ix, fx);
-            {
-              const float* q = qb + iy * NPc + ix;
-              const float top = fmaf(fx, q[1] - q[0], q[0]);
-              const float bot = fmaf(fx, q[NPc + 1] - q[NPc], q[NPc]);
-              sW[si] = fmaf(fy, bot - top, top);
-            }
-            if (two) {
-              if (!same_row) split_shift(fmaf(tv1, om, Sf), iy, fy);
-              split_shift(fmaf(tu1, om, Sf), ix, fx);
-              const float* q = qb + iy * NPc + ix;
-              const float top = fmaf(fx, q[1] - q[0], q[0]);
-              const float bot = fmaf(fx, q[NPc + 1] - q[NPc], q[NPc]);
-              sW[SH::WS + si] = fmaf(fy, bot - top, top);
-            }
-          }
-        }
-      }
-      __syncthreads();
-      // 2. horizontal blur at decimated columns; lanes along rows
-      for (int t = tid; t < VB * NE * SH::NB2; t += FT_THREADS) {
-        const int v = t / (NE * SH::NB2), r2 = t - v * (NE * SH::NB2);
-        if (v >= nv) continue;
-        const int er = r2 % NE, cb = r2 / NE;
-        const float* w = sW + v * SH::WS + er * NEp + Z * SH::MB2 * cb;
-        float win[SH::W2];
-#pragma unroll
-        for (int c = 0; c < SH::W2; ++c) win[c] = w[c];
-#pragma unroll
-        for (int o = 0; o < SH::MB2; ++o) {
-          float acc = 0.f;
-#pragma unroll
-          for (int b = 0; b < KB; ++b) acc = fmaf(g.kh[b], win[Z * o + b], acc);
-          const int lc = cb * SH::MB2 + o;
-          if (lc < NL) sH[v * SH::HS + er * NHp + lc] = acc;
-        }
-      }
-      __syncthreads();
-      // 3. vertical blur at decimated rows, then the per-LR-pixel step;
-      //    lanes along LR columns
-      float psum = 0.f;
-#pragma unroll
-      for (int it = 0; it < SH::IT3; ++it) {
-        const int t = tid + it * FT_THREADS;
-        const int v = t / (NL * SH::NB3), r3 = t - v * (NL * SH::NB3);
-        if (v >= nv) break;
-        const int lc = r3 % NL, rb = r3 / NL;
-        const int k = kbase + v;
-        const float* hcol = sH + v * SH::HS + (Z * SH::MB3 * rb) * NHp + lc;
-        float win[SH::W3];
-#pragma unroll
-        for (int c = 0; c < SH::W3; ++c) win[c] = hcol[c * NHp];
-#pragma unroll
-        for (int o = 0; o < SH::MB3; ++o) {
-          const int lr = rb * SH::MB3 + o;
-          if (lr >= NL) continue;
-          float acc = 0.f;
-#pragma unroll
-          for (int b = 0; b < KB; ++b) acc = fmaf(g.kv[b], win[Z * o + b], acc);
-          float h = 0.f;
-          if (lr < lr_n && lc < lc_n) {
-            const int gr = lr_lo + lr, gc = lc_lo + lc;
-            const bool owned = (Z * gr >= i0) && (Z * gr < i0 + T) && (Z * gc >= j0) &&
-                               (Z * gc < j0 + T);
-            h = acc;
-            if (MODE == OP_NORMAL) {
-              if (owned) psum = fmaf(acc, acc, psum);
-            } else if (MODE == OP_DATA) {
-              const size_t gi = (size_t)k * q_lr + (size_t)gr * g.W + gc;
-              const float yv = raw_to_float(pre_y[it][o], g.st_y);
-              const float wa = raw_to_float(pre_w[it][o], g.st);
-              const float res = acc - yv;
-              const float uu = fmaf(g.lambda1, res, wa);
-              const float wn = fminf(fmaxf(uu, -g.thr), g.thr);
-              const float f = 2.f * wn - wa;
-              h = fmaf(g.lambda2, res, 0.5f * g.mu * g.lambda1 * f);
-              if (owned) {
-                st_kind(a.wA_new, gi, g.st, wn);
-                const float dd = wn - wa;
-                psum = fmaf(dd, dd, psum);
-              }
-            } else if (MODE == OP_FWD) {
-              if (owned) a.out[(size_t)k * q_lr + (size_t)gr * g.W + gc] = acc;
-            }
-          }
-          sG[v * SH::GS + (lr + MG) * NGp + (lc + MG)] = h;
-        }
-      }
-      part += (double)psum;
-    } else {
-      for (int t = tid; t < VB * NL * NL; t += FT_THREADS) {
-        const int v = t / (NL * NL), r0 = t - v * (NL * NL);
-        if (v >= nv) continue;
-        const int lr = r0 / NL, lc = r0 - lr * NL;
-        float val = 0.f;
-        if (lr < lr_n && lc < lc_n)
-          val = __ldg(a.src + (size_t)(kbase + v) * q_lr + (size_t)(lr_lo + lr) * g.W + (lc_lo + lc));
-        sG[v * SH::GS + (lr + MG) * NGp + (lc + MG)] = val;
-      }
-    }
-    __syncthreads();
-    if (MODE == OP_FWD) continue;
-
-    // 4. adjoint blur, rows (polyphase): V(hi, c) for hi in the tile and
-    //    every column c of the LR grid (margins included, they are zero)
-    const int m_lo = floor_div(i0, Z);
-    for (int t = tid; t < VB * SH::NG * SH::NB5; t += FT_THREADS) {
-      const int v = t / (SH::NG * SH::NB5), r4 = t - v * (SH::NG * SH::NB5);
-      if (v >= nv) continue;
-      const int c = r4 % SH::NG, mb = r4 / SH::NG;
-      const int m0 = m_lo + mb * SH::MB5;
-      const float* gv = sG + v * SH::GS;
-      // window rows l = m0 + DMIN .. m0 + MB5 - 1 + DMAX (grid row l - lr_lo + MG)
-      const int r0 = m0 + SH::DMIN - lr_lo + MG;
-      float win[SH::W5];
-#pragma unroll
-      for (int w = 0; w < SH::W5; ++w) {
-        const int rr = r0 + w;
-        win[w] = (rr >= 0 && rr < SH::NG) ? gv[rr * NGp + c] : 0.f;
-      }
-#pragma unroll
-      for (int o = 0; o < SH::MB5; ++o) {
-#pragma unroll
-        for (int ph = 0; ph < Z; ++ph) {
-          const int hi = Z * (m0 + o) + ph;
-          float acc = 0.f;
-#pragma unroll
-          for (int d = SH::DMIN; d <= SH::DMAX; ++d) {
-            const int ai = ph + R - Z * d;
-            if (ai >= 0 && ai <= 2 * R) acc = fmaf(g.kv[ai], win[o + d - SH::DMIN], acc);
-          }
-          const int ri = hi - i0;
-          if (ri >= 0 && ri < T) sV[v * SH::VS + ri * NVp + c] = acc;
-        }
-      }
-    }
-    __syncthreads();
-    // 5. adjoint blur, columns (polyphase), then the bilinear scatter W_k^T;
-    //    lanes along rows; one task covers the same pixels in both views
-    const int n_lo = floor_div(j0, Z);
-    const int TRr = min(T, g.Hh - i0);
-    const bool full_cols = j0 + T <= g.Wh;
-    const float tu0 = g.tu[kbase], tv0 = g.tv[kbase];
-    const int k1 = kbase + (nv > 1 ? 1 : 0);
-    const float tu1 = g.tu[k1], tv1 = g.tv[k1];
-    const bool two = nv > 1;
-    const bool same_row = tv1 == tv0;
-    for (int t = tid; t < T * SH::NB6; t += FT_THREADS) {
-      const int i = t % T, nb = t / T;
-      if (i >= TRr) continue;
-      const int n0 = n_lo + nb * SH::MB6;
-      const int c0 = n0 + SH::DMIN - lc_lo + MG;     // in [0, NG - W6] for every tile
-      float win0[SH::W6], win1[SH::W6];
-      {
-        const float* v0 = sV + i * NVp + c0;
-        const float* v1 = v0 + SH::VS;
-#pragma unroll
-        for (int w = 0; w < SH::W6; ++w) {
-          win0[w] = v0[w];
-          win1[w] = two ? v1[w] : 0.f;
-        }
-      }
-      const int hi = i0 + i;
-      const float* orow = sO + (hi - e_r0) * NEp - e_c0;
-      // taps of consecutive pixels of this row segment: when a pixel's
-      // integer shift equals its left neighbour's, its left taps coincide
-      // with the neighbour's right taps and are added before one atomic
-      bool pend0 = false, pend1 = false;
-      int pr0 = 0, pc0 = 0, pr1 = 0, pc1 = 0;
-      float pt0 = 0.f, pb0 = 0.f, pt1 = 0.f, pb1 = 0.f;
-      auto scatter = [&](float tval, int r, int c, float fy, float fx, bool& pend, int& pr_,
-                         int& pc_, float& pt, float& pb) {
-        const float ty = fy * tval, by = tval - ty;
-        float tl = by - fx * by, bl = ty - fx * ty;
-        const float tr = fx * by, br = fx * ty;
-        const bool merged = pend && pr_ == r && pc_ == c;
-        if (merged) {
-          tl += pt;
-          bl += pb;
-        } else if (pend) {
-          atomicAdd(sA + pr_ * NAc + pc_, pt);
-          atomicAdd(sA + (pr_ + 1) * NAc + pc_, pb);
-        }
-        atomicAdd(sA + r * NAc + c, tl);
-        atomicAdd(sA + (r + 1) * NAc + c, bl);
-        pend = true;
-        pr_ = r;
-        pc_ = c + 1;
-        pt = tr;
-        pb = br;
-      };
-      auto pixel = [&](int o, int ph) {
-        const int hj = Z * (n0 + o) + ph;
-        float t0 = 0.f, t1 = 0.f;
-#pragma unroll
-        for (int d = SH::DMIN; d <= SH::DMAX; ++d) {
-          const int ai = ph + R - Z * d;
-          if (ai >= 0 && ai <= 2 * R) {
-            t0 = fmaf(g.kh[ai], win0[o + d - SH::DMIN], t0);
-            t1 = fmaf(g.kh[ai], win1[o + d - SH::DMIN], t1);
-          }
-        }
-        const float om = orow[hj];
-        const int cc = hj - j0;
-        int iy, ix;
-        float fy, fx;
-        split_shift(fmaf(tv0, om, Sf), iy, fy);
-        split_shift(fmaf(tu0, om, Sf), ix, fx);
-        scatter(t0, i + iy, cc + ix, fy, fx, pend0, pr0, pc0, pt0, pb0);
-        if (two) {
-          if (!same_row) split_shift(fmaf(tv1, om, Sf), iy, fy);
-          split_shift(fmaf(tu1, om, Sf), ix, fx);
-          scatter(t1, i + iy, cc + ix, fy, fx, pend1, pr1, pc1, pt1, pb1);
-        }
-      };
-      if (SH::ALIGNED && full_cols) {
-#pragma unroll
-        for (int o = 0; o < SH::MB6; ++o)
-#pragma unroll
-          for (int ph = 0; ph < Z; ++ph) pixel(o, ph);
-      } else {
-#pragma unroll
-        for (int o = 0; o < SH::MB6; ++o)
-#pragma unroll
-          for (int ph = 0; ph < Z; ++ph) {
-            const int hj = Z * (n0 + o) + ph;
-            if (hj >= j0 && hj < j0 + T && hj < g.Wh) pixel(o, ph);
-          }
-      }
-      if (pend0) {
-        atomicAdd(sA + pr0 * NAc + pc0, pt0);
-        atomicAdd(sA + (pr0 + 1) * NAc + pc0, pb0);
-      }
-      if (pend1) {
-        atomicAdd(sA + pr1 * NAc + pc1, pt1);
-        atomicAdd(sA + (pr1 + 1) * NAc + pc1, pb1);
-      }
-    }
-    // no barrier here: the next unit's stages 1-2 write sW and sH, which this
-    // stage does not read, and sG / sV are rewritten only after two barriers;
-    // a tile change starts with a barrier before the flush
-  }
-
-  if (MODE != OP_FWD && cur_tile >= 0) {
-    __syncthreads();
-    flush();
-  }
-  if (MODE == OP_NORMAL || MODE == OP_DATA) {
-    const int slot = (MODE == OP_NORMAL) ? RED_OP : RED_DW_A;
-    double total = 0.0;
-    if (grid_sum_last<FT_THREADS>(part, a.partials, &a.sc->counter[slot], &total) &&
-        threadIdx.x == 0) {
-      a.sc->red[slot] = total;
-      if (MODE == OP_NORMAL) {
-        const double pAp = (double)g.cA * total + (double)g.mu * a.sc->red[RED_NLTV];
-        a.sc->pAp = pAp;
-        if (!(pAp > 0.0) || !isfinite(pAp)) {
-          set_status(a.sc, -4);  // LFSR_ENUMERIC
-          a.sc->cg_done = 1;
-          a.sc->alpha = 0.0;
-        } else {
-          a.sc->alpha = a.sc->pi / pAp;
-        }
-      } else {
-        a.sc->dwA = total;
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// host side
-// ---------------------------------------------------------------------------
 template <int Z, int KB>
 static size_t fast_layout(const Geom& g, OpPlan* P) {
   using SH = FastShape<Z, KB>;
@@ -571,38 +33,43 @@ static size_t fast_layout(const Geom& g, OpPlan* P) {
 
 template <int Z, int KB>
 static cudaError_t fast_prepare_zk(int optin) {
-  cudaError_t e = set_max_dynamic_smem(k_operator_fast<OP_NORMAL, Z, KB>, optin);
-  if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator_fast<OP_DATA, Z, KB>, optin);
-  if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator_fast<OP_FWD, Z, KB>, optin);
-  if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator_fast<OP_ADJ, Z, KB>, optin);
+  cudaError_t e = set_max_dynamic_smem(k_operator_fast<OP_NORMAL, Z, KB, true>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator_fast<OP_DATA, Z, KB, true>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator_fast<OP_FWD, Z, KB, true>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator_fast<OP_ADJ, Z, KB, true>, optin);
+  if (e == cudaSuccess) e = fast_prepare_table(Z, KB, optin);
   return e;
 }
 
 template <int Z, int KB>
 static int fast_occupancy(size_t smem) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_operator_fast<OP_NORMAL, Z, KB>,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_operator_fast<OP_NORMAL, Z, KB, true>,
                                                     FT_THREADS, smem) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
 template <int Z, int KB>
-static cudaError_t fast_launch_zk(int mode, const Geom& g, const OpPlan& P, const OpArgs& a,
-                                  int grid, cudaStream_t s) {
+static cudaError_t fast_launch_zk(int mode, const Geom& g, const OpPlan& P, const TableArgs& t,
+                                  const JobArgs& one, int grid, cudaStream_t s) {
   switch (mode) {
-    case OP_NORMAL: k_operator_fast<OP_NORMAL, Z, KB><<<grid, FT_THREADS, P.smem_bytes, s>>>(g, P, a); break;
-    case OP_DATA: k_operator_fast<OP_DATA, Z, KB><<<grid, FT_THREADS, P.smem_bytes, s>>>(g, P, a); break;
-    case OP_FWD: k_operator_fast<OP_FWD, Z, KB><<<grid, FT_THREADS, P.smem_bytes, s>>>(g, P, a); break;
-    case OP_ADJ: k_operator_fast<OP_ADJ, Z, KB><<<grid, FT_THREADS, P.smem_bytes, s>>>(g, P, a); break;
+    case OP_NORMAL:
+      k_operator_fast<OP_NORMAL, Z, KB, true><<<grid, FT_THREADS, P.smem_bytes, s>>>(g, P, t, one);
+      break;
+    case OP_DATA:
+      k_operator_fast<OP_DATA, Z, KB, true><<<grid, FT_THREADS, P.smem_bytes, s>>>(g, P, t, one);
+      break;
+    case OP_FWD:
+      k_operator_fast<OP_FWD, Z, KB, true><<<grid, FT_THREADS, P.smem_bytes, s>>>(g, P, t, one);
+      break;
+    case OP_ADJ:
+      k_operator_fast<OP_ADJ, Z, KB, true><<<grid, FT_THREADS, P.smem_bytes, s>>>(g, P, t, one);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
-
-// (Z, KB) pairs with a specialised kernel.
-#define LFSR_FAST_CASES(X) \
-  X(1, 3) X(1, 5) X(1, 7) X(2, 3) X(2, 5) X(2, 7) X(2, 9) X(3, 5) X(3, 7) X(3, 9) X(4, 7) X(4, 9)
 
 bool fast_supported(const Geom& g) {
   if (!g.separable) return false;
@@ -633,9 +100,12 @@ cudaError_t fast_plan(const Geom& g, OpPlan* P, int smem_limit) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t fast_launch(int mode, const Geom& g, const OpPlan& P, const OpArgs& a, int grid,
-                        cudaStream_t s) {
-#define X(z, k) if (g.zeta == z && g.kb == k) return fast_launch_zk<z, k>(mode, g, P, a, grid, s);
+cudaError_t fast_launch(int mode, const Geom& g, const OpPlan& P, const TableArgs& t, int grid,
+                        cudaStream_t s, const JobArgs* single) {
+  if (grid < 1 || t.total_units < 0) return cudaErrorInvalidValue;
+  if (!single) return fast_launch_table(mode, g, P, t, grid, s);
+#define X(z, k) \
+  if (g.zeta == z && g.kb == k) return fast_launch_zk<z, k>(mode, g, P, t, *single, grid, s);
   LFSR_FAST_CASES(X)
 #undef X
   return cudaErrorInvalidValue;

@@ -11,71 +11,86 @@
 
 namespace lfsr {
 
-constexpr int VEC_THREADS = 512;
+// Table-driven: one CTA per chunk of HR pixels of one light field (unit
+// blockIdx.x of the table); the inner products go to one slot per unit.
 
+// x-step initialisation without stored NLTV terms: r = -v, x' = x, pi = <r, r>.
 __global__ void __launch_bounds__(VEC_THREADS)
-k_cg_init(const Geom g, float* __restrict__ rv, const float* __restrict__ x,
-          float* __restrict__ x_next, double* partials, DevScalars* sc) {
-  const size_t n = (size_t)g.Hh * g.Wh;
+k_cg_init(const Geom g, const TableArgs tb) {
+  __shared__ double s_red[VEC_THREADS / 32];
+  const JobArgs* jp = tb.jobs + table_job(tb, blockIdx.x);
+  const size_t n = (size_t)jp->Hh * jp->Wh;
+  float* __restrict__ rv = jp->out;
+  const float* __restrict__ x = jp->src;
+  float* __restrict__ x_next = jp->x_next;
+  const size_t c0 = (size_t)(blockIdx.x - jp->unit0) * jp->chunk;
+  const size_t c1 = min(n, c0 + (size_t)jp->chunk);
   double part = 0.0;
-  for (size_t i = (size_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * VEC_THREADS) {
+  for (size_t i = c0 + threadIdx.x; i < c1; i += VEC_THREADS) {
     const float r = -rv[i];
     rv[i] = r;
     x_next[i] = x[i];
     part += (double)r * (double)r;
   }
-  double total = 0.0;
-  if (grid_sum_last<VEC_THREADS>(part, partials, &sc->counter[RED_PI], &total) &&
-      threadIdx.x == 0) {
-    sc->pi = total;
-    sc->cg_first = 1;
-    sc->cg_steps = 0;
-    sc->beta = 0.0;
-    sc->dw2 = sc->dwA + sc->dwS;
-    if (!isfinite(total)) set_status(sc, -4);  // LFSR_ENUMERIC
-    sc->cg_done = (total > g.tau && isfinite(total)) ? 0 : 1;
-  }
+  const double bs = block_sum<VEC_THREADS>(part, s_red);
+  if (threadIdx.x == 0) tb.partials[blockIdx.x] = bs;
+  if (table_arrive_last(tb.counter)) cg_init_finalize<VEC_THREADS>(g, tb);
 }
 
+// CG update: x += alpha p, r -= alpha q, pi' = <r, r>, beta = pi' / pi.
 __global__ void __launch_bounds__(VEC_THREADS)
-k_cg_update(const Geom g, const float* __restrict__ p, const float* __restrict__ q,
-            float* __restrict__ x_next, float* __restrict__ r, double* partials,
-            DevScalars* sc) {
-  if (sc->cg_done) return;
-  const float alpha = (float)sc->alpha;
-  const size_t n = (size_t)g.Hh * g.Wh;
+k_cg_update(const Geom g, const TableArgs tb) {
+  __shared__ double s_red[VEC_THREADS / 32];
+  const JobArgs* jp = tb.jobs + table_job(tb, blockIdx.x);
+  DevScalars* sc = jp->sc;
   double part = 0.0;
-  for (size_t i = (size_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * VEC_THREADS) {
-    x_next[i] = fmaf(alpha, p[i], x_next[i]);
-    const float rn = fmaf(-alpha, q[i], r[i]);
-    r[i] = rn;
-    part += (double)rn * (double)rn;
+  if (!((volatile int*)&sc->cg_done)[0]) {
+    const size_t n = (size_t)jp->Hh * jp->Wh;
+    const float* __restrict__ p = jp->p_old;
+    const float* __restrict__ q = jp->q;
+    float* __restrict__ r = jp->rr;
+    float* __restrict__ x_next = jp->x_next;
+    const float alpha = (float)sc->alpha;
+    const size_t c0 = (size_t)(blockIdx.x - jp->unit0) * jp->chunk;
+    const size_t c1 = min(n, c0 + (size_t)jp->chunk);
+    for (size_t i = c0 + threadIdx.x; i < c1; i += VEC_THREADS) {
+      x_next[i] = fmaf(alpha, p[i], x_next[i]);
+      const float rn = fmaf(-alpha, q[i], r[i]);
+      r[i] = rn;
+      part += (double)rn * (double)rn;
+    }
   }
-  double total = 0.0;
-  if (grid_sum_last<VEC_THREADS>(part, partials, &sc->counter[RED_PI], &total) &&
-      threadIdx.x == 0) {
-    const double pi_old = sc->pi;
-    sc->beta = total / pi_old;
-    sc->pi = total;
-    sc->cg_first = 0;
-    sc->cg_steps += 1;
-    if (!isfinite(total)) set_status(sc, -4);  // LFSR_ENUMERIC
-    if (!(total > g.tau) || !isfinite(total)) sc->cg_done = 1;
+  const double bs = block_sum<VEC_THREADS>(part, s_red);
+  if (threadIdx.x == 0) tb.partials[blockIdx.x] = bs;
+  if (table_arrive_last(tb.counter)) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < tb.n_jobs; j += VEC_THREADS / 32) {
+      const JobArgs* jj = tb.jobs + j;
+      DevScalars* s = jj->sc;
+      if (((volatile int*)&s->cg_done)[0]) continue;
+      const double total = warp_sum_slots(tb.partials + jj->unit0, jj->units);
+      if (lane == 0) {
+        const double pi_old = s->pi;
+        s->beta = total / pi_old;
+        s->pi = total;
+        s->cg_first = 0;
+        s->cg_steps += 1;
+        if (!isfinite(total)) set_status(s, -4);  // LFSR_ENUMERIC
+        if (!(total > g.tau) || !isfinite(total)) s->cg_done = 1;
+      }
+    }
   }
 }
 
-cudaError_t cg_init_launch(const Geom& g, float* rv, const float* x, float* x_next,
-                           double* partials, DevScalars* sc, int grid, cudaStream_t s) {
-  k_cg_init<<<grid, VEC_THREADS, 0, s>>>(g, rv, x, x_next, partials, sc);
+cudaError_t cg_init_launch(const Geom& g, const TableArgs& t, cudaStream_t s) {
+  if (t.total_units < 1) return cudaErrorInvalidValue;
+  k_cg_init<<<t.total_units, VEC_THREADS, 0, s>>>(g, t);
   return cudaGetLastError();
 }
 
-cudaError_t cg_update_launch(const Geom& g, const float* p, const float* q, float* x_next,
-                             float* r, double* partials, DevScalars* sc, int grid,
-                             cudaStream_t s) {
-  k_cg_update<<<grid, VEC_THREADS, 0, s>>>(g, p, q, x_next, r, partials, sc);
+cudaError_t cg_update_launch(const Geom& g, const TableArgs& t, cudaStream_t s) {
+  if (t.total_units < 1) return cudaErrorInvalidValue;
+  k_cg_update<<<t.total_units, VEC_THREADS, 0, s>>>(g, t);
   return cudaGetLastError();
 }
 

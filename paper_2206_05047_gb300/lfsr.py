@@ -39,7 +39,11 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblfsr.so
 EXPORTS = ("lfsr_create", "lfsr_solve", "lfsr_destroy", "lfsr_last_error", "lfsr_stats",
            "lfsr_load", "lfsr_iterate", "lfsr_get_x", "lfsr_set_state", "lfsr_get_state",
            "lfsr_apply_A", "lfsr_apply_AT", "lfsr_weights", "lfsr_apply_normal",
-           "lfsr_set_profiling", "lfsr_apply_normal_noalloc")
+           "lfsr_set_profiling", "lfsr_apply_normal_noalloc", "lfsr_batch_create",
+           "lfsr_batch_destroy", "lfsr_batch_last_error", "lfsr_batch_size", "lfsr_batch_load",
+           "lfsr_batch_iterate", "lfsr_batch_get_x", "lfsr_batch_stats",
+           "lfsr_batch_launches_per_iteration", "lfsr_batch_set_profiling",
+           "lfsr_batch_kernel_times")
 
 
 class lfsr_params(C.Structure):
@@ -95,6 +99,19 @@ def load_library(path: str = _LIB_PATH):
         "lfsr_set_profiling": (C.c_int, [H, C.c_int]),
         "lfsr_apply_normal_noalloc": (C.c_int, [C.POINTER(lfsr_params), fp, fp, fp, fp,
                                                 C.POINTER(C.c_double), C.c_void_p]),
+        "lfsr_batch_create": (C.c_int, [C.POINTER(lfsr_params), C.c_int, C.c_void_p,
+                                        C.POINTER(C.c_void_p)]),
+        "lfsr_batch_destroy": (None, [H]),
+        "lfsr_batch_last_error": (C.c_char_p, [H]),
+        "lfsr_batch_size": (C.c_int, [H]),
+        "lfsr_batch_load": (C.c_int, [H, C.c_int, fp, fp, C.c_int]),
+        "lfsr_batch_iterate": (C.c_int, [H, C.c_int]),
+        "lfsr_batch_get_x": (C.c_int, [H, C.c_int, fp, C.c_int]),
+        "lfsr_batch_stats": (C.c_int, [H, C.c_int, C.POINTER(lfsr_stats_t)]),
+        "lfsr_batch_launches_per_iteration": (C.c_int, [H]),
+        "lfsr_batch_set_profiling": (C.c_int, [H, C.c_int]),
+        "lfsr_batch_kernel_times": (C.c_int, [H, C.POINTER(C.c_double),
+                                              C.POINTER(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -142,6 +159,32 @@ def _check(rc: int, handle=None):
         raise LfsrError(rc, last_error(handle))
 
 
+def _params(U, V, H, W, scale, blur, disparity, lambda1=1.0, lambda2=4.0, mu=1.0,
+            nltv_window=5, nltv_patch=3, nltv_h=0.1, cg_iters=5, cg_tol=0.0,
+            precision=LFSR_FP32):
+    """(lfsr_params, arrays it points to: keep them alive while it is used)."""
+    blur = np.ascontiguousarray(blur, dtype=np.float32)
+    disp = np.ascontiguousarray(disparity, dtype=np.float32)
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    prm = lfsr_params(C.sizeof(lfsr_params), U, V, H, W, scale, blur.shape[0],
+                      blur.ctypes.data_as(C.POINTER(C.c_float)),
+                      disp.ctypes.data_as(C.POINTER(C.c_float)),
+                      lambda1, lambda2, mu, nltv_window, nltv_patch, nltv_h, cg_iters, cg_tol,
+                      precision)
+    return prm, (blur, disp)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        except ImportError:
+            return 0
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
 def create(U, V, H, W, scale, blur, disparity, lambda1=1.0, lambda2=4.0, mu=1.0,
            nltv_window=5, nltv_patch=3, nltv_h=0.1, cg_iters=5, cg_tol=0.0,
            precision=LFSR_FP32, stream=None):
@@ -149,25 +192,11 @@ def create(U, V, H, W, scale, blur, disparity, lambda1=1.0, lambda2=4.0, mu=1.0,
     an integer cudaStream_t, or None (the current torch stream if torch has
     CUDA, else the legacy default stream)."""
     lib = load_library()
-    blur = np.ascontiguousarray(blur, dtype=np.float32)
-    disp = np.ascontiguousarray(disparity, dtype=np.float32)
-    prm = lfsr_params(C.sizeof(lfsr_params), U, V, H, W, scale, blur.shape[0],
-                      blur.ctypes.data_as(C.POINTER(C.c_float)),
-                      disp.ctypes.data_as(C.POINTER(C.c_float)),
-                      lambda1, lambda2, mu, nltv_window, nltv_patch, nltv_h, cg_iters, cg_tol,
-                      precision)
-    if stream is None:
-        try:
-            import torch
-            s = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
-        except ImportError:
-            s = 0
-    elif isinstance(stream, int):
-        s = stream
-    else:
-        s = stream.cuda_stream
+    prm, keep = _params(U, V, H, W, scale, blur, disparity, lambda1, lambda2, mu, nltv_window,
+                        nltv_patch, nltv_h, cg_iters, cg_tol, precision)
     h = C.c_void_p()
-    _check(lib.lfsr_create(C.byref(prm), C.c_void_p(s), C.byref(h)))
+    _check(lib.lfsr_create(C.byref(prm), C.c_void_p(_stream(stream)), C.byref(h)))
+    del keep
     return h
 
 
@@ -310,3 +339,88 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---- batches ---------------------------------------------------------------
+def batch_last_error(batch) -> str:
+    return load_library().lfsr_batch_last_error(batch).decode()
+
+
+def _bcheck(rc: int, batch=None):
+    if rc != LFSR_OK:
+        raise LfsrError(rc, batch_last_error(batch))
+
+
+class Batch:
+    """lfsr_batch: many light fields stepped together, one launch per phase.
+
+    jobs: a list of dicts of create()'s keyword arguments (U, V, H, W, scale,
+    blur, disparity, and the solver constants, which must be equal)."""
+
+    def __init__(self, jobs, stream=None):
+        lib = load_library()
+        arr = (lfsr_params * len(jobs))()
+        keep = []
+        for j, kw in enumerate(jobs):
+            kw = dict(kw)
+            kw.pop("stream", None)
+            prm, k = _params(**kw)
+            arr[j] = prm
+            keep.append(k)
+        b = C.c_void_p()
+        _bcheck(lib.lfsr_batch_create(arr, len(jobs), C.c_void_p(_stream(stream)), C.byref(b)))
+        del keep
+        self.handle = b
+        self.n = len(jobs)
+
+    def load(self, job, lr_views, x0):
+        py, ky = _ptr(lr_views)
+        px, kx = _ptr(x0)
+        _bcheck(load_library().lfsr_batch_load(self.handle, int(job), py, px, _kind(ky, kx)),
+                self.handle)
+
+    def iterate(self, iterations):
+        _bcheck(load_library().lfsr_batch_iterate(self.handle, int(iterations)), self.handle)
+
+    def get_x(self, job, x_out):
+        po, ko = _ptr(x_out)
+        _bcheck(load_library().lfsr_batch_get_x(self.handle, int(job), po, ko), self.handle)
+
+    def stats(self, job) -> dict:
+        st = lfsr_stats_t()
+        st.struct_size = C.sizeof(lfsr_stats_t)
+        _bcheck(load_library().lfsr_batch_stats(self.handle, int(job), C.byref(st)), self.handle)
+        return dict(iterations=st.iterations, cg_steps=st.cg_steps, status=st.status,
+                    dual_change_sq=st.dual_change_sq, cg_pi=st.cg_pi,
+                    state_bytes=st.state_bytes)
+
+    def launches_per_iteration(self) -> int:
+        return load_library().lfsr_batch_launches_per_iteration(self.handle)
+
+    def set_profiling(self, on: bool):
+        _bcheck(load_library().lfsr_batch_set_profiling(self.handle, int(bool(on))), self.handle)
+
+    def kernel_times(self):
+        """(ms[8], launches[8]) by launch class since profiling was switched on."""
+        ms = (C.c_double * 8)()
+        n = (C.c_int64 * 8)()
+        _bcheck(load_library().lfsr_batch_kernel_times(self.handle, ms, n), self.handle)
+        return list(ms), list(n)
+
+    def close(self):
+        if self.handle is not None:
+            load_library().lfsr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+

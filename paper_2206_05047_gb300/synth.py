@@ -99,6 +99,30 @@ WORKLOADS: Dict[str, Workload] = {
 }
 
 
+def batch_workloads(n: int = 64, seed: int = 4000) -> List[Workload]:
+    """The uneven light fields of the batched configuration: square angular
+    grid from {5, 7, 9}, square LR side uniform in [96, 384], scale from
+    {2, 3} (blur 7 / sigma 1.2 for x2 and 9 / sigma 1.5 for x3), 2-6 planes at
+    sorted disparities uniform in [-2, 2], impulse fraction uniform in
+    [0, 0.2], Gaussian sigma uniform in [0.01, 0.03]; 7x7 NLTV window, 3x3
+    patch, h = 0.1, 100 iterations.  Light field i is generated with
+    make_problem(wl, seed + 1 + i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        ang = int(rng.choice([5, 7, 9]))
+        side = int(rng.integers(96, 385))
+        zeta = int(rng.choice([2, 3]))
+        planes = int(rng.integers(2, 7))
+        disp = tuple(float(d) for d in np.sort(rng.uniform(-2.0, 2.0, planes)))
+        impulse = float(rng.uniform(0.0, 0.2))
+        sigma = float(rng.uniform(0.01, 0.03))
+        kb, bs = (7, 1.2) if zeta == 2 else (9, 1.5)
+        out.append(Workload(f"batch{seed}_{i:03d}", ang, ang, side, side, zeta, kb, bs, disp,
+                            sigma, impulse, 7, 3, 0.1, 100))
+    return out
+
+
 def custom(name: str = "custom", **kw) -> Workload:
     """A Workload with explicit sizes (used for small and edge-case tests)."""
     base = dict(U=3, V=3, H=8, W=8, scale=2, kb=3, blur_sigma=0.8,

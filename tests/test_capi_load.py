@@ -70,3 +70,19 @@ def test_precision_is_validated_without_gpu():
         lfsr.create(3, 3, 8, 8, 2, blur, disp, mu=1e-4, precision=lfsr.LFSR_FP16_STORAGE)
     assert e.value.code == lfsr.LFSR_EUNSUPPORTED
     assert "8192" in lfsr.last_error(None)
+
+
+def test_batch_arguments_are_validated_without_gpu():
+    import numpy as np
+    import pytest
+    blur = np.ones((3, 3), np.float32) / 9
+    disp = np.zeros((16, 16), np.float32)
+    job = dict(U=3, V=3, H=8, W=8, scale=2, blur=blur, disparity=disp)
+    with pytest.raises(lfsr.LfsrError) as e:
+        lfsr.Batch([])
+    assert e.value.code == lfsr.LFSR_EINVAL
+    # light fields of one batch share the solver constants
+    with pytest.raises(lfsr.LfsrError) as e:
+        lfsr.Batch([job, dict(job, mu=2.0)])
+    assert e.value.code == lfsr.LFSR_EINVAL
+    assert "share" in lfsr.batch_last_error(None)
