@@ -145,20 +145,35 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
 
   // the light field of the current unit (a CTA's contiguous range of units
   // may span several; all fields are block-uniform)
-  int jb = -1, unit0 = 0, j_end = 0;
-  int H = 0, W = 0, Hh = 0, Wh = 0, U = 1, tiles_x = 1, view0 = 0, nviews = 0, nvb = 1;
-  float hu = 0.f, hv = 0.f, scale = 0.f;
-  size_t q_lr = 0;
+  // the current light field's fields: kernel parameters (SINGLE) or a
+  // shared-memory copy of its table entry, read where used (block-uniform
+  // values that never occupy registers across the stages)
+  __shared__ JobArgs s_job;
+  // SINGLE: the fields and their derived values, computed once from the
+  // kernel parameters
+  const int p_H = one.H, p_W = one.W, p_Hh = one.Hh, p_Wh = one.Wh, p_U = one.U;
+  const int p_tiles_x = one.tiles_x, p_view0 = one.view0, p_nviews = one.nviews;
+  const int p_unit0 = one.unit0;
+  const float p_scale = one.scale;
+  const float* const p_src = one.src;
+  const float* const p_disp = one.disp;
+  float* const p_out = one.out;
+  const void* const p_y = one.y;
+  const void* const p_wA_old = one.wA_old;
+  void* const p_wA_new = one.wA_new;
+  const int p_nvb = (one.nviews + VB - 1) / VB;
+  const size_t p_qlr = (size_t)one.H * one.W;
+  const float p_hu = 0.5f * (float)(one.U - 1), p_hv = 0.5f * (float)(one.V - 1);
+#define JF(f) (SINGLE ? p_##f : s_job.f)
+#define JNVB (SINGLE ? p_nvb : (s_job.nviews + VB - 1) / VB)
+#define JQLR (SINGLE ? p_qlr : (size_t)s_job.H * s_job.W)
+#define JHU (SINGLE ? p_hu : 0.5f * (float)(s_job.U - 1))
+#define JHV (SINGLE ? p_hv : 0.5f * (float)(s_job.V - 1))
+  int jb = -1, j_end = 0;
   bool skip = false;
-  const float* src = nullptr;
-  const float* disp = nullptr;
-  float* out = nullptr;
-  const void* y = nullptr;
-  const void* wA_old = nullptr;
-  void* wA_new = nullptr;
   // angular offsets theta_k of view k = v U + u (Sec. 3.1)
-  auto tu_of = [&](int k) { return (float)(k % U) - hu; };
-  auto tv_of = [&](int k) { return (float)(k / U) - hv; };
+  auto tu_of = [&](int k) { return (float)(k % JF(U)) - JHU; };
+  auto tv_of = [&](int k) { return (float)(k / JF(U)) - JHV; };
 
   static_assert(VB == 2, "the sample and scatter stages handle view pairs");
   int cur_tile = -1;
@@ -177,12 +192,12 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
     const int warp = tid >> 5, lane = tid & 31;
     for (int ar = warp; ar < NAr_t; ar += FT_THREADS / 32) {
       const int hi = i0 - S + ar;
-      const bool row_in = hi >= 0 && hi < Hh;
+      const bool row_in = hi >= 0 && hi < JF(Hh);
       for (int ac = lane; ac < NAc_t; ac += 32) {
         const int hj = j0 - S + ac;
         const float v = sA[ar * NAc + ac];
-        if (row_in && hj >= 0 && hj < Wh && v != 0.f)
-          atomicAdd(out + (size_t)hi * Wh + hj, scale * v);
+        if (row_in && hj >= 0 && hj < JF(Wh) && v != 0.f)
+          atomicAdd(JF(out) + (size_t)hi * JF(Wh) + hj, JF(scale) * v);
         sA[ar * NAc + ac] = 0.f;
       }
     }
@@ -201,50 +216,26 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
     __syncthreads();
   };
 
-  // the fields of light field `jr` (a kernel parameter or a table entry;
-  // a macro, so that the parameter is read in place and never copied)
-#define LFSR_LOAD_JOB(jr)                                        \
-  do {                                                           \
-    H = (jr).H;                                                  \
-    W = (jr).W;                                                  \
-    Hh = (jr).Hh;                                                \
-    Wh = (jr).Wh;                                                \
-    U = (jr).U;                                                  \
-    hu = 0.5f * (float)((jr).U - 1);                             \
-    hv = 0.5f * (float)((jr).V - 1);                             \
-    tiles_x = (jr).tiles_x;                                      \
-    view0 = (jr).view0;                                          \
-    nviews = (jr).nviews;                                        \
-    nvb = (nviews + VB - 1) / VB;                                \
-    scale = (jr).scale;                                          \
-    unit0 = (jr).unit0;                                          \
-    j_end = unit0 + (jr).units;                                  \
-    q_lr = (size_t)H * W;                                        \
-    src = (jr).src;                                              \
-    disp = (jr).disp;                                            \
-    out = (jr).out;                                              \
-    y = (jr).y;                                                  \
-    wA_old = (jr).wA_old;                                        \
-    wA_new = (jr).wA_new;                                        \
-    skip = t.check_done && ((volatile int*)&(jr).sc->cg_done)[0]; \
-  } while (0)
   if (SINGLE) {
     jb = 0;
-    LFSR_LOAD_JOB(one);
+    j_end = units;
+    skip = t.check_done && ((volatile int*)&one.sc->cg_done)[0];
   }
 
   for (int u = u_begin; u < u_end; ++u) {
     if (!SINGLE && u >= j_end) {
       if (jb >= 0) end_job();
       jb = table_job(t, u);
-      const JobArgs& jr = t.jobs[jb];
-      LFSR_LOAD_JOB(jr);
+      if (tid == 0) s_job = t.jobs[jb];
+      __syncthreads();
+      j_end = s_job.unit0 + s_job.units;
+      skip = t.check_done && ((volatile int*)&s_job.sc->cg_done)[0];
     }
     if (skip) continue;
-    const int ul = u - unit0;
-    const int tile = ul / nvb;
-    const int kbase = view0 + VB * (ul - tile * nvb);
-    const int nv = min(VB, view0 + nviews - kbase);   // views of this unit
+    const int ul = u - JF(unit0);
+    const int tile = ul / JNVB;
+    const int kbase = JF(view0) + VB * (ul - tile * JNVB);
+    const int nv = min(VB, JF(view0) + JF(nviews) - kbase);   // views of this unit
     if (tile != cur_tile) {
       __syncthreads();
       if (cur_tile >= 0 && MODE != OP_FWD) {
@@ -252,14 +243,14 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
         __syncthreads();
       }
       cur_tile = tile;
-      const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+      const int ty = tile / JF(tiles_x), tx = tile - ty * JF(tiles_x);
       i0 = ty * T;
       j0 = tx * T;
-      const int TRr = min(T, Hh - i0), TRc = min(T, Wh - j0);
+      const int TRr = min(T, JF(Hh) - i0), TRc = min(T, JF(Wh) - j0);
       lr_lo = max(0, ceil_div(i0 - R, Z));
-      lr_n = min(H - 1, floor_div(i0 + TRr - 1 + R, Z)) - lr_lo + 1;
+      lr_n = min(JF(H) - 1, floor_div(i0 + TRr - 1 + R, Z)) - lr_lo + 1;
       lc_lo = max(0, ceil_div(j0 - R, Z));
-      lc_n = min(W - 1, floor_div(j0 + TRc - 1 + R, Z)) - lc_lo + 1;
+      lc_n = min(JF(W) - 1, floor_div(j0 + TRc - 1 + R, Z)) - lc_lo + 1;
       e_r0 = Z * lr_lo - R;
       e_c0 = Z * lc_lo - R;
       NAr_t = TRr + 2 * S + 1;
@@ -273,23 +264,23 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
           const int np = NE + 2 * S + 1;
           for (int pr = warp; pr < np; pr += NWARP) {
             const int hi = e_r0 - S + pr;
-            const bool row_in = hi >= 0 && hi < Hh;
-            const float* src_row = src + (size_t)(row_in ? hi : 0) * Wh;
+            const bool row_in = hi >= 0 && hi < JF(Hh);
+            const float* src_row = JF(src) + (size_t)(row_in ? hi : 0) * JF(Wh);
             for (int pc = lane; pc < np; pc += 32) {
               const int hj = e_c0 - S + pc;
-              const bool ok = row_in && hj >= 0 && hj < Wh;
-              cp_async_f32(sP + pr * NPc + pc, ok ? src_row + hj : src, ok);
+              const bool ok = row_in && hj >= 0 && hj < JF(Wh);
+              cp_async_f32(sP + pr * NPc + pc, ok ? src_row + hj : JF(src), ok);
             }
           }
         }
         for (int er = warp; er < NE; er += NWARP) {
           const int hi = e_r0 + er;
-          const bool row_in = hi >= 0 && hi < Hh;
-          const float* d_row = disp + (size_t)(row_in ? hi : 0) * Wh;
+          const bool row_in = hi >= 0 && hi < JF(Hh);
+          const float* d_row = JF(disp) + (size_t)(row_in ? hi : 0) * JF(Wh);
           for (int ec = lane; ec < NE; ec += 32) {
             const int hj = e_c0 + ec;
-            const bool ok = row_in && hj >= 0 && hj < Wh;
-            cp_async_f32(sO + er * NEp + ec, ok ? d_row + hj : disp, ok);
+            const bool ok = row_in && hj >= 0 && hj < JF(Wh);
+            cp_async_f32(sO + er * NEp + ec, ok ? d_row + hj : JF(disp), ok);
           }
         }
         cp_async_wait_all();
@@ -323,9 +314,9 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
           pre_y[it][o] = 0u;
           pre_w[it][o] = 0u;
           if (v < nv && lr < lr_n && lc < lc_n) {
-            const size_t gi = (size_t)(kbase + v) * q_lr + (size_t)(lr_lo + lr) * W + (lc_lo + lc);
-            pre_y[it][o] = ld_raw_kind(y, gi, g.st_y);
-            pre_w[it][o] = ld_raw_kind(wA_old, gi, g.st);
+            const size_t gi = (size_t)(kbase + v) * JQLR + (size_t)(lr_lo + lr) * JF(W) + (lc_lo + lc);
+            pre_y[it][o] = ld_raw_kind(JF(y), gi, g.st_y);
+            pre_w[it][o] = ld_raw_kind(JF(wA_old), gi, g.st);
           }
         }
       }
@@ -420,7 +411,7 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
             if (MODE == OP_NORMAL) {
               if (owned) psum = fmaf(acc, acc, psum);
             } else if (MODE == OP_DATA) {
-              const size_t gi = (size_t)k * q_lr + (size_t)gr * W + gc;
+              const size_t gi = (size_t)k * JQLR + (size_t)gr * JF(W) + gc;
               const float yv = raw_to_float(pre_y[it][o], g.st_y);
               const float wa = raw_to_float(pre_w[it][o], g.st);
               const float res = acc - yv;
@@ -429,12 +420,12 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
               const float f = 2.f * wn - wa;
               h = fmaf(g.lambda2, res, 0.5f * g.mu * g.lambda1 * f);
               if (owned) {
-                st_kind(wA_new, gi, g.st, wn);
+                st_kind(JF(wA_new), gi, g.st, wn);
                 const float dd = wn - wa;
                 psum = fmaf(dd, dd, psum);
               }
             } else if (MODE == OP_FWD) {
-              if (owned) out[(size_t)k * q_lr + (size_t)gr * W + gc] = acc;
+              if (owned) JF(out)[(size_t)k * JQLR + (size_t)gr * JF(W) + gc] = acc;
             }
           }
           sG[v * SH::GS + (lr + MG) * NGp + (lc + MG)] = h;
@@ -448,7 +439,7 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
         const int lr = r0 / NL, lc = r0 - lr * NL;
         float val = 0.f;
         if (lr < lr_n && lc < lc_n)
-          val = __ldg(src + (size_t)(kbase + v) * q_lr + (size_t)(lr_lo + lr) * W + (lc_lo + lc));
+          val = __ldg(JF(src) + (size_t)(kbase + v) * JQLR + (size_t)(lr_lo + lr) * JF(W) + (lc_lo + lc));
         sG[v * SH::GS + (lr + MG) * NGp + (lc + MG)] = val;
       }
     }
@@ -492,8 +483,8 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
     // 5. adjoint blur, columns (polyphase), then the bilinear scatter W_k^T;
     //    lanes along rows; one task covers the same pixels in both views
     const int n_lo = floor_div(j0, Z);
-    const int TRr = min(T, Hh - i0);
-    const bool full_cols = j0 + T <= Wh;
+    const int TRr = min(T, JF(Hh) - i0);
+    const bool full_cols = j0 + T <= JF(Wh);
     const float tu0 = tu_of(kbase), tv0 = tv_of(kbase);
     const int k1 = kbase + (nv > 1 ? 1 : 0);
     const float tu1 = tu_of(k1), tv1 = tv_of(k1);
@@ -578,7 +569,7 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
 #pragma unroll
           for (int ph = 0; ph < Z; ++ph) {
             const int hj = Z * (n0 + o) + ph;
-            if (hj >= j0 && hj < j0 + T && hj < Wh) pixel(o, ph);
+            if (hj >= j0 && hj < j0 + T && hj < JF(Wh)) pixel(o, ph);
           }
       }
       if (pend0) {
@@ -621,7 +612,11 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
       }
     }
   }
-#undef LFSR_LOAD_JOB
+#undef JF
+#undef JNVB
+#undef JQLR
+#undef JHU
+#undef JHV
 }
 
 // (Z, KB) pairs with a specialised kernel.

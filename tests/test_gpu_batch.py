@@ -19,14 +19,14 @@ GEOMS = [
     dict(U=1, V=1, H=25, W=22, scale=2, kb=5, blur_sigma=1.0, disparities=(0.0, 0.4)),
     dict(U=3, V=5, H=11, W=30, scale=3, kb=7, blur_sigma=1.3, disparities=(-0.5, 1.5)),
 ]
-SOLVER = dict(lambda1=1.0, lambda2=4.0, mu=1.0, nltv_window=5, nltv_patch=3, nltv_h=0.3,
+SOLVER = dict(lambda1=2.0, lambda2=4.0, mu=300.0, nltv_window=5, nltv_patch=3, nltv_h=0.1,
               cg_iters=5, cg_tol=0.0)
 
 
 def _jobs(precision="fp32"):
     probs, kws = [], []
     for i, gm in enumerate(GEOMS):
-        wl = synth.custom(window=5, patch=3, h=0.3, **gm)
+        wl = synth.custom(window=5, patch=3, **gm)
         pr = synth.make_problem(wl, seed=20 + i)
         probs.append(pr)
         kws.append(dict(U=wl.U, V=wl.V, H=wl.H, W=wl.W, scale=wl.scale, blur=f32(pr.blur),
@@ -70,8 +70,8 @@ def test_batch_equals_each_light_field_alone_and_the_oracle():
         xa = _alone(kw, pr, n_iter)
         assert rel_err(xb, xa) <= 1e-5, j
         o = om.Oracle(kw["U"], kw["V"], kw["H"], kw["W"], kw["scale"], f32(pr.blur).astype(np.float64),
-                      f32(pr.disparity).astype(np.float64), lambda1=1.0, lambda2=4.0, mu=1.0,
-                      window=5, patch=3, h=0.3, cg_iters=5, cg_tol=0.0)
+                      f32(pr.disparity).astype(np.float64), lambda1=2.0, lambda2=4.0, mu=300.0,
+                      window=5, patch=3, h=0.1, cg_iters=5, cg_tol=0.0)
         ref, _, _ = o.admm(f32(pr.y).astype(np.float64), f32(pr.x0).astype(np.float64), n_iter)
         assert rel_err(xb, ref) <= 1e-4, j
         st = b.stats(j)

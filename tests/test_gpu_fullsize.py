@@ -3,8 +3,8 @@ times (graph-captured lfsr_load + lfsr_iterate on the same plan).
 
 * every operator of one ADMM iteration at full size against the oracle;
 * the first iterations of the 9x9-view x2 and x3 light fields against the
-  oracle (the configured h = 0.1 amplifies perturbations over long runs, so
-  full-N comparison is done in the stable h = 0.3 regime, opt-in as slow);
+  oracle, and the whole 100-iteration solve of the 9x9-view x2 light field
+  at its configured h = 0.1 (the x3 one opt-in as slow: minutes of oracle);
 * properties that hold at any N: a constant image stays fixed, duals stay in
   [-1/mu, 1/mu].
 """
@@ -84,22 +84,32 @@ def test_full_size_constant_image_and_dual_bounds():
     wA = c.empty(o.s_k, wl.H, wl.W)
     wS = c.empty(o.s_d, *o.hr)
     lfsr.get_state(c.h, None, wA, wS)
-    t = 1.0 / wl.mu
+    t = float(np.float32(1.0 / wl.mu))          # the kernels' float threshold
     assert c.np(wA).max() <= t and c.np(wA).min() >= -t
     assert c.np(wS).max() <= t and c.np(wS).min() >= -t
     assert lfsr.stats(c.h)["status"] == 0
     c.solver.close()
 
 
-@pytest.mark.slow
-@pytest.mark.skipif(os.environ.get("LFSR_SLOW") != "1", reason="set LFSR_SLOW=1 (minutes of oracle)")
-def test_full_size_full_N_stable_regime():
-    wl = synth.WORKLOADS["lf9x9_256_x2"]
-    c = Case(wl, seed=2000, h=0.3)
+def _full_n(name, seed):
+    wl = synth.WORKLOADS[name]
+    c = Case(wl, seed=seed)
     x = c.empty(*c.oracle.hr)
     lfsr.solve(c.h, c.t(c.y), wl.iterations, c.t(c.x0), x)
     ref, _, _ = c.oracle.admm(c.y.astype(np.float64), c.x0.astype(np.float64), wl.iterations)
     gx = c.np(x)
     assert rel_err(gx, ref) <= 1e-4
     assert abs(synth.psnr(gx, c.prob.gt) - synth.psnr(ref, c.prob.gt)) <= 0.01
+    assert synth.psnr(ref, c.prob.gt) > synth.psnr(c.x0, c.prob.gt) + 3.0
     c.solver.close()
+
+
+def test_full_size_full_N_lf9x9_256_x2():
+    """The benchmark workload, all 100 iterations at its configured h = 0.1."""
+    _full_n("lf9x9_256_x2", 2000)
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("LFSR_SLOW") != "1", reason="set LFSR_SLOW=1 (minutes of oracle)")
+def test_full_size_full_N_lf9x9_200_x3():
+    _full_n("lf9x9_200_x3", 3000)

@@ -138,9 +138,9 @@ def test_quality_improves_over_iterations(oracle_mod):
                       disparities=(-1.0, 0.0, 0.8), noise_sigma=0.02, impulse=0.05,
                       window=5, iterations=10)
     prob = synth.make_problem(wl, seed=11)
-    o = oracle_mod.Oracle.from_problem(prob, h=0.3)
-    x1, wA, wS = o.admm(prob.y, prob.x0, 1)
-    x5, _, _ = o.admm(prob.y, x1, 4, wA=wA, wS=wS)
-    p0, p1, p5 = (synth.psnr(v, prob.gt) for v in (prob.x0, x1, x5))
-    assert p5 > p0 + 1.5
-    assert p5 > p1 + 1.0
+    o = oracle_mod.Oracle.from_problem(prob)       # the configured h = 0.1
+    x20, wA, wS = o.admm(prob.y, prob.x0, 20)
+    x40, _, _ = o.admm(prob.y, x20, 20, wA=wA, wS=wS)
+    p0, p20, p40 = (synth.psnr(v, prob.gt) for v in (prob.x0, x20, x40))
+    assert p20 > p0 + 1.5
+    assert p40 > p20 + 1.0
