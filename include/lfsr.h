@@ -263,6 +263,26 @@ int lfsr_batch_stats(const lfsr_batch *b, int job, lfsr_stats_t *out);
 /* Kernel launches per ADMM iteration of the whole batch. */
 int lfsr_batch_launches_per_iteration(const lfsr_batch *b);
 
+/* Autotuner: times, on the loaded light fields, the candidate tile shapes
+ * of the operator kernel (64 x 64 and 32 x 32 HR pixels per work unit) for
+ * each group of light fields sharing scale and blur, and the stencil
+ * blocking of the NLTV divergence kernel (6 or 3 window directions per batch
+ * of weight loads), and keeps the fastest of each.  It runs about
+ * 3 x (candidate tiles) x (groups) + 4 ADMM iterations on the loaded state,
+ * which therefore has to be loaded again (lfsr_batch_load) before a solve
+ * whose result matters.  Synchronous. */
+int lfsr_batch_autotune(lfsr_batch *b);
+
+/* The current choices: op_tile[g] for g < min(groups, max_groups) and
+ * *nla_chunk (either pointer may be NULL).  Returns the number of operator
+ * groups (0 for NULL). */
+int lfsr_batch_tuning(const lfsr_batch *b, int *op_tile, int max_groups, int *nla_chunk);
+
+/* Sets the choices directly (e.g. ones saved from an earlier autotune):
+ * op_tile holds one tile side (64 or 32) per operator group, in the order
+ * lfsr_batch_tuning reports them; nla_chunk is 6 or 3. */
+int lfsr_batch_set_tuning(lfsr_batch *b, const int *op_tile, int n_groups, int nla_chunk);
+
 /* Profiling mode (as lfsr_set_profiling): lfsr_batch_iterate launches one by
  * one with CUDA events around each launch; lfsr_batch_kernel_times
  * synchronises and returns the summed milliseconds and launch counts by

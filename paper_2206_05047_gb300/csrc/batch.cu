@@ -7,7 +7,9 @@
 // the scale and the blur for the operator phases (the operator kernel is
 // compiled per (scale, blur size)).  Two iterations are captured as one CUDA
 // graph.  Each light field keeps its own state (an lfsr_handle), so loading,
-// reading and diagnostics reuse the single-light-field entry points.
+// reading and diagnostics reuse the single-light-field entry points.  An
+// autotuner picks, on the batch's own data, the operator tile side of each
+// group and the NLTV-apply direction chunk (lfsr_batch_autotune).
 #include <cstring>
 #include <new>
 #include <string>
@@ -23,11 +25,14 @@ thread_local std::string t_batch_err = "no error";
 
 struct Group {
   Geom g{};                 // constants of the group; S = the largest shift bound
-  OpPlan P{};
+  OpPlan P{};               // plan of the chosen tile side (P.TH)
+  int tile = FAST_TILE;     // operator tile side (autotuned: 64 or 32)
   int grid = 0;
   int units = 0;
   std::vector<int> members; // indices into lfsr_batch::jobs
   std::vector<int> unit0;   // first operator unit of each member
+  std::vector<int> units_m; // operator units of each member at this tile side
+  std::vector<int> tiles_x; // tile columns of each member at this tile side
 };
 
 }  // namespace
@@ -37,7 +42,9 @@ struct lfsr_batch {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   int sm_count = 0;
+  int smem_limit = 0;
   int cg_iters = 0;
+  int nla_chunk = NLA_CHUNK; // NLTV-apply direction chunk (autotuned: 6 or 3)
   Geom g{};                 // solver constants shared by all light fields
   std::vector<Group> groups;
   int nl_total = 0, vec_total = 0, vec_chunk = 0;
@@ -48,6 +55,7 @@ struct lfsr_batch {
   int* maps = nullptr;
   double* partials = nullptr;
   size_t part_stride = 0;
+  size_t cap_tables = 0, cap_maps = 0, cap_partials = 0;   // allocated entries
   unsigned int* counters = nullptr;
   // table offsets (entries): all light fields for the NLTV / vector launches,
   // the members of each group for the operator launches
@@ -124,31 +132,32 @@ TableArgs table(lfsr_batch* b, int offset, int n, int units, int map_offset, int
   return t;
 }
 
-// One ADMM iteration of every light field of the batch at parity pa; in
-// profiling mode each launch is bracketed by events (class = launch kind).
-cudaError_t batch_iteration(lfsr_batch* b, int pa, cudaStream_t s, bool prof) {
+// One ADMM iteration of every light field of the batch at parity pa.  With
+// a sink, each launch is bracketed by events (class = launch kind, grp =
+// operator group).
+cudaError_t batch_iteration(lfsr_batch* b, int pa, cudaStream_t s, std::vector<ProfEvent>* sink) {
   const int n = (int)b->jobs.size();
   const int G = (int)b->groups.size();
   auto ctr = [&](int kind, int gi) { return kind * (G + 1) + gi; };
-  auto run = [&](int cls, auto&& launch) -> cudaError_t {
-    if (!prof) return launch();
-    ProfEvent ev{cls, nullptr, nullptr};
+  auto run = [&](int cls, int grp, auto&& launch) -> cudaError_t {
+    if (!sink) return launch();
+    ProfEvent ev{cls, nullptr, nullptr, grp};
     cudaError_t e = cudaEventCreate(&ev.a);
     if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
     if (e != cudaSuccess) return e;
     cudaEventRecord(ev.a, s);
     e = launch();
     cudaEventRecord(ev.b, s);
-    b->prof.push_back(ev);
+    sink->push_back(ev);
     return e;
   };
-  cudaError_t e = run(KD_NLW, [&] {
+  cudaError_t e = run(KD_NLW, 0, [&] {
     return nlw2_launch(
         1, b->g, table(b, b->t_nlw[pa], n, b->nl_total, b->m_nl, KD_NLW, ctr(KD_NLW, G), 0), s);
   });
   for (int gi = 0; gi < G && e == cudaSuccess; ++gi) {
     const Group& gr = b->groups[gi];
-    e = run(KD_DATA, [&] {
+    e = run(KD_DATA, gi, [&] {
       return fast_launch(OP_DATA, gr.g, gr.P,
                          table(b, b->t_data[pa][gi], (int)gr.members.size(), gr.units,
                                b->m_op[gi], KD_DATA, ctr(KD_DATA, gi), 0),
@@ -156,21 +165,21 @@ cudaError_t batch_iteration(lfsr_batch* b, int pa, cudaStream_t s, bool prof) {
     });
   }
   if (e == cudaSuccess)
-    e = run(KD_INIT, [&] {
+    e = run(KD_INIT, 0, [&] {
       return cg_init_nltv_launch(
           b->g, table(b, b->t_init[pa], n, b->vec_total, b->m_vec, KD_INIT, ctr(KD_INIT, G), 0),
           s);
     });
   for (int k = 0; k < b->cg_iters && e == cudaSuccess; ++k) {
     const int pb = k & 1;
-    e = run(KD_NLA, [&] {
+    e = run(KD_NLA, 0, [&] {
       return nla2_launch(
           b->g, table(b, b->t_nla[pa][pb], n, b->nl_total, b->m_nl, KD_NLA, ctr(KD_NLA, G), 1),
-          s);
+          s, b->nla_chunk);
     });
     for (int gi = 0; gi < G && e == cudaSuccess; ++gi) {
       const Group& gr = b->groups[gi];
-      e = run(KD_NORMAL, [&] {
+      e = run(KD_NORMAL, gi, [&] {
         return fast_launch(OP_NORMAL, gr.g, gr.P,
                            table(b, b->t_norm[pa][pb][gi], (int)gr.members.size(), gr.units,
                                  b->m_op[gi], KD_NORMAL, ctr(KD_NORMAL, gi), 1),
@@ -178,7 +187,7 @@ cudaError_t batch_iteration(lfsr_batch* b, int pa, cudaStream_t s, bool prof) {
       });
     }
     if (e == cudaSuccess)
-      e = run(KD_UPDATE, [&] {
+      e = run(KD_UPDATE, 0, [&] {
         return cg_update_launch(b->g,
                                 table(b, b->t_upd[pa][pb], n, b->vec_total, b->m_vec, KD_UPDATE,
                                       ctr(KD_UPDATE, G), 0),
@@ -194,7 +203,7 @@ cudaError_t batch_graph(lfsr_batch* b, int first_parity, int n, cudaGraphExec_t*
   if (e != cudaSuccess) return e;
   cudaError_t el = cudaSuccess;
   for (int i = 0; i < n && el == cudaSuccess; ++i)
-    el = batch_iteration(b, (first_parity + i) & 1, b->cap_stream, false);
+    el = batch_iteration(b, (first_parity + i) & 1, b->cap_stream, nullptr);
   e = cudaStreamEndCapture(b->cap_stream, &graph);
   if (el != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -203,6 +212,135 @@ cudaError_t batch_graph(lfsr_batch* b, int first_parity, int n, cudaGraphExec_t*
   if (e != cudaSuccess) return e;
   e = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
+  return e;
+}
+
+// Operator tile side of group gr: plan, per-member tiling and units, grid.
+cudaError_t set_tile(lfsr_batch* b, Group& gr, int tile) {
+  OpPlan P{};
+  cudaError_t e = fast_plan_table(gr.g, &P, b->smem_limit, tile);
+  if (e != cudaSuccess) return e;
+  gr.P = P;
+  gr.tile = tile;
+  gr.units = 0;
+  gr.unit0.clear();
+  gr.units_m.clear();
+  gr.tiles_x.clear();
+  for (int j : gr.members) {
+    const lfsr_handle* h = b->jobs[j];
+    const int tx = (h->g.Wh + tile - 1) / tile, ty = (h->g.Hh + tile - 1) / tile;
+    const int um = tx * ty * ((h->g.sk + FAST_VIEWS - 1) / FAST_VIEWS);
+    gr.unit0.push_back(gr.units);
+    gr.units_m.push_back(um);
+    gr.tiles_x.push_back(tx);
+    gr.units += um;
+  }
+  gr.grid = op_grid(gr.P, gr.units, b->sm_count);
+  return cudaSuccess;
+}
+
+// Builds the job tables and unit maps of every launch for the current tile
+// sides, uploads them (growing the device buffers when needed) and drops
+// the captured graphs, which hold the old launch shapes.
+cudaError_t build_tables(lfsr_batch* b) {
+  const int n = (int)b->jobs.size();
+  std::vector<JobArgs> tabs;
+  auto vec_job = [&](int j, int kind, int pa, int pb) {
+    JobArgs a = make_job(b->jobs[j], kind, pa, pb, b->vec_unit0[j]);
+    a.chunk = b->vec_chunk;
+    a.units = b->vec_units[j];
+    return a;
+  };
+  auto op_job = [&](const Group& gr, size_t m, int kind, int pa, int pb) {
+    JobArgs a = make_job(b->jobs[gr.members[m]], kind, pa, pb, gr.unit0[m]);
+    a.units = gr.units_m[m];
+    a.tiles_x = gr.tiles_x[m];
+    return a;
+  };
+  for (int pa = 0; pa < 2; ++pa) {
+    b->t_data[pa].clear();
+    for (int pb = 0; pb < 2; ++pb) b->t_norm[pa][pb].clear();
+    b->t_nlw[pa] = (int)tabs.size();
+    for (int j = 0; j < n; ++j) tabs.push_back(make_job(b->jobs[j], KD_NLW, pa, 0, b->nl_unit0[j]));
+    b->t_init[pa] = (int)tabs.size();
+    for (int j = 0; j < n; ++j) tabs.push_back(vec_job(j, KD_INIT, pa, 0));
+    for (int pb = 0; pb < 2; ++pb) {
+      b->t_nla[pa][pb] = (int)tabs.size();
+      for (int j = 0; j < n; ++j) tabs.push_back(make_job(b->jobs[j], KD_NLA, pa, pb, b->nl_unit0[j]));
+      b->t_upd[pa][pb] = (int)tabs.size();
+      for (int j = 0; j < n; ++j) tabs.push_back(vec_job(j, KD_UPDATE, pa, pb));
+    }
+    for (const Group& gr : b->groups) {
+      b->t_data[pa].push_back((int)tabs.size());
+      for (size_t m = 0; m < gr.members.size(); ++m) tabs.push_back(op_job(gr, m, KD_DATA, pa, 0));
+      for (int pb = 0; pb < 2; ++pb) {
+        b->t_norm[pa][pb].push_back((int)tabs.size());
+        for (size_t m = 0; m < gr.members.size(); ++m)
+          tabs.push_back(op_job(gr, m, KD_NORMAL, pa, pb));
+      }
+    }
+  }
+  std::vector<int> maps;
+  b->m_nl = (int)maps.size();
+  for (int j = 0; j < n; ++j) maps.insert(maps.end(), b->jobs[j]->nl_units, j);
+  b->m_vec = (int)maps.size();
+  for (int j = 0; j < n; ++j) maps.insert(maps.end(), b->vec_units[j], j);
+  b->m_op.clear();
+  for (const Group& gr : b->groups) {
+    b->m_op.push_back((int)maps.size());
+    for (size_t m = 0; m < gr.members.size(); ++m) maps.insert(maps.end(), gr.units_m[m], (int)m);
+  }
+  // reduction slots: operator launches n_members x grid, the others one per unit
+  size_t stride = (size_t)b->nl_total;
+  if ((size_t)b->vec_total > stride) stride = b->vec_total;
+  for (const Group& gr : b->groups)
+    if (gr.members.size() * (size_t)gr.grid > stride) stride = gr.members.size() * (size_t)gr.grid;
+  b->part_stride = stride;
+  cudaError_t e = cudaStreamSynchronize(b->stream);   // no launch may still read the old tables
+  auto grow = [&](auto** buf, size_t* cap, size_t need, size_t elem) {
+    if (e != cudaSuccess || need <= *cap) return;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    e = cudaMalloc((void**)buf, need * elem);
+    if (e == cudaSuccess) *cap = need;
+  };
+  grow(&b->tables, &b->cap_tables, tabs.size(), sizeof(JobArgs));
+  grow(&b->maps, &b->cap_maps, maps.size(), sizeof(int));
+  grow(&b->partials, &b->cap_partials, KD_NUM * stride, sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->tables, tabs.data(), tabs.size() * sizeof(JobArgs),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (b->graph_pair) cudaGraphExecDestroy(b->graph_pair);
+  b->graph_pair = nullptr;
+  for (auto& gs : b->graph_single) {
+    if (gs) cudaGraphExecDestroy(gs);
+    gs = nullptr;
+  }
+  return e;
+}
+
+// Device time of one iteration's launches that match (cls, grp) (grp < 0:
+// any group); the iteration runs at the current parity and advances it.
+cudaError_t time_iteration(lfsr_batch* b, int cls, int grp, double* ms) {
+  std::vector<ProfEvent> ev;
+  cudaError_t e = batch_iteration(b, b->parity, b->stream, &ev);
+  b->parity ^= 1;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  double t = 0.0;
+  for (auto& x : ev) {
+    float m = 0.f;
+    if (e == cudaSuccess && x.cls == cls && (grp < 0 || x.grp == grp))
+      e = cudaEventElapsedTime(&m, x.a, x.b);
+    t += m;
+    cudaEventDestroy(x.a);
+    cudaEventDestroy(x.b);
+  }
+  *ms = t;
   return e;
 }
 
@@ -249,6 +387,7 @@ int lfsr_batch_create(const lfsr_params* params, int n, void* cuda_stream, lfsr_
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                          b->jobs[0]->device);
+  b->smem_limit = optin - 1024;
   // operator groups: shared scale and blur; the layout takes the group's
   // largest shift bound
   for (int j = 0; j < n && e == cudaSuccess; ++j) {
@@ -261,19 +400,16 @@ int lfsr_batch_create(const lfsr_params* params, int n, void* cuda_stream, lfsr_
     }
     Group& gr = b->groups[gi];
     if (gj.S > gr.g.S) gr.g.S = gj.S;
-    gr.unit0.push_back(gr.units);
     gr.members.push_back(j);
-    gr.units += b->jobs[j]->op_units;
   }
   for (Group& gr : b->groups) {
     if (e != cudaSuccess) break;
-    if (fast_plan(gr.g, &gr.P, optin - 1024) != cudaSuccess) {
+    if (set_tile(b, gr, FAST_TILE) != cudaSuccess) {
       batch_free(b);
       delete b;
       return bfail(nullptr, LFSR_EUNSUPPORTED,
                    "disparity * angular offset too large for the shared-memory tile");
     }
-    gr.grid = op_grid(gr.P, gr.units, b->sm_count);
   }
   // vector kernels: one chunk size for the batch, about two CTAs per SM in
   // all (plus at most one partial chunk per light field)
@@ -293,67 +429,12 @@ int lfsr_batch_create(const lfsr_params* params, int n, void* cuda_stream, lfsr_
     b->vec_units.push_back(vu);
     b->vec_total += vu;
   }
-  // host tables and maps
-  std::vector<JobArgs> tabs;
-  auto vec_job = [&](int j, int kind, int pa, int pb) {
-    JobArgs a = make_job(b->jobs[j], kind, pa, pb, b->vec_unit0[j]);
-    a.chunk = b->vec_chunk;
-    a.units = b->vec_units[j];
-    return a;
-  };
-  for (int pa = 0; pa < 2; ++pa) {
-    b->t_nlw[pa] = (int)tabs.size();
-    for (int j = 0; j < n; ++j) tabs.push_back(make_job(b->jobs[j], KD_NLW, pa, 0, b->nl_unit0[j]));
-    b->t_init[pa] = (int)tabs.size();
-    for (int j = 0; j < n; ++j) tabs.push_back(vec_job(j, KD_INIT, pa, 0));
-    for (int pb = 0; pb < 2; ++pb) {
-      b->t_nla[pa][pb] = (int)tabs.size();
-      for (int j = 0; j < n; ++j) tabs.push_back(make_job(b->jobs[j], KD_NLA, pa, pb, b->nl_unit0[j]));
-      b->t_upd[pa][pb] = (int)tabs.size();
-      for (int j = 0; j < n; ++j) tabs.push_back(vec_job(j, KD_UPDATE, pa, pb));
-    }
-    for (const Group& gr : b->groups) {
-      b->t_data[pa].push_back((int)tabs.size());
-      for (size_t m = 0; m < gr.members.size(); ++m)
-        tabs.push_back(make_job(b->jobs[gr.members[m]], KD_DATA, pa, 0, gr.unit0[m]));
-      for (int pb = 0; pb < 2; ++pb) {
-        b->t_norm[pa][pb].push_back((int)tabs.size());
-        for (size_t m = 0; m < gr.members.size(); ++m)
-          tabs.push_back(make_job(b->jobs[gr.members[m]], KD_NORMAL, pa, pb, gr.unit0[m]));
-      }
-    }
-  }
-  std::vector<int> maps;
-  b->m_nl = (int)maps.size();
-  for (int j = 0; j < n; ++j) maps.insert(maps.end(), b->jobs[j]->nl_units, j);
-  b->m_vec = (int)maps.size();
-  for (int j = 0; j < n; ++j) maps.insert(maps.end(), b->vec_units[j], j);
-  for (const Group& gr : b->groups) {
-    b->m_op.push_back((int)maps.size());
-    for (size_t m = 0; m < gr.members.size(); ++m)
-      maps.insert(maps.end(), b->jobs[gr.members[m]]->op_units, (int)m);
-  }
-  // reduction slots: operator launches n_members x grid, the others one per unit
-  size_t stride = (size_t)b->nl_total;
-  if ((size_t)b->vec_total > stride) stride = b->vec_total;
-  for (const Group& gr : b->groups)
-    if (gr.members.size() * (size_t)gr.grid > stride) stride = gr.members.size() * (size_t)gr.grid;
-  b->part_stride = stride;
   const size_t n_counters = (size_t)KD_NUM * (b->groups.size() + 1);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->tables, tabs.size() * sizeof(JobArgs));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->maps, maps.size() * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->partials, KD_NUM * stride * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->counters, n_counters * sizeof(unsigned int));
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->tables, tabs.data(), tabs.size() * sizeof(JobArgs),
-                        cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice,
-                        b->stream);
-  if (e == cudaSuccess)
     e = cudaMemsetAsync(b->counters, 0, n_counters * sizeof(unsigned int), b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = build_tables(b);
   if (e != cudaSuccess) {
     const std::string msg = std::string("lfsr_batch_create: ") + cudaGetErrorString(e);
     batch_free(b);
@@ -392,7 +473,7 @@ int lfsr_batch_iterate(lfsr_batch* b, int iterations) {
   cudaError_t e = cudaSuccess;
   if (b->profiling) {
     for (; left > 0 && e == cudaSuccess; --left) {
-      e = batch_iteration(b, b->parity, b->stream, true);
+      e = batch_iteration(b, b->parity, b->stream, &b->prof);
       b->parity ^= 1;
     }
   }
@@ -467,6 +548,81 @@ int lfsr_batch_kernel_times(lfsr_batch* b, double* ms, int64_t* launches) {
     ms[c] = b->prof_ms[c];
     launches[c] = b->prof_n[c];
   }
+  return LFSR_OK;
+}
+
+int lfsr_batch_autotune(lfsr_batch* b) {
+  if (!b) return bfail(nullptr, LFSR_EINVAL, "batch is NULL");
+  cudaError_t e = cudaSuccess;
+  double t = 0.0;
+  // operator tile side, group by group: the data block and the normal-matrix
+  // launches of the group, timed on one iteration after one warm-up
+  for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+    Group& gr = b->groups[gi];
+    int best = gr.tile;
+    double best_ms = 1e300;
+    for (int tile : {64, 32}) {
+      if (set_tile(b, gr, tile) != cudaSuccess) continue;   // layout too large
+      e = build_tables(b);
+      double ms_data = 0.0, ms_norm = 0.0;
+      if (e == cudaSuccess) e = time_iteration(b, KD_NORMAL, (int)gi, &t);
+      if (e == cudaSuccess) e = time_iteration(b, KD_NORMAL, (int)gi, &ms_norm);
+      if (e == cudaSuccess) e = time_iteration(b, KD_DATA, (int)gi, &ms_data);
+      if (e == cudaSuccess && ms_norm + ms_data < best_ms) {   // per-iteration operator time
+        best_ms = ms_norm + ms_data;
+        best = tile;
+      }
+    }
+    if (e == cudaSuccess && set_tile(b, gr, best) != cudaSuccess) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = build_tables(b);
+  }
+  // NLTV-apply direction chunk
+  if (e == cudaSuccess) {
+    int best = b->nla_chunk;
+    double best_ms = 1e300;
+    for (int chunk : {6, 3}) {
+      b->nla_chunk = chunk;
+      double ms = 0.0;
+      e = time_iteration(b, KD_NLA, -1, &t);
+      if (e == cudaSuccess) e = time_iteration(b, KD_NLA, -1, &ms);
+      if (e != cudaSuccess) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = chunk;
+      }
+    }
+    b->nla_chunk = best;
+    if (e == cudaSuccess) e = build_tables(b);   // drops the graphs of the old shapes
+  }
+  for (lfsr_handle* h : b->jobs) h->parity = b->parity;
+  if (e != cudaSuccess)
+    return bfail(b, LFSR_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  return LFSR_OK;
+}
+
+int lfsr_batch_tuning(const lfsr_batch* b, int* op_tile, int max_groups, int* nla_chunk) {
+  if (!b) return 0;
+  const int G = (int)b->groups.size();
+  for (int gi = 0; gi < G && gi < max_groups && op_tile; ++gi) op_tile[gi] = b->groups[gi].tile;
+  if (nla_chunk) *nla_chunk = b->nla_chunk;
+  return G;
+}
+
+int lfsr_batch_set_tuning(lfsr_batch* b, const int* op_tile, int n_groups, int nla_chunk) {
+  if (!b) return bfail(nullptr, LFSR_EINVAL, "batch is NULL");
+  if (nla_chunk != 6 && nla_chunk != 3) return bfail(b, LFSR_EINVAL, "nla_chunk must be 6 or 3");
+  if (!op_tile || n_groups != (int)b->groups.size())
+    return bfail(b, LFSR_EINVAL, "op_tile must hold one tile side per operator group");
+  for (int gi = 0; gi < n_groups; ++gi)
+    if (op_tile[gi] != 64 && op_tile[gi] != 32)
+      return bfail(b, LFSR_EINVAL, "operator tile sides are 64 or 32");
+  for (int gi = 0; gi < n_groups; ++gi)
+    if (set_tile(b, b->groups[gi], op_tile[gi]) != cudaSuccess)
+      return bfail(b, LFSR_EUNSUPPORTED, "tile side does not fit the shared memory");
+  b->nla_chunk = nla_chunk;
+  const cudaError_t e = build_tables(b);
+  if (e != cudaSuccess)
+    return bfail(b, LFSR_ECUDA, std::string("set tuning: ") + cudaGetErrorString(e));
   return LFSR_OK;
 }
 

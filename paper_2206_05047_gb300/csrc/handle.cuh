@@ -14,6 +14,7 @@ namespace lfsr {
 struct ProfEvent {
   int cls;
   cudaEvent_t a, b;
+  int grp;   // operator group of a batch launch (0 otherwise)
 };
 
 // Launch kinds of one ADMM iteration, in schedule order (also the profiling

@@ -190,7 +190,9 @@ bool nlf_supported(const Geom& g);
 constexpr int NLF_TILE = 32;
 cudaError_t weights_to_canonical(const Geom& g, const void* wt, float* can, cudaStream_t s);
 cudaError_t nlw2_launch(int block, const Geom& g, const TableArgs& t, cudaStream_t s);
-cudaError_t nla2_launch(const Geom& g, const TableArgs& t, cudaStream_t s);
+// chunk: directions per batch of weight loads, 6 (default) or 3.
+constexpr int NLA_CHUNK = 6;
+cudaError_t nla2_launch(const Geom& g, const TableArgs& t, cudaStream_t s, int chunk = NLA_CHUNK);
 cudaError_t cg_init_nltv_launch(const Geom& g, const TableArgs& t, cudaStream_t s);
 
 // Specialised operator kernel for separable kernels of common (zeta, kb).
@@ -208,6 +210,9 @@ cudaError_t fast_launch(int mode, const Geom& g, const OpPlan& plan, const Table
 cudaError_t fast_launch_table(int mode, const Geom& g, const OpPlan& plan, const TableArgs& t,
                               int grid, cudaStream_t s);
 cudaError_t fast_prepare_table(int zeta, int kb, int smem_optin);
+// Plan of the table variant for tile side 64 or 32 (the batch autotuner's
+// candidates); plan.TH selects the variant at launch.
+cudaError_t fast_plan_table(const Geom& g, OpPlan* plan, int smem_limit, int tile);
 cudaError_t nl_launch(int mode, const Geom& g, const NlPlan& plan, const NlArgs& a,
                       cudaStream_t s);
 

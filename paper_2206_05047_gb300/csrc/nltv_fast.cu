@@ -10,7 +10,9 @@ namespace lfsr {
 
 // k_nla2: q(u) = mu sum_d w(u,u+d)^2 (p(u) - p(u+d)) + w(u-d,u)^2 (p(u) - p(u-d)),
 // with <p, q>'s NLTV part sum_d w(u,u+d)^2 (p(u) - p(u+d))^2 (each edge once).
-template <int WR, class ST>
+// DB: directions per chunk of weight loads (the stencil blocking the batch
+// autotuner chooses: 6 or 3).
+template <int WR, class ST, int DB>
 __global__ void __launch_bounds__(NF_THREADS)
 k_nla2(const Geom g, const TableArgs tb) {
   using D = HalfDirs<WR>;
@@ -58,7 +60,6 @@ k_nla2(const Geom g, const TableArgs tb) {
   for (int m = 0; m < NF_PIX; ++m) acc[m] = 0.f;
   // directions in chunks of DB: all weight loads of a chunk are issued
   // before any is used (memory-level parallelism)
-  constexpr int DB = 6;
 #pragma unroll
   for (int i0d = 0; i0d < D::SH; i0d += DB) {
     using B = SBits<ST>;
@@ -194,23 +195,30 @@ bool nlf_supported(const Geom& g) {
   return g.win_r >= 1 && g.win_r <= 3 && g.patch_r >= 0 && g.patch_r <= 2;
 }
 
-template <class ST>
+template <class ST, int DB>
 static cudaError_t nla2_st(const Geom& g, const TableArgs& t, cudaStream_t s) {
   switch (g.win_r) {
-    case 1: k_nla2<1, ST><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
-    case 2: k_nla2<2, ST><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
-    case 3: k_nla2<3, ST><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
+    case 1: k_nla2<1, ST, DB><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
+    case 2: k_nla2<2, ST, DB><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
+    case 3: k_nla2<3, ST, DB><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t nla2_launch(const Geom& g, const TableArgs& t, cudaStream_t s) {
+template <class ST>
+static cudaError_t nla2_db(const Geom& g, const TableArgs& t, cudaStream_t s, int chunk) {
+  if (chunk == 6) return nla2_st<ST, 6>(g, t, s);
+  if (chunk == 3) return nla2_st<ST, 3>(g, t, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t nla2_launch(const Geom& g, const TableArgs& t, cudaStream_t s, int chunk) {
   if (t.total_units < 1) return cudaErrorInvalidValue;
   switch (g.st) {
-    case ST_F32: return nla2_st<float>(g, t, s);
-    case ST_F16: return nla2_st<__half>(g, t, s);
-    case ST_BF16: return nla2_st<__nv_bfloat16>(g, t, s);
+    case ST_F32: return nla2_db<float>(g, t, s, chunk);
+    case ST_F16: return nla2_db<__half>(g, t, s, chunk);
+    case ST_BF16: return nla2_db<__nv_bfloat16>(g, t, s, chunk);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -6,32 +6,6 @@
 namespace lfsr {
 
 template <int Z, int KB>
-static size_t fast_layout(const Geom& g, OpPlan* P) {
-  using SH = FastShape<Z, KB>;
-  const int S = g.S;
-  auto al = [](size_t n) { return (n + 3) & ~(size_t)3; };
-  P->TH = P->TW = SH::T;
-  P->NLr = P->NLc = SH::NL;
-  P->NEr = P->NEc = SH::NE;
-  P->NPr = SH::NE + 2 * S + 1;
-  P->NPc = (SH::NE + 2 * S + 2) | 1;         // +1: the last tap column; odd pitch
-  P->NAr = SH::T + 2 * S + 2;
-  P->NAc = (SH::T + 2 * S + 2) | 1;
-  size_t off = 0;
-  P->off_P = (int)off; off += al((size_t)(P->NPr + 1) * P->NPc);
-  P->off_W = (int)off; off += al((size_t)(1 + SH::VB) * SH::WS);
-  P->off_H = (int)off; off += al((size_t)SH::VB * (SH::HS + SH::VS));
-  P->off_G = (int)off; off += al((size_t)SH::VB * SH::GS);
-  P->off_A = (int)off; off += al((size_t)P->NAr * P->NAc);
-  P->smem_bytes = off * sizeof(float);
-  P->tiles_x = (g.Wh + SH::T - 1) / SH::T;
-  P->tiles_y = (g.Hh + SH::T - 1) / SH::T;
-  P->n_tiles = P->tiles_x * P->tiles_y;
-  P->threads = FT_THREADS;
-  return P->smem_bytes;
-}
-
-template <int Z, int KB>
 static cudaError_t fast_prepare_zk(int optin) {
   cudaError_t e = set_max_dynamic_smem(k_operator_fast<OP_NORMAL, Z, KB, true>, optin);
   if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator_fast<OP_DATA, Z, KB, true>, optin);

@@ -45,9 +45,9 @@ constexpr int pick_block(int rows, int n) {
   return best;
 }
 
-template <int Z, int KB>
+template <int Z, int KB, int TILE = FAST_TILE>
 struct FastShape {
-  static constexpr int T = 64;                               // tile side (HR px)
+  static constexpr int T = TILE;                             // tile side (HR px)
   static constexpr int VB = FT_VB;
   static constexpr int R = (KB - 1) / 2;                     // blur radius
   static constexpr int NL = (T + 2 * R + Z - 1) / Z;         // LR rows/cols touching a tile
@@ -113,10 +113,10 @@ __device__ __forceinline__ void split_shift(float t, int& ip, float& fr) {
 // SINGLE: one light field whose fields come by value (kernel parameters,
 // read from the constant bank); else a table of light fields, the fields of
 // the current one in registers.
-template <int MODE, int Z, int KB, bool SINGLE>
+template <int MODE, int Z, int KB, bool SINGLE, int TILE = FAST_TILE>
 __global__ void __launch_bounds__(FT_THREADS, 1)
 k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs one) {
-  using SH = FastShape<Z, KB>;
+  using SH = FastShape<Z, KB, TILE>;
   constexpr int T = SH::T, R = SH::R, NL = SH::NL, NE = SH::NE, MG = SH::MG, NGp = SH::NGp;
   constexpr int NEp = SH::NEp, NHp = SH::NHp, NVp = SH::NVp, VB = SH::VB;
   extern __shared__ __align__(16) float smem[];
@@ -617,6 +617,34 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
 #undef JQLR
 #undef JHU
 #undef JHV
+}
+
+// Shared-memory layout and tiling of the specialised kernel for tile side
+// TILE (host side; S from g).
+template <int Z, int KB, int TILE = FAST_TILE>
+inline size_t fast_layout(const Geom& g, OpPlan* P) {
+  using SH = FastShape<Z, KB, TILE>;
+  const int S = g.S;
+  auto al = [](size_t n) { return (n + 3) & ~(size_t)3; };
+  P->TH = P->TW = SH::T;
+  P->NLr = P->NLc = SH::NL;
+  P->NEr = P->NEc = SH::NE;
+  P->NPr = SH::NE + 2 * S + 1;
+  P->NPc = (SH::NE + 2 * S + 2) | 1;         // +1: the last tap column; odd pitch
+  P->NAr = SH::T + 2 * S + 2;
+  P->NAc = (SH::T + 2 * S + 2) | 1;
+  size_t off = 0;
+  P->off_P = (int)off; off += al((size_t)(P->NPr + 1) * P->NPc);
+  P->off_W = (int)off; off += al((size_t)(1 + SH::VB) * SH::WS);
+  P->off_H = (int)off; off += al((size_t)SH::VB * (SH::HS + SH::VS));
+  P->off_G = (int)off; off += al((size_t)SH::VB * SH::GS);
+  P->off_A = (int)off; off += al((size_t)P->NAr * P->NAc);
+  P->smem_bytes = off * sizeof(float);
+  P->tiles_x = (g.Wh + SH::T - 1) / SH::T;
+  P->tiles_y = (g.Hh + SH::T - 1) / SH::T;
+  P->n_tiles = P->tiles_x * P->tiles_y;
+  P->threads = FT_THREADS;
+  return P->smem_bytes;
 }
 
 // (Z, KB) pairs with a specialised kernel.

@@ -43,7 +43,8 @@ EXPORTS = ("lfsr_create", "lfsr_solve", "lfsr_destroy", "lfsr_last_error", "lfsr
            "lfsr_batch_destroy", "lfsr_batch_last_error", "lfsr_batch_size", "lfsr_batch_load",
            "lfsr_batch_iterate", "lfsr_batch_get_x", "lfsr_batch_stats",
            "lfsr_batch_launches_per_iteration", "lfsr_batch_set_profiling",
-           "lfsr_batch_kernel_times")
+           "lfsr_batch_kernel_times", "lfsr_batch_autotune", "lfsr_batch_tuning",
+           "lfsr_batch_set_tuning")
 
 
 class lfsr_params(C.Structure):
@@ -110,6 +111,9 @@ def load_library(path: str = _LIB_PATH):
         "lfsr_batch_stats": (C.c_int, [H, C.c_int, C.POINTER(lfsr_stats_t)]),
         "lfsr_batch_launches_per_iteration": (C.c_int, [H]),
         "lfsr_batch_set_profiling": (C.c_int, [H, C.c_int]),
+        "lfsr_batch_autotune": (C.c_int, [H]),
+        "lfsr_batch_set_tuning": (C.c_int, [H, C.POINTER(C.c_int), C.c_int, C.c_int]),
+        "lfsr_batch_tuning": (C.c_int, [H, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
         "lfsr_batch_kernel_times": (C.c_int, [H, C.POINTER(C.c_double),
                                               C.POINTER(C.c_int64)]),
     }
@@ -396,6 +400,23 @@ class Batch:
 
     def launches_per_iteration(self) -> int:
         return load_library().lfsr_batch_launches_per_iteration(self.handle)
+
+    def autotune(self) -> dict:
+        """lfsr_batch_autotune (iterates the loaded state: load again
+        afterwards); returns the choices."""
+        _bcheck(load_library().lfsr_batch_autotune(self.handle), self.handle)
+        return self.tuning()
+
+    def tuning(self) -> dict:
+        tiles = (C.c_int * 64)()
+        chunk = C.c_int(0)
+        g = load_library().lfsr_batch_tuning(self.handle, tiles, 64, C.byref(chunk))
+        return {"operator_tile": list(tiles[:g]), "nltv_apply_chunk": chunk.value}
+
+    def set_tuning(self, operator_tile, nltv_apply_chunk):
+        tiles = (C.c_int * len(operator_tile))(*operator_tile)
+        _bcheck(load_library().lfsr_batch_set_tuning(self.handle, tiles, len(operator_tile),
+                                                     int(nltv_apply_chunk)), self.handle)
 
     def set_profiling(self, on: bool):
         _bcheck(load_library().lfsr_batch_set_profiling(self.handle, int(bool(on))), self.handle)

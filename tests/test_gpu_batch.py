@@ -127,3 +127,38 @@ def test_batch_rejects_unsupported_light_fields():
         lfsr.Batch([kws[1], bad])
     assert e.value.code == lfsr.LFSR_EUNSUPPORTED
     assert "light field 1" in lfsr.batch_last_error(None)
+
+
+@pytest.mark.parametrize("tiles,chunk", [((32, 32), 3), ((64, 32), 6), ((32, 64), 6)])
+def test_batch_tunings_give_the_same_results(tiles, chunk):
+    """Every tile side / stencil blocking the autotuner may choose computes
+    the same iteration (up to the order of float atomic additions)."""
+    probs, kws = _jobs()
+    b = lfsr.Batch(kws)
+    b.set_tuning(tiles, chunk)
+    assert b.tuning() == {"operator_tile": list(tiles), "nltv_apply_chunk": chunk}
+    for j, pr in enumerate(probs):
+        b.load(j, _t(pr.y), _t(pr.x0))
+    b.iterate(5)
+    for j in range(len(probs)):
+        assert rel_err(_batch_x(b, j, probs[j].wl.HR), _alone(kws[j], probs[j], 5)) <= 1e-5, j
+    b.close()
+
+
+def test_batch_autotune_then_reload():
+    probs, kws = _jobs()
+    b = lfsr.Batch(kws)
+    for j, pr in enumerate(probs):
+        b.load(j, _t(pr.y), _t(pr.x0))
+    choice = b.autotune()
+    assert all(t in (32, 64) for t in choice["operator_tile"]) and len(choice["operator_tile"]) == 2
+    assert choice["nltv_apply_chunk"] in (3, 6)
+    for j, pr in enumerate(probs):
+        b.load(j, _t(pr.y), _t(pr.x0))
+    b.iterate(4)
+    for j in range(len(probs)):
+        assert rel_err(_batch_x(b, j, probs[j].wl.HR), _alone(kws[j], probs[j], 4)) <= 1e-5, j
+    with pytest.raises(lfsr.LfsrError):
+        b.set_tuning((64,), 6)                     # one tile side per group
+    b.close()
+
