@@ -291,6 +291,83 @@ int lfsr_batch_set_tuning(lfsr_batch *b, const int *op_tile, int n_groups, int n
 int lfsr_batch_set_profiling(lfsr_batch *b, int on);
 int lfsr_batch_kernel_times(lfsr_batch *b, double *ms, int64_t *launches);
 
+/* Upper bound of the device bytes lfsr_create allocates for params (the
+ * state of one light field; the float staging buffer for host transfers,
+ * allocated on first use, excluded).  -1 for invalid params.  No device
+ * call. */
+int64_t lfsr_estimate_state_bytes(const lfsr_params *params);
+
+/* ---- continuous-batching server ---------------------------------------
+ *
+ * Requests (one light field each, any geometry the batches accept) arrive at
+ * any time and are admitted in arrival order as soon as an active slot is
+ * free and the sum of the active light fields' state bytes
+ * (lfsr_estimate_state_bytes) stays within the budget; a request that does
+ * not fit waits, and none behind it overtakes it.  An admitted request's
+ * state is created and loaded at once and stays on the device; all active
+ * light fields step through the ADMM iteration together (one launch per
+ * phase for all of them, as a batch), so requests that arrive while others
+ * run share the GPU with them.  A request leaves exactly at its
+ * `iterations`-th iteration: its result is copied to host memory and its
+ * device state freed.  Every result equals the request's own lfsr_solve up
+ * to the order of float atomic additions.  Requests must share the solver
+ * constants (as in a batch).  Single-threaded use. */
+#define LFSR_SERVER_DRY_RUN 1   /* flags: schedule without a device (checks) */
+
+#define LFSR_REQ_QUEUED  0
+#define LFSR_REQ_ACTIVE  1
+#define LFSR_REQ_DONE    2
+#define LFSR_REQ_FETCHED 3
+#define LFSR_REQ_FAILED  4
+
+typedef struct lfsr_server lfsr_server;
+
+typedef struct lfsr_server_config {
+  uint32_t struct_size;        /* sizeof(lfsr_server_config)                 */
+  int64_t hbm_budget_bytes;    /* device bytes for the active light fields    */
+  int32_t max_active;          /* active slots, 1 .. LFSR_BATCH_MAX          */
+  int32_t iterations;          /* ADMM iterations per request (N)            */
+  int32_t iterations_per_step; /* iterations between scheduling points (>= 1) */
+  int32_t flags;               /* LFSR_SERVER_DRY_RUN or 0                   */
+} lfsr_server_config;
+
+typedef struct lfsr_server_stats_t {
+  uint32_t struct_size;        /* set to sizeof(lfsr_server_stats_t)         */
+  int32_t queued, active, done, failed;
+  int64_t bytes_in_use, bytes_peak;
+  int64_t iterations;          /* batch iterations run                       */
+  int64_t batch_rebuilds;      /* launch-structure rebuilds (active set changed) */
+  int64_t admitted, retired;
+} lfsr_server_stats_t;
+
+/* Creates a server; work is ordered on cuda_stream.  No device call. */
+int lfsr_server_create(const lfsr_server_config *cfg, void *cuda_stream, lfsr_server **out);
+void lfsr_server_destroy(lfsr_server *s);
+const char *lfsr_server_last_error(const lfsr_server *s);
+
+/* Queues a request: params as for lfsr_create (host blur and disparity),
+ * views (s_k*q floats) and x0 (p floats) in host memory; all are copied.
+ * *id receives the request's id (0, 1, 2, ... in submission order). */
+int lfsr_server_submit(lfsr_server *s, const lfsr_params *params, const float *lr_views,
+                       const float *x0, int64_t *id);
+
+/* One scheduling round: admit what fits, then run the active light fields
+ * up to iterations_per_step iterations (fewer when one of them is due
+ * sooner), then retire the ones that reached their N.  Blocks until the
+ * iterations are done.  Returns the number of active requests afterwards
+ * (>= 0) or a negative LFSR_E* code. */
+int lfsr_server_step(lfsr_server *s);
+
+/* *state (LFSR_REQ_*) and *iterations of request id.  Returns LFSR_OK, the
+ * request's error code if it failed, or LFSR_EINVAL for an unknown id. */
+int lfsr_server_status(const lfsr_server *s, int64_t id, int *state, int *iterations);
+
+/* Copies a done request's x (p floats) to x_out and drops the server's
+ * copy. */
+int lfsr_server_fetch(lfsr_server *s, int64_t id, float *x_out, int mem_kind);
+
+int lfsr_server_stats(const lfsr_server *s, lfsr_server_stats_t *out);
+
 /* ---- no-allocation variant ------------------------------------------
  *
  * Some callers cannot allocate device memory: code that runs inside a host

@@ -39,6 +39,8 @@ struct Group {
 
 struct lfsr_batch {
   std::vector<lfsr_handle*> jobs;
+  bool owns_jobs = true;      // false: the light fields belong to a server
+  std::vector<std::pair<Geom, int>> tuned_tiles;   // operator tile chosen per (scale, blur)
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   int sm_count = 0;
@@ -55,7 +57,7 @@ struct lfsr_batch {
   int* maps = nullptr;
   double* partials = nullptr;
   size_t part_stride = 0;
-  size_t cap_tables = 0, cap_maps = 0, cap_partials = 0;   // allocated entries
+  size_t cap_tables = 0, cap_maps = 0, cap_partials = 0, cap_counters = 0;  // allocated entries
   unsigned int* counters = nullptr;
   // table offsets (entries): all light fields for the NLTV / vector launches,
   // the members of each group for the operator launches
@@ -102,7 +104,8 @@ void batch_free(lfsr_batch* b) {
   if (b->partials) cudaFree(b->partials);
   if (b->counters) cudaFree(b->counters);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  for (lfsr_handle* h : b->jobs) lfsr_destroy(h);
+  if (b->owns_jobs)
+    for (lfsr_handle* h : b->jobs) lfsr_destroy(h);
   b->jobs.clear();
 }
 
@@ -346,6 +349,103 @@ cudaError_t time_iteration(lfsr_batch* b, int cls, int grp, double* ms) {
 
 }  // namespace
 
+// (Re)builds the launch structure of the batch over `jobs` (all of them on
+// the specialised path, sharing the solver constants): operator groups and
+// their plans, unit offsets, vector chunking, job tables and maps.  The
+// graphs are dropped.  An empty list leaves an empty batch.
+cudaError_t lfsr::batch_assign(lfsr_batch* b, const std::vector<lfsr_handle*>& jobs) {
+  // remember the tuned tile side of every group before regrouping
+  for (const Group& gr : b->groups) {
+    bool found = false;
+    for (auto& tt : b->tuned_tiles)
+      if (same_operator(tt.first, gr.g)) {
+        tt.second = gr.tile;
+        found = true;
+      }
+    if (!found) b->tuned_tiles.emplace_back(gr.g, gr.tile);
+  }
+  if (&jobs != &b->jobs) b->jobs = jobs;
+  b->groups.clear();
+  b->nl_unit0.clear();
+  b->vec_unit0.clear();
+  b->vec_units.clear();
+  b->nl_total = b->vec_total = 0;
+  const int n = (int)b->jobs.size();
+  if (n == 0) return cudaSuccess;
+  b->g = b->jobs[0]->g;
+  b->sm_count = b->jobs[0]->sm_count;
+  b->cg_iters = b->jobs[0]->prm.cg_iters;
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                         b->jobs[0]->device);
+  b->smem_limit = optin - 1024;
+  // operator groups: shared scale and blur; the layout takes the group's
+  // largest shift bound
+  for (int j = 0; j < n && e == cudaSuccess; ++j) {
+    const Geom& gj = b->jobs[j]->g;
+    int gi = 0;
+    while (gi < (int)b->groups.size() && !same_operator(b->groups[gi].g, gj)) ++gi;
+    if (gi == (int)b->groups.size()) {
+      b->groups.emplace_back();
+      b->groups.back().g = gj;
+    }
+    Group& gr = b->groups[gi];
+    if (gj.S > gr.g.S) gr.g.S = gj.S;
+    gr.members.push_back(j);
+  }
+  for (Group& gr : b->groups) {
+    if (e != cudaSuccess) break;
+    int tile = FAST_TILE;
+    for (const auto& tt : b->tuned_tiles)
+      if (same_operator(tt.first, gr.g)) tile = tt.second;
+    if (set_tile(b, gr, tile) != cudaSuccess && set_tile(b, gr, FAST_TILE) != cudaSuccess)
+      return cudaErrorInvalidValue;
+  }
+  // vector kernels: one chunk size for the batch, about two CTAs per SM in
+  // all (plus at most one partial chunk per light field)
+  size_t total_p = 0;
+  for (lfsr_handle* h : b->jobs) total_p += h->p;
+  {
+    size_t chunk = (total_p + 2 * (size_t)b->sm_count - 1) / (2 * (size_t)b->sm_count);
+    chunk = (chunk + 31) / 32 * 32;
+    if (chunk < 1024) chunk = 1024;
+    b->vec_chunk = (int)chunk;
+  }
+  for (lfsr_handle* h : b->jobs) {
+    b->nl_unit0.push_back(b->nl_total);
+    b->nl_total += h->nl_units;
+    const int vu = (int)((h->p + b->vec_chunk - 1) / b->vec_chunk);
+    b->vec_unit0.push_back(b->vec_total);
+    b->vec_units.push_back(vu);
+    b->vec_total += vu;
+  }
+  const size_t n_counters = (size_t)KD_NUM * (b->groups.size() + 1);
+  if (e == cudaSuccess && !b->cap_stream)
+    e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && n_counters > b->cap_counters) {
+    if (b->counters) cudaFree(b->counters);
+    b->counters = nullptr;
+    b->cap_counters = 0;
+    e = cudaMalloc((void**)&b->counters, n_counters * sizeof(unsigned int));
+    if (e == cudaSuccess) {
+      b->cap_counters = n_counters;
+      e = cudaMemsetAsync(b->counters, 0, n_counters * sizeof(unsigned int), b->stream);
+    }
+  }
+  if (e == cudaSuccess) e = build_tables(b);
+  return e;
+}
+
+lfsr_batch* lfsr::batch_new_shared(cudaStream_t stream) {
+  lfsr_batch* b = new (std::nothrow) lfsr_batch();
+  if (!b) return nullptr;
+  b->owns_jobs = false;
+  b->stream = stream;
+  return b;
+}
+
+int lfsr::batch_parity(const lfsr_batch* b) { return b->parity; }
+
 extern "C" {
 
 int lfsr_batch_create(const lfsr_params* params, int n, void* cuda_stream, lfsr_batch** out) {
@@ -382,64 +482,17 @@ int lfsr_batch_create(const lfsr_params* params, int n, void* cuda_stream, lfsr_
                        "NLTV window of 3, 5 or 7 with a patch of 1, 3 or 5");
     }
   }
-  b->g = b->jobs[0]->g;
-  b->sm_count = b->jobs[0]->sm_count;
-  int optin = 0;
-  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
-                                         b->jobs[0]->device);
-  b->smem_limit = optin - 1024;
-  // operator groups: shared scale and blur; the layout takes the group's
-  // largest shift bound
-  for (int j = 0; j < n && e == cudaSuccess; ++j) {
-    const Geom& gj = b->jobs[j]->g;
-    int gi = 0;
-    while (gi < (int)b->groups.size() && !same_operator(b->groups[gi].g, gj)) ++gi;
-    if (gi == (int)b->groups.size()) {
-      b->groups.emplace_back();
-      b->groups.back().g = gj;
-    }
-    Group& gr = b->groups[gi];
-    if (gj.S > gr.g.S) gr.g.S = gj.S;
-    gr.members.push_back(j);
-  }
-  for (Group& gr : b->groups) {
-    if (e != cudaSuccess) break;
-    if (set_tile(b, gr, FAST_TILE) != cudaSuccess) {
-      batch_free(b);
-      delete b;
-      return bfail(nullptr, LFSR_EUNSUPPORTED,
-                   "disparity * angular offset too large for the shared-memory tile");
-    }
-  }
-  // vector kernels: one chunk size for the batch, about two CTAs per SM in
-  // all (plus at most one partial chunk per light field)
-  size_t total_p = 0;
-  for (lfsr_handle* h : b->jobs) total_p += h->p;
-  {
-    size_t chunk = (total_p + 2 * (size_t)b->sm_count - 1) / (2 * (size_t)b->sm_count);
-    chunk = (chunk + 31) / 32 * 32;
-    if (chunk < 1024) chunk = 1024;
-    b->vec_chunk = (int)chunk;
-  }
-  for (lfsr_handle* h : b->jobs) {
-    b->nl_unit0.push_back(b->nl_total);
-    b->nl_total += h->nl_units;
-    const int vu = (int)((h->p + b->vec_chunk - 1) / b->vec_chunk);
-    b->vec_unit0.push_back(b->vec_total);
-    b->vec_units.push_back(vu);
-    b->vec_total += vu;
-  }
-  const size_t n_counters = (size_t)KD_NUM * (b->groups.size() + 1);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->counters, n_counters * sizeof(unsigned int));
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(b->counters, 0, n_counters * sizeof(unsigned int), b->stream);
-  if (e == cudaSuccess) e = build_tables(b);
+  const cudaError_t e = batch_assign(b, b->jobs);
   if (e != cudaSuccess) {
     const std::string msg = std::string("lfsr_batch_create: ") + cudaGetErrorString(e);
+    const int code = e == cudaErrorMemoryAllocation ? LFSR_ENOMEM
+                     : e == cudaErrorInvalidValue  ? LFSR_EUNSUPPORTED : LFSR_ECUDA;
     batch_free(b);
     delete b;
-    return bfail(nullptr, e == cudaErrorMemoryAllocation ? LFSR_ENOMEM : LFSR_ECUDA, msg);
+    return bfail(nullptr, code, e == cudaErrorInvalidValue
+                                    ? std::string("disparity * angular offset too large for the "
+                                                  "shared-memory tile")
+                                    : msg);
   }
   *out = b;
   return LFSR_OK;

@@ -93,6 +93,14 @@ cudaError_t from_dev(lfsr_handle* h, float* dst, const float* src, size_t n, int
                          h->stream);
 }
 
+// The float staging buffer for host transfers and layout conversions is
+// allocated on first use, so light fields that only move device memory
+// (batches, servers) never hold it.
+cudaError_t ensure_io(lfsr_handle* h) {
+  if (h->io) return cudaSuccess;
+  return dalloc(h, &h->io, h->io_floats);
+}
+
 int check_mem(lfsr_handle* h, int mem) {
   if (mem != LFSR_MEM_HOST && mem != LFSR_MEM_DEVICE)
     return fail(h, LFSR_EINVAL, "mem_kind must be LFSR_MEM_HOST or LFSR_MEM_DEVICE");
@@ -346,6 +354,29 @@ int lfsr::handle_cuda_fail(lfsr_handle* h, cudaError_t e, const char* what) {
   return cuda_fail(h, e, what);
 }
 
+int64_t lfsr::estimate_state_bytes(const lfsr_params* pr) {
+  const int64_t Hh = (int64_t)pr->scale * pr->H, Wh = (int64_t)pr->scale * pr->W;
+  const int64_t p = Hh * Wh, q = (int64_t)pr->H * pr->W, sk = (int64_t)pr->U * pr->V;
+  const int64_t sh = ((int64_t)pr->nltv_window * pr->nltv_window - 1) / 2;
+  const int64_t nA = sk * q, nS = 2 * sh * p;
+  const int base = pr->precision & ~LFSR_KEEP_VIEWS_FP32;
+  const int64_t es = base == LFSR_FP32 ? 4 : 2;
+  const int64_t ey = (base == LFSR_FP32 || (pr->precision & LFSR_KEEP_VIEWS_FP32)) ? 4 : 2;
+  const bool nlf = pr->nltv_window >= 3 && pr->nltv_window <= 7 && pr->nltv_patch <= 5;
+  int64_t b = 4 * p              // disparity
+              + ey * nA          // views
+              + 2 * 4 * p        // x ping-pong
+              + 2 * es * nA      // data duals
+              + 2 * es * nS      // regulariser duals
+              + 4 * 4 * p;       // P ping-pong, R, Q
+  if (nlf) b += es * sh * p + 4 * sh * p;   // stored weights, divergence terms
+  const int64_t nl_tiles = ((Hh + 31) / 32) * ((Wh + 31) / 32);
+  b += (int64_t)RED_NUM * 8 * (nl_tiles > 4096 ? nl_tiles : 4096);   // reduction slots (bound)
+  b += 2 * (int64_t)sizeof(DevScalars) + (4 * KD_NUM + 4) * (int64_t)sizeof(JobArgs) +
+       (KD_NUM + 4) * 4;
+  return b;
+}
+
 int lfsr::kind_slot(int kind) {
   switch (kind) {
     case KD_NLW: return RED_DW_S;
@@ -570,7 +601,6 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   }
   if (e == cudaSuccess) e = dalloc(h, &h->R, p);
   if (e == cudaSuccess) e = dalloc(h, &h->Q, p);
-  if (e == cudaSuccess) e = dalloc(h, &h->io, h->io_floats);
   h->nlf = nlf_supported(g);
   if (e == cudaSuccess && h->nlf) e = dalloc_st(h, &h->wt, (size_t)g.sh * p, h->esize);
   if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->cb, (size_t)g.sh * p);
@@ -630,6 +660,7 @@ int lfsr::load_state(lfsr_handle* h, const float* lr_views, const float* x0, int
   } else {
     const float* src = lr_views;
     if (mem == LFSR_MEM_HOST) {
+      CK(h, ensure_io(h), "staging buffer");
       CK(h, to_dev(h, h->io, lr_views, h->nA, mem), "upload views");
       src = h->io;
     }
@@ -735,6 +766,11 @@ int lfsr_stats(const lfsr_handle* hc, lfsr_stats_t* out) {
   return LFSR_OK;
 }
 
+int64_t lfsr_estimate_state_bytes(const lfsr_params* params) {
+  if (validate(params) != LFSR_OK) return -1;
+  return estimate_state_bytes(params);
+}
+
 int lfsr_set_profiling(lfsr_handle* h, int on) {
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
   h->profiling = on != 0;
@@ -748,6 +784,7 @@ int lfsr_set_profiling(lfsr_handle* h, int on) {
 int lfsr_set_state(lfsr_handle* h, const float* x, const float* wA, const float* wS, int mem) {
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
   if (check_mem(h, mem)) return LFSR_EINVAL;
+  CK(h, ensure_io(h), "staging buffer");
   const int b = h->parity;
   if (x) CK(h, to_dev(h, h->x[b], x, h->p, mem), "set x");
   if (wA && h->g.st == ST_F32) CK(h, to_dev(h, (float*)h->wA[b], wA, h->nA, mem), "set data duals");
@@ -769,6 +806,7 @@ int lfsr_set_state(lfsr_handle* h, const float* x, const float* wA, const float*
 int lfsr_get_state(lfsr_handle* h, float* x, float* wA, float* wS, int mem) {
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
   if (check_mem(h, mem)) return LFSR_EINVAL;
+  CK(h, ensure_io(h), "staging buffer");
   const int b = h->parity;
   if (x) CK(h, from_dev(h, x, h->x[b], h->p, mem), "get x");
   if (wA && h->g.st == ST_F32) CK(h, from_dev(h, wA, (const float*)h->wA[b], h->nA, mem), "get data duals");
@@ -788,6 +826,7 @@ int lfsr_apply_A(lfsr_handle* h, int view, const float* x, float* out, int mem) 
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
   if (!x || !out) return fail(h, LFSR_EINVAL, "x and out are required");
   if (check_mem(h, mem)) return LFSR_EINVAL;
+  CK(h, ensure_io(h), "staging buffer");
   if (view < -1 || view >= h->g.sk) return fail(h, LFSR_EINVAL, "view out of range");
   const int nv = view < 0 ? h->g.sk : 1;
   const float* xs = x;
@@ -830,6 +869,7 @@ int lfsr_apply_AT(lfsr_handle* h, int view, const float* gin, float* out, int me
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
   if (!gin || !out) return fail(h, LFSR_EINVAL, "g and out are required");
   if (check_mem(h, mem)) return LFSR_EINVAL;
+  CK(h, ensure_io(h), "staging buffer");
   if (view < -1 || view >= h->g.sk) return fail(h, LFSR_EINVAL, "view out of range");
   const int nv = view < 0 ? h->g.sk : 1;
   const float* gs = gin;
@@ -875,6 +915,7 @@ int lfsr_weights(lfsr_handle* h, const float* x, float* w, int mem) {
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
   if (!x || !w) return fail(h, LFSR_EINVAL, "x and w are required");
   if (check_mem(h, mem)) return LFSR_EINVAL;
+  CK(h, ensure_io(h), "staging buffer");
   const float* xs = x;
   float* ws = w;
   if (mem == LFSR_MEM_HOST) {
@@ -910,6 +951,7 @@ int lfsr_apply_normal(lfsr_handle* h, const float* xw, const float* p, float* qo
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
   if (!xw || !p || !qo) return fail(h, LFSR_EINVAL, "xw, p and q are required");
   if (check_mem(h, mem)) return LFSR_EINVAL;
+  CK(h, ensure_io(h), "staging buffer");
   const float* xs = xw;
   const float* ps = p;
   float* qs = qo;

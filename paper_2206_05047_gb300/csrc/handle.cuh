@@ -89,6 +89,14 @@ int kind_units(const lfsr_handle* h, int kind);
 int kind_slot(int kind);
 // lfsr_load into state `parity` (x[parity] := x0, duals[parity] := 0).
 int load_state(lfsr_handle* h, const float* lr_views, const float* x0, int mem, int parity);
+// Upper bound of the device bytes lfsr_create allocates for params (the
+// staging buffer excluded: it is allocated on first host transfer).
+int64_t estimate_state_bytes(const lfsr_params* params);
+// Batches: an empty batch over light fields owned by someone else; its
+// launch structure rebuilt over `jobs` (see batch.cu); its state parity.
+lfsr_batch* batch_new_shared(cudaStream_t stream);
+cudaError_t batch_assign(lfsr_batch* b, const std::vector<lfsr_handle*>& jobs);
+int batch_parity(const lfsr_batch* b);
 // Records an error on h (and the thread) and returns code.
 int handle_fail(lfsr_handle* h, int code, const std::string& msg);
 int handle_cuda_fail(lfsr_handle* h, cudaError_t e, const char* what);

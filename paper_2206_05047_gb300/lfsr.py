@@ -28,6 +28,8 @@ LFSR_FP16_STORAGE = 1
 LFSR_BF16_STORAGE = 2
 LFSR_KEEP_VIEWS_FP32 = 256
 LFSR_FP16_MAX_INV_MU = 8192.0
+LFSR_SERVER_DRY_RUN = 1
+LFSR_REQ_QUEUED, LFSR_REQ_ACTIVE, LFSR_REQ_DONE, LFSR_REQ_FETCHED, LFSR_REQ_FAILED = 0, 1, 2, 3, 4
 # precision names accepted by Solver(precision=...) and the benchmark
 PRECISIONS = {"fp32": LFSR_FP32, "fp16": LFSR_FP16_STORAGE, "bf16": LFSR_BF16_STORAGE,
               "fp16-views32": LFSR_FP16_STORAGE | LFSR_KEEP_VIEWS_FP32,
@@ -44,7 +46,9 @@ EXPORTS = ("lfsr_create", "lfsr_solve", "lfsr_destroy", "lfsr_last_error", "lfsr
            "lfsr_batch_iterate", "lfsr_batch_get_x", "lfsr_batch_stats",
            "lfsr_batch_launches_per_iteration", "lfsr_batch_set_profiling",
            "lfsr_batch_kernel_times", "lfsr_batch_autotune", "lfsr_batch_tuning",
-           "lfsr_batch_set_tuning")
+           "lfsr_batch_set_tuning", "lfsr_estimate_state_bytes", "lfsr_server_create",
+           "lfsr_server_destroy", "lfsr_server_last_error", "lfsr_server_submit",
+           "lfsr_server_step", "lfsr_server_status", "lfsr_server_fetch", "lfsr_server_stats")
 
 
 class lfsr_params(C.Structure):
@@ -61,6 +65,19 @@ class lfsr_stats_t(C.Structure):
                 ("status", C.c_int32), ("dual_change_sq", C.c_double), ("cg_pi", C.c_double),
                 ("state_bytes", C.c_int64), ("launches", C.c_int64),
                 ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_int64 * 8)]
+
+
+class lfsr_server_config(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("hbm_budget_bytes", C.c_int64),
+                ("max_active", C.c_int32), ("iterations", C.c_int32),
+                ("iterations_per_step", C.c_int32), ("flags", C.c_int32)]
+
+
+class lfsr_server_stats_t(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("queued", C.c_int32), ("active", C.c_int32),
+                ("done", C.c_int32), ("failed", C.c_int32), ("bytes_in_use", C.c_int64),
+                ("bytes_peak", C.c_int64), ("iterations", C.c_int64),
+                ("batch_rebuilds", C.c_int64), ("admitted", C.c_int64), ("retired", C.c_int64)]
 
 
 class LfsrError(RuntimeError):
@@ -112,6 +129,18 @@ def load_library(path: str = _LIB_PATH):
         "lfsr_batch_launches_per_iteration": (C.c_int, [H]),
         "lfsr_batch_set_profiling": (C.c_int, [H, C.c_int]),
         "lfsr_batch_autotune": (C.c_int, [H]),
+        "lfsr_estimate_state_bytes": (C.c_int64, [C.POINTER(lfsr_params)]),
+        "lfsr_server_create": (C.c_int, [C.POINTER(lfsr_server_config), C.c_void_p,
+                                         C.POINTER(C.c_void_p)]),
+        "lfsr_server_destroy": (None, [H]),
+        "lfsr_server_last_error": (C.c_char_p, [H]),
+        "lfsr_server_submit": (C.c_int, [H, C.POINTER(lfsr_params), fp, fp,
+                                         C.POINTER(C.c_int64)]),
+        "lfsr_server_step": (C.c_int, [H]),
+        "lfsr_server_status": (C.c_int, [H, C.c_int64, C.POINTER(C.c_int),
+                                         C.POINTER(C.c_int)]),
+        "lfsr_server_fetch": (C.c_int, [H, C.c_int64, fp, C.c_int]),
+        "lfsr_server_stats": (C.c_int, [H, C.POINTER(lfsr_server_stats_t)]),
         "lfsr_batch_set_tuning": (C.c_int, [H, C.POINTER(C.c_int), C.c_int, C.c_int]),
         "lfsr_batch_tuning": (C.c_int, [H, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
         "lfsr_batch_kernel_times": (C.c_int, [H, C.POINTER(C.c_double),
@@ -444,4 +473,83 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---- size estimate and the continuous-batching server ----------------------
+def estimate_state_bytes(**kw) -> int:
+    """lfsr_estimate_state_bytes for create()'s keyword arguments."""
+    prm, keep = _params(**kw)
+    n = load_library().lfsr_estimate_state_bytes(C.byref(prm))
+    del keep
+    if n < 0:
+        raise LfsrError(LFSR_EINVAL, last_error(None))
+    return int(n)
+
+
+def server_last_error(server) -> str:
+    return load_library().lfsr_server_last_error(server).decode()
+
+
+class Server:
+    """lfsr_server: requests admitted as slots and the budget allow, all
+    active light fields stepped together, each retired at its N-th
+    iteration."""
+
+    def __init__(self, hbm_budget_bytes, max_active=64, iterations=100, iterations_per_step=4,
+                 dry_run=False, stream=None):
+        cfg = lfsr_server_config(C.sizeof(lfsr_server_config), int(hbm_budget_bytes),
+                                 int(max_active), int(iterations), int(iterations_per_step),
+                                 LFSR_SERVER_DRY_RUN if dry_run else 0)
+        h = C.c_void_p()
+        rc = load_library().lfsr_server_create(C.byref(cfg), C.c_void_p(_stream(stream)),
+                                               C.byref(h))
+        if rc != LFSR_OK:
+            raise LfsrError(rc, server_last_error(None))
+        self.handle = h
+
+    def _check(self, rc):
+        if rc < 0:
+            raise LfsrError(rc, server_last_error(self.handle))
+        return rc
+
+    def submit(self, lr_views, x0, **kw) -> int:
+        """Queues one request (host numpy arrays); kw as for create()."""
+        prm, keep = _params(**kw)
+        y = np.ascontiguousarray(lr_views, dtype=np.float32)
+        x = np.ascontiguousarray(x0, dtype=np.float32)
+        rid = C.c_int64(-1)
+        self._check(load_library().lfsr_server_submit(
+            self.handle, C.byref(prm), y.ctypes.data_as(C.c_void_p), x.ctypes.data_as(C.c_void_p),
+            C.byref(rid)))
+        del keep
+        return rid.value
+
+    def step(self) -> int:
+        return self._check(load_library().lfsr_server_step(self.handle))
+
+    def status(self, rid):
+        st, it = C.c_int(0), C.c_int(0)
+        rc = load_library().lfsr_server_status(self.handle, int(rid), C.byref(st), C.byref(it))
+        return st.value, it.value, rc
+
+    def fetch(self, rid, x_out):
+        po, ko = _ptr(x_out)
+        self._check(load_library().lfsr_server_fetch(self.handle, int(rid), po, ko))
+
+    def stats(self) -> dict:
+        st = lfsr_server_stats_t()
+        st.struct_size = C.sizeof(lfsr_server_stats_t)
+        self._check(load_library().lfsr_server_stats(self.handle, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in lfsr_server_stats_t._fields_ if k != "struct_size"}
+
+    def close(self):
+        if self.handle is not None:
+            load_library().lfsr_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 

@@ -1,0 +1,57 @@
+"""The continuous-batching server on the GPU: requests admitted while others
+run (at either state parity) give the same result as each solved alone, and
+the device memory returns to zero."""
+import numpy as np
+import pytest
+
+from paper_2206_05047_gb300 import lfsr, synth
+from tests.gpu_util import f32, rel_err
+from tests.test_gpu_batch import GEOMS, SOLVER, _alone
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests():
+    out = []
+    for i, gm in enumerate(GEOMS + GEOMS[:2]):
+        wl = synth.custom(window=5, patch=3, **gm)
+        pr = synth.make_problem(wl, seed=40 + i)
+        kw = dict(U=wl.U, V=wl.V, H=wl.H, W=wl.W, scale=wl.scale, blur=f32(pr.blur),
+                  disparity=f32(pr.disparity), **SOLVER)
+        out.append((pr, kw))
+    return out
+
+
+def test_results_are_the_same_alone_and_in_the_mix():
+    reqs = _requests()
+    n_iter = 9
+    srv = lfsr.Server(8 << 30, max_active=3, iterations=n_iter, iterations_per_step=2)
+    ids = [srv.submit(f32(pr.y), f32(pr.x0), **kw) for pr, kw in reqs[:2]]
+    srv.step()                                   # 2 iterations
+    srv.step()
+    ids += [srv.submit(f32(pr.y), f32(pr.x0), **kw) for pr, kw in reqs[2:5]]
+    srv.step()                                   # one joins (3 slots), 1 more iteration: odd parity
+    ids += [srv.submit(f32(pr.y), f32(pr.x0), **kw) for pr, kw in reqs[5:]]
+    for _ in range(200):
+        if srv.stats()["done"] == len(reqs):
+            break
+        srv.step()
+    st = srv.stats()
+    assert st["done"] == len(reqs) and st["failed"] == 0 and st["active"] == 0
+    assert st["bytes_in_use"] == 0 and st["batch_rebuilds"] >= 3
+    for rid, (pr, kw) in zip(ids, reqs):
+        state, iters, rc = srv.status(rid)
+        assert state == lfsr.LFSR_REQ_DONE and iters == n_iter and rc == 0
+        x = np.zeros(pr.wl.HR, np.float32)
+        srv.fetch(rid, x)
+        assert rel_err(x, _alone(kw, pr, n_iter)) <= 1e-5, rid
+    srv.close()
+
+
+def test_estimate_bounds_the_allocation():
+    for pr, kw in _requests()[:3]:
+        est = lfsr.estimate_state_bytes(**kw)
+        s = lfsr.Solver(**kw)
+        got = lfsr.stats(s.handle)["state_bytes"]
+        assert got <= est <= got + (1 << 20), (got, est)
+        s.close()
