@@ -40,6 +40,7 @@ from paper_2206_05047_gb300 import synth  # noqa: E402
 
 METRIC = "HR LF Mpix*ADMM-iter/s"
 BATCH_WORKLOAD = "batch_uneven"
+SERVE_WORKLOAD = "serve_poisson"
 UNIT = "Mpix*iter/s"
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
@@ -52,8 +53,14 @@ def args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lf9x9_256_x2",
-                    choices=sorted(synth.WORKLOADS) + [BATCH_WORKLOAD])
+                    choices=sorted(synth.WORKLOADS) + [BATCH_WORKLOAD, SERVE_WORKLOAD])
     ap.add_argument("--batch", type=int, default=64, help="light fields of the batch workload")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="arrival window of the serving workload (Poisson, 20 requests/s)")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-no-plain", action="store_true",
+                    help="skip the serial plain-path comparison of the serving workload")
     ap.add_argument("--iterations", type=int, default=None, help="ADMM iterations per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -447,8 +454,156 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# serving: Poisson arrivals, continuous batching under a memory budget,
+# against the same arrivals served one at a time by the plain path
+# --------------------------------------------------------------------------
+def run_serve(a):
+    import torch
+    from paper_2206_05047_gb300 import lfsr
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit("the serving workload runs on one GPU")
+    seed = 5000
+    t_gen = time.perf_counter()
+    wls, probs = batch_problems(64, seed)          # the pool requests are drawn from
+    t_gen = time.perf_counter() - t_gen
+    n_iter = a.iterations if a.iterations is not None else wls[0].iterations
+    rng = np.random.default_rng(seed)
+    arrivals, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / a.serve_rate)
+        if t > a.serve_seconds:
+            break
+        arrivals.append(t)
+    picks = rng.integers(0, len(wls), len(arrivals))
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    kws = [dict(U=w.U, V=w.V, H=w.H, W=w.W, scale=w.scale, blur=p[2], disparity=p[3],
+                lambda1=w.lambda1, lambda2=w.lambda2, mu=w.mu, nltv_window=w.window,
+                nltv_patch=w.patch, nltv_h=w.h, cg_iters=w.cg_iters, cg_tol=0.0,
+                precision=a.precision) for w, p in zip(wls, probs)]
+    work = [wls[k].s_k * wls[k].HR[0] * wls[k].HR[1] * n_iter for k in picks]
+    budget = 120 * 10**9
+
+    def pctl(v, q):
+        return float(np.percentile(np.asarray(v), q))
+
+    # warm-up: one small request through the server (kernels, allocator)
+    small = min(range(len(wls)), key=lambda k: wls[k].H * wls[k].W * wls[k].s_k)
+    warm = lfsr.Server(budget, max_active=a.serve_slots, iterations=2, iterations_per_step=2,
+                       stream=stream)
+    warm.submit(probs[small][0], probs[small][1], **kws[small])
+    while warm.stats()["done"] < 1:
+        warm.step()
+    warm.close()
+
+    srv = lfsr.Server(budget, max_active=a.serve_slots, iterations=n_iter, iterations_per_step=4,
+                      stream=stream)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ids, done_t, pending = {}, {}, set()
+    nxt = 0
+    t0 = time.perf_counter()
+    while len(done_t) < len(arrivals):
+        now = time.perf_counter() - t0
+        while nxt < len(arrivals) and arrivals[nxt] <= now:
+            k = picks[nxt]
+            ids[nxt] = srv.submit(probs[k][0], probs[k][1], **kws[k])
+            pending.add(nxt)
+            nxt += 1
+        active = srv.step()
+        tnow = time.perf_counter() - t0
+        for r in list(pending):
+            state, _, rc = srv.status(ids[r])
+            if state == lfsr.LFSR_REQ_DONE:
+                done_t[r] = tnow
+                pending.discard(r)
+            elif state == lfsr.LFSR_REQ_FAILED:
+                raise SystemExit(f"request {r} failed: {rc}")
+        if active == 0 and not pending and nxt < len(arrivals):
+            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+    t_end = max(done_t.values())
+    clk = clocks.stop()
+    st = srv.stats()
+    lat = [done_t[r] - arrivals[r] for r in range(len(arrivals))]
+    xs = {}
+    for r in range(len(arrivals)):
+        x = np.zeros(wls[picks[r]].HR, np.float32)
+        srv.fetch(ids[r], x)
+        xs[r] = x
+    srv.close()
+    value = sum(work) / (t_end - arrivals[0]) / 1e6
+
+    # the same arrivals, first come first served, one plain solve at a time
+    if a.serve_no_plain:
+        picks_plain = []
+    else:
+        picks_plain = picks
+    solvers = {}
+    for k in sorted(set(np.asarray(picks_plain).tolist())):
+        solvers[k] = lfsr.Solver(stream=stream, **kws[k])
+    out = {k: np.zeros(wls[k].HR, np.float32) for k in solvers}
+    for k in solvers:                                  # warm-up
+        lfsr.solve(solvers[k].handle, probs[k][0], 2, probs[k][1], out[k])
+    done_p, dpsnr = {}, []
+    t0 = time.perf_counter()
+    for r in range(len(picks_plain)):
+        now = time.perf_counter() - t0
+        if arrivals[r] > now:
+            time.sleep(arrivals[r] - now)
+        k = picks[r]
+        lfsr.solve(solvers[k].handle, probs[k][0], n_iter, probs[k][1], out[k])
+        done_p[r] = time.perf_counter() - t0
+        gt = probs[k][4]
+        dpsnr.append(synth.psnr(xs[r], gt) - synth.psnr(out[k], gt))
+    for sv in solvers.values():
+        sv.close()
+    if done_p:
+        t_end_p = max(done_p.values())
+        lat_p = [done_p[r] - arrivals[r] for r in range(len(arrivals))]
+        value_p = sum(work) / (t_end_p - arrivals[0]) / 1e6
+    else:
+        lat_p, value_p, dpsnr = [float("nan")], float("nan"), [float("nan")]
+    h2d = int(sum(probs[k][0].nbytes + probs[k][1].nbytes for k in picks))
+    d2h = int(sum(xs[r].nbytes for r in xs))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * (t_end - arrivals[0]), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded textured-plane light fields)",
+            "config": {"workload": SERVE_WORKLOAD, "arrivals_per_s": a.serve_rate,
+                       "arrival_window_s": a.serve_seconds, "requests": len(arrivals),
+                       "pool": f"64 light fields of the batched distribution (seed {seed})",
+                       "iterations": n_iter, "hbm_budget_gb": budget / 1e9,
+                       "slots": a.serve_slots, "iterations_per_step": 4,
+                       "peak_state_gb": st["bytes_peak"] / 1e9,
+                       "batch_rebuilds": st["batch_rebuilds"], "storage": a.precision,
+                       "generation_s": round(t_gen, 1),
+                       "timing": "wall clock from the first arrival to the last result on "
+                                 "the host; requests and results in host memory"},
+            "latency_s": {"p50": pctl(lat, 50), "p99": pctl(lat, 99), "mean": float(np.mean(lat)),
+                          "max": float(np.max(lat))},
+            "plain_serial": {"value": value_p, "unit": UNIT,
+                             "latency_s": {"p50": pctl(lat_p, 50), "p99": pctl(lat_p, 99),
+                                           "mean": float(np.mean(lat_p))}},
+            "served_vs_plain": value / value_p,
+            "equal_psnr": {"max_abs_db": float(np.max(np.abs(dpsnr))),
+                           "mean_db": float(np.mean(dpsnr))},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": None, "cpu_baseline": None,
+            "gpu_launches": int(st["launches"]), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = args()
+    if a.workload == SERVE_WORKLOAD:
+        if a.impl == "reference":
+            run_reference(a, synth.batch_workloads(1, 5000)[0], 1)
+        else:
+            run_serve(a)
+        return
     if a.workload == BATCH_WORKLOAD:
         if a.impl == "reference":
             run_reference(a, synth.batch_workloads(1)[0], 1)

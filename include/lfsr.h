@@ -338,6 +338,7 @@ typedef struct lfsr_server_stats_t {
   int64_t iterations;          /* batch iterations run                       */
   int64_t batch_rebuilds;      /* launch-structure rebuilds (active set changed) */
   int64_t admitted, retired;
+  int64_t launches;            /* kernel launches of the batch iterations    */
 } lfsr_server_stats_t;
 
 /* Creates a server; work is ordered on cuda_stream.  No device call. */

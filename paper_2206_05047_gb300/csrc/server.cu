@@ -50,7 +50,7 @@ struct lfsr_server {
   bool changed = false;                       // active set differs from the batch's
   int64_t next_id = 0;
   int64_t bytes_in_use = 0, bytes_peak = 0;
-  int64_t iterations = 0, rebuilds = 0, admitted = 0, retired = 0, dry_parity = 0;
+  int64_t iterations = 0, rebuilds = 0, admitted = 0, retired = 0, dry_parity = 0, launches = 0;
   std::string err = "no error";
 };
 
@@ -222,6 +222,7 @@ int lfsr_server_step(lfsr_server* s) {
     if (!dry(s)) {
       int rc = lfsr_batch_iterate(s->batch, k);
       if (rc != LFSR_OK) return sfail(s, rc, lfsr_batch_last_error(s->batch));
+      s->launches += (int64_t)k * lfsr_batch_launches_per_iteration(s->batch);
       const cudaError_t e = cudaStreamSynchronize(s->stream);
       if (e != cudaSuccess) return sfail(s, LFSR_ECUDA, cudaGetErrorString(e));
     } else {
@@ -302,6 +303,7 @@ int lfsr_server_stats(const lfsr_server* s, lfsr_server_stats_t* out) {
   out->batch_rebuilds = s->rebuilds;
   out->admitted = s->admitted;
   out->retired = s->retired;
+  out->launches = s->launches;
   return LFSR_OK;
 }
 

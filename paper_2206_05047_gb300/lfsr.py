@@ -77,7 +77,8 @@ class lfsr_server_stats_t(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("queued", C.c_int32), ("active", C.c_int32),
                 ("done", C.c_int32), ("failed", C.c_int32), ("bytes_in_use", C.c_int64),
                 ("bytes_peak", C.c_int64), ("iterations", C.c_int64),
-                ("batch_rebuilds", C.c_int64), ("admitted", C.c_int64), ("retired", C.c_int64)]
+                ("batch_rebuilds", C.c_int64), ("admitted", C.c_int64), ("retired", C.c_int64),
+                ("launches", C.c_int64)]
 
 
 class LfsrError(RuntimeError):

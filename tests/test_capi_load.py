@@ -13,7 +13,7 @@ def _declared():
     for f in os.listdir(os.path.join(ROOT, "include")):
         if f.endswith(".h"):
             src = open(os.path.join(ROOT, "include", f)).read()
-            names |= set(re.findall(r"^\s*(?:int|void|const char \*)\s*(lfsr_\w+)\s*\(", src, re.M))
+            names |= set(re.findall(r"^\s*(?:int64_t|int|void|const char \*)\s*(lfsr_\w+)\s*\(", src, re.M))
     return names
 
 
