@@ -31,6 +31,9 @@
  *  - Regulariser duals in the canonical layout are s_d x Hh x Wh, the dual
  *    of direction d at pixel u at [d][u] (Eq. sr_admm_compact row order);
  *    data duals are s_k x H x W.
+ *  - s_k is the number of views used: U*V, or n_views when params->views
+ *    lists a subset; the views' data (LR views, data duals, apply_A's view
+ *    argument) are indexed 0 .. s_k-1 in the order of that list.
  *
  * Memory kinds: LFSR_MEM_HOST pointers are ordinary host memory (pinned or
  * pageable; the call copies through the handle's stream); LFSR_MEM_DEVICE
@@ -115,6 +118,11 @@ typedef struct lfsr_params {
   double cg_tol;           /* tau: CG stops once pi = |r|^2 <= tau          */
   int32_t precision;       /* LFSR_FP32, LFSR_FP16_STORAGE or
                               LFSR_BF16_STORAGE [| LFSR_KEEP_VIEWS_FP32]      */
+  const int32_t *views;    /* host, optional: the grid indices k = v*U + u of
+                              the views used, strictly ascending (Sec. 6.1's
+                              x4 experiment uses a star of 17 of 5 x 5);
+                              NULL: all U*V.  Copied.                        */
+  int32_t n_views;         /* entries of views (ignored when views is NULL)  */
 } lfsr_params;
 
 typedef struct lfsr_handle lfsr_handle;

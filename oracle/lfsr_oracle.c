@@ -86,7 +86,14 @@ void orc_dirs(const orc_problem *P, int *di, int *dj) {
 }
 
 /* Angular offset of view k = v*U + u relative to the centre view. */
-void orc_view_theta(const orc_problem *P, int k, double *tu, double *tv) {
+int orc_num_views(const orc_problem *P) {
+  return (P->views && P->n_views > 0) ? P->n_views : P->U * P->V;
+}
+
+/* Angular offset of data view j: grid index k = views[j] (Sec. 6.1 uses a
+ * subset of the grid, e.g. a star of 17 of 5 x 5 views). */
+void orc_view_theta(const orc_problem *P, int j, double *tu, double *tv) {
+  const int k = (P->views && P->n_views > 0) ? P->views[j] : j;
   int u = k % P->U, v = k / P->U;
   *tu = u - 0.5 * (P->U - 1);
   *tv = v - 0.5 * (P->V - 1);
@@ -323,7 +330,7 @@ void orc_prox(long n, const double *u, double t, double *z) {
  * serial inside, nested parallelism is off), per-view buffers are summed in
  * view order. */
 static void sum_AT(const orc_problem *P, const double *g, double *out) {
-  const int sk = P->U * P->V;
+  const int sk = orc_num_views(P);
   const long p = (long)HR_H(P) * HR_W(P), q = (long)P->H * P->W;
   double *buf = dalloc(p * sk);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -339,7 +346,7 @@ static void sum_AT(const orc_problem *P, const double *g, double *out) {
 
 /* out[k] = A_k x for every view. */
 static void all_A(const orc_problem *P, const double *x, double *out) {
-  const int sk = P->U * P->V;
+  const int sk = orc_num_views(P);
   const long q = (long)P->H * P->W;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int k = 0; k < sk; ++k) orc_A(P, k, x, out + k * q);
@@ -348,7 +355,7 @@ static void all_A(const orc_problem *P, const double *x, double *out) {
 /* M p with M = (lambda2 + mu lambda1^2/2) sum_k A_k^T A_k + mu/2 S^T S,
  * the normal matrix G^T G of the x-step least squares (Sec. 4.2). */
 void orc_normal_apply(const orc_problem *P, const double *w, const double *p, double *q) {
-  const int sk = P->U * P->V, sd = orc_num_dirs(P);
+  const int sk = orc_num_views(P), sd = orc_num_dirs(P);
   const long np = (long)HR_H(P) * HR_W(P), nq = (long)P->H * P->W;
   const double cA = P->lambda2 + 0.5 * P->mu * P->lambda1 * P->lambda1;
   double *Ap = dalloc(nq * sk), *AtAp = dalloc(np), *Sp = dalloc(np * sd), *StSp = dalloc(np);
@@ -365,7 +372,7 @@ void orc_normal_apply(const orc_problem *P, const double *w, const double *p, do
 
 /* J(x) of Eq. sr_fin with the given weights. */
 double orc_cost(const orc_problem *P, const double *y, const double *w, const double *x) {
-  const int sk = P->U * P->V, sd = orc_num_dirs(P);
+  const int sk = orc_num_views(P), sd = orc_num_dirs(P);
   const long np = (long)HR_H(P) * HR_W(P), nq = (long)P->H * P->W;
   double *Ax = dalloc(nq * sk), *Sx = dalloc(np * sd);
   all_A(P, x, Ax);
@@ -430,7 +437,7 @@ int orc_cg(const orc_problem *P, const double *w, const double *v, double *x,
  * final CG pi, CG steps. */
 int orc_admm(const orc_problem *P, const double *y, const double *x0, int N,
              double *x, double *wA, double *wS, double *diag) {
-  const int sk = P->U * P->V, sd = orc_num_dirs(P);
+  const int sk = orc_num_views(P), sd = orc_num_dirs(P);
   const long np = (long)HR_H(P) * HR_W(P), nq = (long)P->H * P->W;
   const long nA = nq * sk, nS = np * sd;
   const double t = 1.0 / P->mu;

@@ -32,6 +32,8 @@ typedef struct orc_problem {
   int cg_iters;           /* K of Algorithm 2                               */
   double cg_tol;          /* tau of Algorithm 2 (stop when pi <= tau)       */
   int freeze_weights;     /* test option: weights from x0, then fixed       */
+  int n_views;            /* views used (0: all U*V)                        */
+  const int *views;       /* their grid indices k = v*U + u, ascending      */
 } orc_problem;
 
 int    orc_num_threads(void);
@@ -40,7 +42,10 @@ void   orc_set_threads(int n);
 /* geometry */
 int    orc_num_dirs(const orc_problem *P);
 void   orc_dirs(const orc_problem *P, int *di, int *dj);
-void   orc_view_theta(const orc_problem *P, int k, double *tu, double *tv);
+/* Views: the data of view j (0 <= j < orc_num_views) is y_j; its grid index
+ * is views[j] (or j for the full grid). */
+int    orc_num_views(const orc_problem *P);
+void   orc_view_theta(const orc_problem *P, int j, double *tu, double *tv);
 
 /* degradation operators (Eq. sr_model_op, Sec. 4.1) and their adjoints */
 void   orc_warp  (const orc_problem *P, int k, const double *x, double *out);

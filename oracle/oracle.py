@@ -40,7 +40,8 @@ class _Problem(C.Structure):
                 ("lambda1", C.c_double), ("lambda2", C.c_double), ("mu", C.c_double),
                 ("window", C.c_int), ("patch", C.c_int), ("h", C.c_double),
                 ("cg_iters", C.c_int), ("cg_tol", C.c_double),
-                ("freeze_weights", C.c_int)]
+                ("freeze_weights", C.c_int), ("n_views", C.c_int),
+                ("views", C.POINTER(C.c_int))]
 
 
 _lib = None
@@ -98,7 +99,7 @@ class Oracle:
 
     def __init__(self, U, V, H, W, zeta, blur, disparity, lambda1=1.0, lambda2=4.0,
                  mu=1.0, window=5, patch=3, h=0.1, cg_iters=5, cg_tol=0.0,
-                 freeze_weights=False):
+                 freeze_weights=False, views=None):
         self._lib = _load()
         self.blur = _f64(blur)
         kb = self.blur.shape[0]
@@ -106,7 +107,14 @@ class Oracle:
         self.disp = _f64(disparity)
         assert self.disp.shape == (zeta * H, zeta * W)
         self.U, self.V, self.H, self.W, self.zeta = U, V, H, W, zeta
-        self.s_k = U * V
+        # views: grid indices k = v*U + u of the views used (Sec. 6.1 uses a
+        # star of 17 of 5 x 5), ascending; None: the full grid
+        self.views = None if views is None else np.ascontiguousarray(views, dtype=np.int32)
+        if self.views is not None:
+            assert self.views.ndim == 1 and len(self.views) >= 1
+            assert (np.diff(self.views) > 0).all() and self.views[0] >= 0
+            assert self.views[-1] < U * V
+        self.s_k = U * V if self.views is None else len(self.views)
         self.hr = (zeta * H, zeta * W)
         self.p = zeta * H * zeta * W
         self.q = H * W
@@ -114,7 +122,10 @@ class Oracle:
                            self.blur.ctypes.data_as(C.POINTER(C.c_double)),
                            self.disp.ctypes.data_as(C.POINTER(C.c_double)),
                            lambda1, lambda2, mu, window, patch, h, cg_iters, cg_tol,
-                           int(bool(freeze_weights)))
+                           int(bool(freeze_weights)),
+                           0 if self.views is None else len(self.views),
+                           None if self.views is None
+                           else self.views.ctypes.data_as(C.POINTER(C.c_int)))
         self.s_d = self._lib.orc_num_dirs(C.byref(self._P))
 
     @classmethod

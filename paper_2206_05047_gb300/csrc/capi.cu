@@ -61,6 +61,7 @@ void free_all(lfsr_handle* h) {
   if (h->partials) cudaFree(h->partials);
   if (h->sc) cudaFree(h->sc);
   if (h->jobs_dev) cudaFree(h->jobs_dev);
+  if (h->theta) cudaFree(h->theta);
   if (h->jobs_scratch) cudaFree(h->jobs_scratch);
   if (h->counters) cudaFree(h->counters);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -298,6 +299,13 @@ int validate(const lfsr_params* pr) {
     return fail(nullptr, LFSR_EINVAL, "nltv_patch must be odd in [1, 7]");
   if (!(pr->nltv_h > 0.0) || !std::isfinite(pr->nltv_h)) return fail(nullptr, LFSR_EINVAL, "nltv_h must be > 0");
   if (pr->cg_iters < 0 || pr->cg_iters > 10000) return fail(nullptr, LFSR_EINVAL, "cg_iters must be in [0, 10000]");
+  if (pr->views) {
+    if (pr->n_views < 1 || pr->n_views > pr->U * pr->V)
+      return fail(nullptr, LFSR_EINVAL, "n_views must be in [1, U*V]");
+    for (int j = 0; j < pr->n_views; ++j)
+      if (pr->views[j] < 0 || pr->views[j] >= pr->U * pr->V || (j && pr->views[j] <= pr->views[j - 1]))
+        return fail(nullptr, LFSR_EINVAL, "views must be strictly ascending grid indices in [0, U*V)");
+  }
   if (!(pr->cg_tol >= 0.0) || !std::isfinite(pr->cg_tol)) return fail(nullptr, LFSR_EINVAL, "cg_tol must be >= 0");
   const int base = pr->precision & ~LFSR_KEEP_VIEWS_FP32;
   if (base != LFSR_FP32 && base != LFSR_FP16_STORAGE && base != LFSR_BF16_STORAGE)
@@ -341,6 +349,7 @@ JobArgs standalone_job(const lfsr_handle* h) {
   j.U = h->g.U;
   j.V = h->g.V;
   j.disp = h->disp;
+  j.theta = h->theta;
   j.sc = h->sc + 1;
   return j;
 }
@@ -356,7 +365,8 @@ int lfsr::handle_cuda_fail(lfsr_handle* h, cudaError_t e, const char* what) {
 
 int64_t lfsr::estimate_state_bytes(const lfsr_params* pr) {
   const int64_t Hh = (int64_t)pr->scale * pr->H, Wh = (int64_t)pr->scale * pr->W;
-  const int64_t p = Hh * Wh, q = (int64_t)pr->H * pr->W, sk = (int64_t)pr->U * pr->V;
+  const int64_t p = Hh * Wh, q = (int64_t)pr->H * pr->W;
+  const int64_t sk = pr->views ? (int64_t)pr->n_views : (int64_t)pr->U * pr->V;
   const int64_t sh = ((int64_t)pr->nltv_window * pr->nltv_window - 1) / 2;
   const int64_t nA = sk * q, nS = 2 * sh * p;
   const int base = pr->precision & ~LFSR_KEEP_VIEWS_FP32;
@@ -373,7 +383,7 @@ int64_t lfsr::estimate_state_bytes(const lfsr_params* pr) {
   const int64_t nl_tiles = ((Hh + 31) / 32) * ((Wh + 31) / 32);
   b += (int64_t)RED_NUM * 8 * (nl_tiles > 4096 ? nl_tiles : 4096);   // reduction slots (bound)
   b += 2 * (int64_t)sizeof(DevScalars) + (4 * KD_NUM + 4) * (int64_t)sizeof(JobArgs) +
-       (KD_NUM + 4) * 4;
+       (KD_NUM + 4) * 4 + 8 * sk;
   return b;
 }
 
@@ -410,6 +420,7 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
   j.unit0 = unit0;
   j.units = kind_units(h, kind);
   j.disp = h->disp;
+  j.theta = h->theta;
   j.sc = h->sc;
   switch (kind) {
     case KD_NLW:   // weights from x^(n-1), regulariser z/w-step, v := 0
@@ -485,11 +496,13 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   h->prm = *pr;
   h->prm.blur = nullptr;
   h->prm.disparity = nullptr;
+  h->prm.views = nullptr;
+  if (pr->views) h->views.assign(pr->views, pr->views + pr->n_views);
   h->stream = (cudaStream_t)cuda_stream;
   Geom& g = h->g;
   g.U = pr->U;
   g.V = pr->V;
-  g.sk = pr->U * pr->V;
+  g.sk = pr->views ? pr->n_views : pr->U * pr->V;
   g.H = pr->H;
   g.W = pr->W;
   g.Hh = Hh;
@@ -503,9 +516,11 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   for (size_t i = 0; i < p; ++i) max_disp = std::fmax(max_disp, std::fabs((double)pr->disparity[i]));
   const double max_theta = 0.5 * (double)((pr->U > pr->V ? pr->U : pr->V) - 1);
   g.S = (int)std::ceil(max_disp * max_theta);
-  for (int k = 0; k < g.sk; ++k) {
-    g.tu[k] = (float)((k % pr->U) - 0.5 * (pr->U - 1));
-    g.tv[k] = (float)((k / pr->U) - 0.5 * (pr->V - 1));
+  // angular offsets of the views of the data (the grid, or the listed subset)
+  for (int j = 0; j < g.sk; ++j) {
+    const int k = pr->views ? pr->views[j] : j;
+    g.tu[j] = (float)((k % pr->U) - 0.5 * (pr->U - 1));
+    g.tv[j] = (float)((k / pr->U) - 0.5 * (pr->V - 1));
   }
   g.win_r = (pr->nltv_window - 1) / 2;
   g.patch_r = (pr->nltv_patch - 1) / 2;
@@ -606,6 +621,12 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->cb, (size_t)g.sh * p);
   if (e == cudaSuccess) e = dalloc(h, &h->partials, (size_t)RED_NUM * h->max_grid);
   if (e == cudaSuccess) e = dalloc(h, &h->sc, 2);
+  if (e == cudaSuccess) e = dalloc(h, &h->theta, (size_t)g.sk);
+  if (e == cudaSuccess) {
+    std::vector<float2> th(g.sk);
+    for (int j = 0; j < g.sk; ++j) th[j] = make_float2(g.tu[j], g.tv[j]);
+    e = cudaMemcpy(h->theta, th.data(), th.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = dalloc(h, &h->jobs_dev, (size_t)4 * KD_NUM);
   if (e == cudaSuccess) e = dalloc(h, &h->jobs_scratch, 4);
   if (e == cudaSuccess) e = dalloc(h, &h->counters, (size_t)KD_NUM + 4);

@@ -36,6 +36,8 @@ struct lfsr_handle {
   int grid_op = 0, grid_vec = 0, max_grid = 0;
   // device buffers
   float* disp = nullptr;
+  float2* theta = nullptr;             // angular offsets of the data's views
+  std::vector<int32_t> views;          // the listed subset (empty: the grid)
   float* x[2] = {nullptr, nullptr};
   float* R = nullptr;   // v, then the CG residual r
   float* P[2] = {nullptr, nullptr};

@@ -123,6 +123,7 @@ struct JobArgs {
   float scale;                // operator: factor of the flushed accumulator
   int use_beta;               // NLTV apply: p_new = r + beta p_old (else p_old is the direction)
   const float* disp;          // HR disparity
+  const float2* theta;        // angular offset (tu, tv) of each view of the data
   const float* src;           // operator: x or p (HR), g (LR, adjoint); NLTV: weights source x;
                               // vector init: x
   float* out;                 // operator: HR accumulator or LR output; NLTV block: v;

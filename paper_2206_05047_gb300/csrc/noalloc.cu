@@ -33,6 +33,7 @@ constexpr int kMaxOpCtas = 1024;
 struct NoallocScratch {
   DevScalars sc;
   unsigned int counter;            // the specialised operator kernel's arrival counter
+  float2 theta[LFSR_MAX_VIEWS];    // angular offsets of the views
   double nl_partials[kMaxCtas];    // NLTV part, one per 32 x 32 tile
   double op_partials[kMaxOpCtas];  // operator part, one per CTA
 };
@@ -117,7 +118,12 @@ extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_d
   Geom g{};
   g.U = pr->U;
   g.V = pr->V;
-  g.sk = pr->U * pr->V;
+  if (pr->views && (pr->n_views < 1 || pr->n_views > pr->U * pr->V))
+    return nfail(LFSR_EINVAL, "n_views must be in [1, U*V]");
+  for (int j = 0; pr->views && j < pr->n_views; ++j)
+    if (pr->views[j] < 0 || pr->views[j] >= pr->U * pr->V || (j && pr->views[j] <= pr->views[j - 1]))
+      return nfail(LFSR_EINVAL, "views must be strictly ascending grid indices in [0, U*V)");
+  g.sk = pr->views ? pr->n_views : pr->U * pr->V;
   g.H = pr->H;
   g.W = pr->W;
   g.Hh = (int)Hh;
@@ -157,9 +163,10 @@ extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_d
   for (long long i = 0; i < Hh * Wh; ++i)
     max_disp = std::fmax(max_disp, std::fabs((double)pr->disparity[i]));
   g.S = (int)std::ceil(max_disp * 0.5 * (double)((pr->U > pr->V ? pr->U : pr->V) - 1));
-  for (int k = 0; k < g.sk; ++k) {
-    g.tu[k] = (float)((k % pr->U) - 0.5 * (pr->U - 1));
-    g.tv[k] = (float)((k / pr->U) - 0.5 * (pr->V - 1));
+  for (int j = 0; j < g.sk; ++j) {
+    const int k = pr->views ? pr->views[j] : j;
+    g.tu[j] = (float)((k % pr->U) - 0.5 * (pr->U - 1));
+    g.tv[j] = (float)((k / pr->U) - 0.5 * (pr->V - 1));
   }
   g.win_r = (pr->nltv_window - 1) / 2;
   g.patch_r = (pr->nltv_patch - 1) / 2;
@@ -201,6 +208,13 @@ extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_d
 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   NoallocScratch* scr = ds.scratch;
+  {
+    float2 th[LFSR_MAX_VIEWS];
+    for (int j = 0; j < g.sk; ++j) th[j] = make_float2(g.tu[j], g.tv[j]);
+    if (cudaMemcpyAsync(scr->theta, th, g.sk * sizeof(float2), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return nfail(LFSR_ECUDA, "writing the view offsets failed");
+  }
   // counters and totals start at zero on every call
   if (cudaMemsetAsync(&scr->sc, 0, sizeof(DevScalars), s) != cudaSuccess ||
       cudaMemsetAsync(&scr->counter, 0, sizeof(unsigned int), s) != cudaSuccess)
@@ -229,6 +243,7 @@ extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_d
     j.nviews = g.sk;
     j.scale = g.cA;
     j.disp = d_disparity;
+    j.theta = scr->theta;
     j.src = d_p;
     j.out = d_q;
     j.sc = &scr->sc;

@@ -151,7 +151,7 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
   __shared__ JobArgs s_job;
   // SINGLE: the fields and their derived values, computed once from the
   // kernel parameters
-  const int p_H = one.H, p_W = one.W, p_Hh = one.Hh, p_Wh = one.Wh, p_U = one.U;
+  const int p_H = one.H, p_W = one.W, p_Hh = one.Hh, p_Wh = one.Wh;
   const int p_tiles_x = one.tiles_x, p_view0 = one.view0, p_nviews = one.nviews;
   const int p_unit0 = one.unit0;
   const float p_scale = one.scale;
@@ -163,17 +163,17 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
   void* const p_wA_new = one.wA_new;
   const int p_nvb = (one.nviews + VB - 1) / VB;
   const size_t p_qlr = (size_t)one.H * one.W;
-  const float p_hu = 0.5f * (float)(one.U - 1), p_hv = 0.5f * (float)(one.V - 1);
+  const float2* const p_theta = one.theta;
 #define JF(f) (SINGLE ? p_##f : s_job.f)
 #define JNVB (SINGLE ? p_nvb : (s_job.nviews + VB - 1) / VB)
 #define JQLR (SINGLE ? p_qlr : (size_t)s_job.H * s_job.W)
-#define JHU (SINGLE ? p_hu : 0.5f * (float)(s_job.U - 1))
-#define JHV (SINGLE ? p_hv : 0.5f * (float)(s_job.V - 1))
+
   int jb = -1, j_end = 0;
   bool skip = false;
-  // angular offsets theta_k of view k = v U + u (Sec. 3.1)
-  auto tu_of = [&](int k) { return (float)(k % JF(U)) - JHU; };
-  auto tv_of = [&](int k) { return (float)(k / JF(U)) - JHV; };
+  // angular offset theta_k of data view k (Sec. 3.1), from the light
+  // field's table (the views may be a subset of the grid)
+  auto tu_of = [&](int k) { return __ldg(&JF(theta)[k].x); };
+  auto tv_of = [&](int k) { return __ldg(&JF(theta)[k].y); };
 
   static_assert(VB == 2, "the sample and scatter stages handle view pairs");
   int cur_tile = -1;
@@ -615,8 +615,7 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
 #undef JF
 #undef JNVB
 #undef JQLR
-#undef JHU
-#undef JHV
+
 }
 
 // Shared-memory layout and tiling of the specialised kernel for tile side

@@ -28,6 +28,7 @@ thread_local std::string t_server_err = "no error";
 struct Request {
   lfsr_params prm{};
   std::vector<float> blur, disp, views, x0;   // owned copies until admission
+  std::vector<int32_t> view_list;             // the listed subset of the grid, if any
   int64_t bytes = 0;                          // state bytes (estimate, budgeted)
   int state = LFSR_REQ_QUEUED;
   int iters = 0;                              // ADMM iterations done
@@ -102,6 +103,7 @@ int admit(lfsr_server* s) {
       lfsr_params p = r.prm;
       p.blur = r.blur.data();
       p.disparity = r.disp.data();
+      p.views = r.view_list.empty() ? nullptr : r.view_list.data();
       lfsr_handle* h = nullptr;
       int rc = lfsr_create(&p, s->stream, &h);
       if (rc == LFSR_OK && (!h->op.fast || !h->nlf)) rc = LFSR_EUNSUPPORTED;
@@ -186,13 +188,15 @@ int lfsr_server_submit(lfsr_server* s, const lfsr_params* params, const float* l
   Request r;
   r.prm = *params;
   const int64_t Hh = (int64_t)params->scale * params->H, Wh = (int64_t)params->scale * params->W;
-  const int64_t sk = (int64_t)params->U * params->V;
+  const int64_t sk = params->views ? (int64_t)params->n_views : (int64_t)params->U * params->V;
+  if (params->views) r.view_list.assign(params->views, params->views + params->n_views);
   r.blur.assign(params->blur, params->blur + (size_t)params->kb * params->kb);
   r.disp.assign(params->disparity, params->disparity + (size_t)(Hh * Wh));
   r.views.assign(lr_views, lr_views + (size_t)(sk * params->H * params->W));
   r.x0.assign(x0, x0 + (size_t)(Hh * Wh));
   r.prm.blur = nullptr;
   r.prm.disparity = nullptr;
+  r.prm.views = nullptr;
   r.bytes = est;
   *id = s->next_id++;
   s->reqs.emplace(*id, std::move(r));

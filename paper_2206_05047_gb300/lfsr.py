@@ -57,7 +57,8 @@ class lfsr_params(C.Structure):
                 ("blur", C.POINTER(C.c_float)), ("disparity", C.POINTER(C.c_float)),
                 ("lambda1", C.c_double), ("lambda2", C.c_double), ("mu", C.c_double),
                 ("nltv_window", C.c_int32), ("nltv_patch", C.c_int32), ("nltv_h", C.c_double),
-                ("cg_iters", C.c_int32), ("cg_tol", C.c_double), ("precision", C.c_int32)]
+                ("cg_iters", C.c_int32), ("cg_tol", C.c_double), ("precision", C.c_int32),
+                ("views", C.POINTER(C.c_int32)), ("n_views", C.c_int32)]
 
 
 class lfsr_stats_t(C.Structure):
@@ -193,20 +194,23 @@ def _check(rc: int, handle=None):
         raise LfsrError(rc, last_error(handle))
 
 
-def _params(U, V, H, W, scale, blur, disparity, lambda1=1.0, lambda2=4.0, mu=1.0,
+def _params(U, V, H, W, scale, blur, disparity, lambda1=2.0, lambda2=4.0, mu=300.0,
             nltv_window=5, nltv_patch=3, nltv_h=0.1, cg_iters=5, cg_tol=0.0,
-            precision=LFSR_FP32):
-    """(lfsr_params, arrays it points to: keep them alive while it is used)."""
+            precision=LFSR_FP32, views=None):
+    """(lfsr_params, arrays it points to: keep them alive while it is used).
+    views: optional grid indices k = v*U + u of the views used (ascending)."""
     blur = np.ascontiguousarray(blur, dtype=np.float32)
     disp = np.ascontiguousarray(disparity, dtype=np.float32)
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
+    vw = None if views is None else np.ascontiguousarray(views, dtype=np.int32)
     prm = lfsr_params(C.sizeof(lfsr_params), U, V, H, W, scale, blur.shape[0],
                       blur.ctypes.data_as(C.POINTER(C.c_float)),
                       disp.ctypes.data_as(C.POINTER(C.c_float)),
                       lambda1, lambda2, mu, nltv_window, nltv_patch, nltv_h, cg_iters, cg_tol,
-                      precision)
-    return prm, (blur, disp)
+                      precision, None if vw is None else vw.ctypes.data_as(C.POINTER(C.c_int32)),
+                      0 if vw is None else len(vw))
+    return prm, (blur, disp, vw)
 
 
 def _stream(stream):
@@ -219,15 +223,15 @@ def _stream(stream):
     return stream if isinstance(stream, int) else stream.cuda_stream
 
 
-def create(U, V, H, W, scale, blur, disparity, lambda1=1.0, lambda2=4.0, mu=1.0,
+def create(U, V, H, W, scale, blur, disparity, lambda1=2.0, lambda2=4.0, mu=300.0,
            nltv_window=5, nltv_patch=3, nltv_h=0.1, cg_iters=5, cg_tol=0.0,
-           precision=LFSR_FP32, stream=None):
+           precision=LFSR_FP32, stream=None, views=None):
     """lfsr_create; returns an opaque handle.  stream: torch.cuda.Stream,
     an integer cudaStream_t, or None (the current torch stream if torch has
     CUDA, else the legacy default stream)."""
     lib = load_library()
     prm, keep = _params(U, V, H, W, scale, blur, disparity, lambda1, lambda2, mu, nltv_window,
-                        nltv_patch, nltv_h, cg_iters, cg_tol, precision)
+                        nltv_patch, nltv_h, cg_iters, cg_tol, precision, views)
     h = C.c_void_p()
     _check(lib.lfsr_create(C.byref(prm), C.c_void_p(_stream(stream)), C.byref(h)))
     del keep
@@ -353,7 +357,7 @@ class Solver:
             kw = dict(kw, precision=PRECISIONS[kw["precision"]])
         self.kw = kw
         self.handle = create(**kw)
-        self.s_k = kw["U"] * kw["V"]
+        self.s_k = kw["U"] * kw["V"] if kw.get("views") is None else len(kw["views"])
         self.hr = (kw["scale"] * kw["H"], kw["scale"] * kw["W"])
         self.s_d = kw.get("nltv_window", 5) ** 2 - 1
 

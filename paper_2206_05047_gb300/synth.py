@@ -257,6 +257,19 @@ def view_offsets(U: int, V: int) -> np.ndarray:
     return out
 
 
+def star_views(U: int, V: int) -> np.ndarray:
+    """Grid indices k = v*U + u of the views on the centre row, the centre
+    column and the two diagonals through the centre (square grid): 17 of
+    5 x 5, the star-shaped subset of Sec. 6.1's x4 experiment."""
+    assert U == V and U % 2 == 1
+    c = (U - 1) // 2
+    ks = set()
+    for t in range(U):
+        for (u, v) in ((t, c), (c, t), (t, t), (t, U - 1 - t)):
+            ks.add(v * U + u)
+    return np.array(sorted(ks), dtype=np.int32)
+
+
 def gaussian_blur_kernel(kb: int, sigma: float) -> np.ndarray:
     """kb x kb Gaussian taps normalised to sum 1 (the blur PSF of Sec. 4.1)."""
     r = (kb - 1) // 2

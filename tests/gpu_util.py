@@ -41,7 +41,8 @@ class Case:
     """One problem: float32 arrays, an oracle on their float64 images and a
     GPU solver on the same float32 values."""
 
-    def __init__(self, wl, seed=0, blur=None, disparity=None, precision="fp32", **overrides):
+    def __init__(self, wl, seed=0, blur=None, disparity=None, precision="fp32", views=None,
+                 **overrides):
         import torch
         from oracle import oracle as om
         from paper_2206_05047_gb300 import lfsr
@@ -49,19 +50,20 @@ class Case:
         self.prob = synth.make_problem(wl, seed=seed)
         self.blur = f32(self.prob.blur if blur is None else blur)
         self.disp = f32(self.prob.disparity if disparity is None else disparity)
-        self.y = f32(self.prob.y)
+        self.views = None if views is None else np.asarray(views, np.int32)
+        self.y = f32(self.prob.y if views is None else self.prob.y[self.views])
         self.x0 = f32(self.prob.x0)
         self.params = dict(lambda1=wl.lambda1, lambda2=wl.lambda2, mu=wl.mu, window=wl.window,
                            patch=wl.patch, h=wl.h, cg_iters=wl.cg_iters, cg_tol=0.0)
         self.params.update(overrides)
         p = self.params
         self.oracle = om.Oracle(wl.U, wl.V, wl.H, wl.W, wl.scale, self.blur.astype(np.float64),
-                                self.disp.astype(np.float64), **p)
+                                self.disp.astype(np.float64), views=self.views, **p)
         self.solver = lfsr.Solver(U=wl.U, V=wl.V, H=wl.H, W=wl.W, scale=wl.scale, blur=self.blur,
                                   disparity=self.disp, lambda1=p["lambda1"], lambda2=p["lambda2"],
                                   mu=p["mu"], nltv_window=p["window"], nltv_patch=p["patch"],
                                   nltv_h=p["h"], cg_iters=p["cg_iters"], cg_tol=p["cg_tol"],
-                                  precision=precision)
+                                  precision=precision, views=self.views)
         self.h = self.solver.handle
         self.torch = torch
         self.dev = torch.device("cuda:0")

@@ -30,7 +30,8 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     import ctypes as C
     # lfsr_params: 7 int32 + 2 pointers + 3 doubles + 2 int32 + double + int32 + double + int32
-    assert C.sizeof(lfsr.lfsr_params) == 112
+    # + views pointer + int32 (padded)
+    assert C.sizeof(lfsr.lfsr_params) == 128
     assert C.sizeof(lfsr.lfsr_stats_t) == 4 * 4 + 8 * 2 + 8 * 2 + 8 * 8 + 8 * 8
 
 
@@ -86,3 +87,20 @@ def test_batch_arguments_are_validated_without_gpu():
         lfsr.Batch([job, dict(job, mu=2.0)])
     assert e.value.code == lfsr.LFSR_EINVAL
     assert "share" in lfsr.batch_last_error(None)
+
+
+def test_view_subsets_are_validated_without_gpu():
+    import numpy as np
+    import pytest
+    blur = np.ones((3, 3), np.float32) / 9
+    disp = np.zeros((16, 16), np.float32)
+    for bad in ([3, 1], [0, 9], [-1, 2], []):
+        with pytest.raises(lfsr.LfsrError) as e:
+            lfsr.create(3, 3, 8, 8, 2, blur, disp, views=bad)
+        assert e.value.code == lfsr.LFSR_EINVAL
+    base = lfsr.estimate_state_bytes(U=5, V=5, H=32, W=32, scale=2, blur=blur,
+                                     disparity=np.zeros((64, 64), np.float32))
+    star = lfsr.estimate_state_bytes(U=5, V=5, H=32, W=32, scale=2, blur=blur,
+                                     disparity=np.zeros((64, 64), np.float32),
+                                     views=[2, 6, 7, 8, 10, 11, 12, 13, 14, 16, 17, 18, 22])
+    assert star < base

@@ -244,3 +244,40 @@ def test_cg_zero_rhs_takes_no_step(oracle_mod):
     x0 = rng.standard_normal(o.hr)
     x, steps, pi = o.cg(w, np.zeros(o.hr), x0, K=5)
     assert steps == 0 and pi == 0.0 and np.array_equal(x, x0)
+
+
+def test_star_subset_of_views():
+    k = synth.star_views(5, 5)
+    assert len(k) == 17 and 12 in k                       # centre view of 5 x 5
+    assert set(24 - k) == set(k)                          # symmetric about the centre
+    assert len(synth.star_views(9, 9)) == 33
+
+
+def test_view_subset_operators_are_the_listed_views(oracle_mod):
+    """A subset problem's view j is the full grid's view views[j]."""
+    wl = synth.custom(U=5, V=5, H=8, W=9, scale=2, kb=3, disparities=(-1.3, 0.7))
+    prob = synth.make_problem(wl, seed=3)
+    full = oracle_mod.Oracle.from_problem(prob)
+    ks = synth.star_views(5, 5)
+    sub = oracle_mod.Oracle.from_problem(prob, views=ks)
+    assert sub.s_k == 17
+    x = np.random.default_rng(0).random(full.hr)
+    g = np.random.default_rng(1).standard_normal((wl.H, wl.W))
+    for j, k in enumerate(ks):
+        assert np.array_equal(sub.A(j, x), full.A(int(k), x))
+        assert np.array_equal(sub.A_T(j, g), full.A_T(int(k), g))
+
+
+def test_single_view_subset_is_a_one_view_problem(oracle_mod):
+    """The centre view alone (theta = 0) equals a 1 x 1 light field: the
+    whole ADMM, not only the operators."""
+    wl = synth.custom(U=3, V=3, H=10, W=10, scale=2, kb=3, disparities=(-1.0, 0.5))
+    prob = synth.make_problem(wl, seed=5)
+    sub = oracle_mod.Oracle.from_problem(prob, views=[4])
+    one = oracle_mod.Oracle(1, 1, wl.H, wl.W, 2, prob.blur, prob.disparity, lambda1=wl.lambda1,
+                            lambda2=wl.lambda2, mu=wl.mu, window=wl.window, patch=wl.patch,
+                            h=wl.h, cg_iters=wl.cg_iters)
+    y = prob.y[4:5]
+    xs, _, _ = sub.admm(y, prob.x0, 4)
+    xo, _, _ = one.admm(y, prob.x0, 4)
+    assert np.array_equal(xs, xo)
