@@ -564,7 +564,7 @@ def run_serve(a):
         lat_p = [done_p[r] - arrivals[r] for r in range(len(arrivals))]
         value_p = sum(work) / (t_end_p - arrivals[0]) / 1e6
     else:
-        lat_p, value_p, dpsnr = [float("nan")], float("nan"), [float("nan")]
+        lat_p, value_p, dpsnr = None, None, None
     h2d = int(sum(probs[k][0].nbytes + probs[k][1].nbytes for k in picks))
     d2h = int(sum(xs[r].nbytes for r in xs))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1,
@@ -583,12 +583,13 @@ def run_serve(a):
                                  "the host; requests and results in host memory"},
             "latency_s": {"p50": pctl(lat, 50), "p99": pctl(lat, 99), "mean": float(np.mean(lat)),
                           "max": float(np.max(lat))},
-            "plain_serial": {"value": value_p, "unit": UNIT,
-                             "latency_s": {"p50": pctl(lat_p, 50), "p99": pctl(lat_p, 99),
-                                           "mean": float(np.mean(lat_p))}},
-            "served_vs_plain": value / value_p,
-            "equal_psnr": {"max_abs_db": float(np.max(np.abs(dpsnr))),
-                           "mean_db": float(np.mean(dpsnr))},
+            "plain_serial": None if value_p is None else {
+                "value": value_p, "unit": UNIT,
+                "latency_s": {"p50": pctl(lat_p, 50), "p99": pctl(lat_p, 99),
+                              "mean": float(np.mean(lat_p))}},
+            "served_vs_plain": None if value_p is None else value / value_p,
+            "equal_psnr": None if dpsnr is None else {"max_abs_db": float(np.max(np.abs(dpsnr))),
+                                                      "mean_db": float(np.mean(dpsnr))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": None, "cpu_baseline": None,
