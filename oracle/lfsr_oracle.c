@@ -17,6 +17,10 @@
  *  - NLTV weights: w_d(u) = exp(-pd/h^2), pd the mean over the patch of
  *    squared differences with clamp-to-edge reads; 0 if u+d leaves the
  *    image.  Directions: the full window minus the centre, raster order.
+ *  - The paper's own weights (Sec. 3.4, weight_scheme 1) with exp(-...)
+ *    where the paper prints exp(+...) for the spatial and edge factors;
+ *    central differences for grad x, forward differences for the
+ *    disparity gradient of the occlusion boundary b.
  *  - Compact form without the 1/sqrt(lambda2) scaling:
  *    F = [lambda1 A; S], b' = [lambda1 y; 0]; the normal matrix is
  *    (lambda2 + mu lambda1^2 / 2) sum_k A_k^T A_k + mu/2 sum_d S_d^T S_d.
@@ -233,7 +237,7 @@ void orc_A_T(const orc_problem *P, int k, const double *g, double *out) {
 /* ------------------------------------------------------------------ */
 static inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-void orc_weights(const orc_problem *P, const double *x, double *w) {
+static void patch_weights(const orc_problem *P, const double *x, double *w) {
   const int Hh = HR_H(P), Wh = HR_W(P), sd = orc_num_dirs(P);
   const int rp = (P->patch - 1) / 2;
   const long p = (long)Hh * Wh;
@@ -263,6 +267,91 @@ void orc_weights(const orc_problem *P, const double *x, double *w) {
   }
   free(di);
   free(dj);
+}
+
+/* Edge factor of the paper's weights (Sec. 3.4): e(u) = exp(-|grad x(u)|^2
+ * / sigma_e), grad x by central differences (x(i+1,j) - x(i-1,j)) / 2 and
+ * (x(i,j+1) - x(i,j-1)) / 2 with clamp-to-edge indices; 1 if sigma_e = 0. */
+void orc_edge_factor(const orc_problem *P, const double *x, double *e) {
+  const int Hh = HR_H(P), Wh = HR_W(P);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < Hh; ++i)
+    for (int j = 0; j < Wh; ++j) {
+      double val = 1.0;
+      if (P->sigma_e > 0.0) {
+        const double gi = 0.5 * (x[(long)clampi(i + 1, 0, Hh - 1) * Wh + j] -
+                                 x[(long)clampi(i - 1, 0, Hh - 1) * Wh + j]);
+        const double gj = 0.5 * (x[(long)i * Wh + clampi(j + 1, 0, Wh - 1)] -
+                                 x[(long)i * Wh + clampi(j - 1, 0, Wh - 1)]);
+        val = exp(-(gi * gi + gj * gj) / P->sigma_e);
+      }
+      e[(long)i * Wh + j] = val;
+    }
+}
+
+/* Occlusion factor (Sec. 3.4, Eq. weight_occ):
+ *   o(u) = exp(-b(u)^2 / (2 sigma_o1^2)) exp(-p(u)^2 / (2 sigma_o2^2)),
+ * b(u) the sum of the two components of the disparity gradient when that
+ * sum is negative, else 0; the gradient by one-sided (forward) differences
+ * omega(i+1,j) - omega(i,j) and omega(i,j+1) - omega(i,j), 0 across the last
+ * row / column.  p(u) is the given projection error (0 without one).  A
+ * factor whose sigma is 0 is 1. */
+void orc_occlusion_factor(const orc_problem *P, double *o) {
+  const int Hh = HR_H(P), Wh = HR_W(P);
+  const double *om = P->disp;
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < Hh; ++i)
+    for (int j = 0; j < Wh; ++j) {
+      const long u = (long)i * Wh + j;
+      double val = 1.0;
+      if (P->sigma_o1 > 0.0) {
+        const double gi = (i + 1 < Hh) ? om[u + Wh] - om[u] : 0.0;
+        const double gj = (j + 1 < Wh) ? om[u + 1] - om[u] : 0.0;
+        const double b = (gi + gj < 0.0) ? gi + gj : 0.0;
+        val *= exp(-b * b / (2.0 * P->sigma_o1 * P->sigma_o1));
+      }
+      if (P->sigma_o2 > 0.0 && P->proj_err) {
+        const double pe = P->proj_err[u];
+        val *= exp(-pe * pe / (2.0 * P->sigma_o2 * P->sigma_o2));
+      }
+      o[u] = val;
+    }
+}
+
+/* The paper's weights (Sec. 3.4): w_d(u) = w_s(d) e(u) o(u) with the
+ * spatial factor w_s(d) = exp(-|d|^2 / sigma_s) (1 if sigma_s = 0); 0 if
+ * u+d leaves the image.  Unlike the patch weights they are not symmetric in
+ * the pixel pair: w_{-d}(u+d) = w_s(d) e(u+d) o(u+d). */
+static void paper_weights(const orc_problem *P, const double *x, double *w) {
+  const int Hh = HR_H(P), Wh = HR_W(P), sd = orc_num_dirs(P);
+  const long p = (long)Hh * Wh;
+  double *e = dalloc(p), *o = dalloc(p);
+  int *di = (int *)malloc(sizeof(int) * sd), *dj = (int *)malloc(sizeof(int) * sd);
+  orc_dirs(P, di, dj);
+  orc_edge_factor(P, x, e);
+  orc_occlusion_factor(P, o);
+  for (int d = 0; d < sd; ++d) {
+    const double ws = P->sigma_s > 0.0 ? exp(-(double)(di[d] * di[d] + dj[d] * dj[d]) / P->sigma_s)
+                                       : 1.0;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < Hh; ++i)
+      for (int j = 0; j < Wh; ++j) {
+        const int ni = i + di[d], nj = j + dj[d];
+        const long u = (long)i * Wh + j;
+        w[d * p + u] = (ni >= 0 && ni < Hh && nj >= 0 && nj < Wh) ? ws * e[u] * o[u] : 0.0;
+      }
+  }
+  free(e);
+  free(o);
+  free(di);
+  free(dj);
+}
+
+void orc_weights(const orc_problem *P, const double *x, double *w) {
+  if (P->weight_scheme == 1)
+    paper_weights(P, x, w);
+  else
+    patch_weights(P, x, w);
 }
 
 /* S: weighted directional gradient G_d(u) = w_d(u) (x(u) - x(u+d))

@@ -34,6 +34,13 @@ typedef struct orc_problem {
   int freeze_weights;     /* test option: weights from x0, then fixed       */
   int n_views;            /* views used (0: all U*V)                        */
   const int *views;       /* their grid indices k = v*U + u, ascending      */
+  /* weight scheme: 0 patch distance (exp(-pd/h^2)); 1 the paper's
+   * spatial * edge * occlusion weights of Sec. 3.4 (each factor whose sigma
+   * is 0 is 1)                                                             */
+  int weight_scheme;
+  double sigma_s, sigma_e;   /* spatial exp(-|d|^2/s_s), edge exp(-|grad x|^2/s_e) */
+  double sigma_o1, sigma_o2; /* occlusion: boundary b, projection error p   */
+  const double *proj_err;    /* HR projection error p(u); NULL: p = 0        */
 } orc_problem;
 
 int    orc_num_threads(void);
@@ -59,6 +66,11 @@ void   orc_A_T   (const orc_problem *P, int k, const double *g, double *out);
 
 /* weighted non-local TV (Eq. sr_reg, Sec. 4.1 wdg / wdd) */
 void   orc_weights(const orc_problem *P, const double *x, double *w);
+/* factors of the paper's weights (Sec. 3.4, Eq. weight_occ): the edge
+ * factor e(u) of x and the occlusion factor o(u) of the disparity map and
+ * projection error, HR images */
+void   orc_edge_factor(const orc_problem *P, const double *x, double *e);
+void   orc_occlusion_factor(const orc_problem *P, double *o);
 void   orc_S  (const orc_problem *P, const double *w, const double *x, double *out);
 void   orc_S_T(const orc_problem *P, const double *w, const double *g, double *out);
 

@@ -41,7 +41,10 @@ class _Problem(C.Structure):
                 ("window", C.c_int), ("patch", C.c_int), ("h", C.c_double),
                 ("cg_iters", C.c_int), ("cg_tol", C.c_double),
                 ("freeze_weights", C.c_int), ("n_views", C.c_int),
-                ("views", C.POINTER(C.c_int))]
+                ("views", C.POINTER(C.c_int)),
+                ("weight_scheme", C.c_int), ("sigma_s", C.c_double), ("sigma_e", C.c_double),
+                ("sigma_o1", C.c_double), ("sigma_o2", C.c_double),
+                ("proj_err", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -66,6 +69,8 @@ def _load():
             "orc_A": (None, [P, C.c_int, _dp, _dp]),
             "orc_A_T": (None, [P, C.c_int, _dp, _dp]),
             "orc_weights": (None, [P, _dp, _dp]),
+            "orc_edge_factor": (None, [P, _dp, _dp]),
+            "orc_occlusion_factor": (None, [P, _dp]),
             "orc_S": (None, [P, _dp, _dp, _dp]),
             "orc_S_T": (None, [P, _dp, _dp, _dp]),
             "orc_prox": (None, [C.c_long, _dp, C.c_double, _dp]),
@@ -99,7 +104,8 @@ class Oracle:
 
     def __init__(self, U, V, H, W, zeta, blur, disparity, lambda1=1.0, lambda2=4.0,
                  mu=1.0, window=5, patch=3, h=0.1, cg_iters=5, cg_tol=0.0,
-                 freeze_weights=False, views=None):
+                 freeze_weights=False, views=None, weights="patch", sigma_s=0.0, sigma_e=0.0,
+                 sigma_o1=0.0, sigma_o2=0.0, proj_err=None):
         self._lib = _load()
         self.blur = _f64(blur)
         kb = self.blur.shape[0]
@@ -115,6 +121,13 @@ class Oracle:
             assert (np.diff(self.views) > 0).all() and self.views[0] >= 0
             assert self.views[-1] < U * V
         self.s_k = U * V if self.views is None else len(self.views)
+        # weights: "patch" (exp(-pd/h^2)) or "paper" (Sec. 3.4: spatial *
+        # edge * occlusion, each factor with sigma 0 is 1); proj_err: the
+        # HR projection error p of the occlusion factor (None: 0)
+        assert weights in ("patch", "paper")
+        self.proj_err = None if proj_err is None else _f64(proj_err)
+        if self.proj_err is not None:
+            assert self.proj_err.shape == (zeta * H, zeta * W)
         self.hr = (zeta * H, zeta * W)
         self.p = zeta * H * zeta * W
         self.q = H * W
@@ -125,7 +138,10 @@ class Oracle:
                            int(bool(freeze_weights)),
                            0 if self.views is None else len(self.views),
                            None if self.views is None
-                           else self.views.ctypes.data_as(C.POINTER(C.c_int)))
+                           else self.views.ctypes.data_as(C.POINTER(C.c_int)),
+                           int(weights == "paper"), sigma_s, sigma_e, sigma_o1, sigma_o2,
+                           None if self.proj_err is None
+                           else self.proj_err.ctypes.data_as(C.POINTER(C.c_double)))
         self.s_d = self._lib.orc_num_dirs(C.byref(self._P))
 
     @classmethod
@@ -193,6 +209,12 @@ class Oracle:
         out = np.zeros((self.s_d,) + self.hr)
         self._lib.orc_weights(self._p, _f64(x), out)
         return out
+
+    def edge_factor(self, x):
+        out = self._hr(); self._lib.orc_edge_factor(self._p, _f64(x), out); return out
+
+    def occlusion_factor(self):
+        out = self._hr(); self._lib.orc_occlusion_factor(self._p, out); return out
 
     def S(self, w, x):
         out = np.zeros((self.s_d,) + self.hr)
