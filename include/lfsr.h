@@ -98,6 +98,28 @@ extern "C" {
 #define LFSR_KEEP_VIEWS_FP32 256
 #define LFSR_FP16_MAX_INV_MU 8192.0
 
+/* Weight scheme of the regulariser (lfsr_params.weights).
+ *
+ * LFSR_WEIGHTS_PATCH (0): w_d(u) = exp(-pd/h^2), the patch distance of the
+ * conventions above; symmetric in the pixel pair.
+ *
+ * LFSR_WEIGHTS_PAPER (1): the paper's weights (Sec. 3.4, Eq. weight_occ),
+ *   w_d(u) = exp(-|d|^2/sigma_s) * e(u) * o(u),   0 if u+d leaves the image,
+ *   e(u) = exp(-|grad x(u)|^2/sigma_e), grad x by central differences
+ *          (x(i+1,j) - x(i-1,j))/2, (x(i,j+1) - x(i,j-1))/2, clamped indices,
+ *          from the current x (rebuilt every ADMM iteration, like the patch
+ *          weights),
+ *   o(u) = exp(-b(u)^2/(2 sigma_o1^2)) * exp(-p(u)^2/(2 sigma_o2^2)),
+ *          b(u) = min(0, (omega(i+1,j) - omega(i,j)) + (omega(i,j+1) - omega(i,j)))
+ *          (forward differences, 0 across the last row / column), p the
+ *          projection error (lfsr_params.proj_err, 0 when NULL); o is fixed
+ *          by the disparity map and computed once by lfsr_create.
+ * A sigma of 0 makes its factor 1.  These weights are directed:
+ * w_{-d}(u+d) = exp(-|d|^2/sigma_s) e(u+d) o(u+d) differs from w_d(u), and
+ * the z/w-step uses each.  nltv_patch and nltv_h are ignored. */
+#define LFSR_WEIGHTS_PATCH 0
+#define LFSR_WEIGHTS_PAPER 1
+
 /* Problem and solver parameters (copied by lfsr_create).  struct_size must
  * be sizeof(lfsr_params). */
 typedef struct lfsr_params {
@@ -123,6 +145,13 @@ typedef struct lfsr_params {
                               x4 experiment uses a star of 17 of 5 x 5);
                               NULL: all U*V.  Copied.                        */
   int32_t n_views;         /* entries of views (ignored when views is NULL)  */
+  int32_t weights;         /* LFSR_WEIGHTS_PATCH or LFSR_WEIGHTS_PAPER        */
+  float sigma_s, sigma_e;  /* paper weights: spatial, edge scale; >= 0      */
+  float sigma_o1, sigma_o2;/* paper weights: occlusion boundary, projection
+                              error scale; >= 0 (0: factor 1)               */
+  const float *proj_err;   /* host, optional: Hh*Wh projection error p of the
+                              occlusion factor; NULL: p = 0.  Read by
+                              lfsr_create only.                             */
 } lfsr_params;
 
 typedef struct lfsr_handle lfsr_handle;
@@ -204,7 +233,10 @@ int lfsr_apply_A(lfsr_handle *h, int view, const float *x, float *out, int mem_k
  * holding s_k*q floats. */
 int lfsr_apply_AT(lfsr_handle *h, int view, const float *g, float *out, int mem_kind);
 
-/* NLTV weights of x in the canonical layout (s_d*p floats). */
+/* NLTV weights of x in the canonical layout (s_d*p floats): w_d(u) at
+ * [d][u].  With 16-bit storage and the patch weights these are the stored
+ * (rounded) edge weights; the paper's directed weights are returned in
+ * float32. */
 int lfsr_weights(lfsr_handle *h, const float *x, float *w, int mem_kind);
 
 /* q = M p with M = (l2 + mu l1^2/2) sum_k A_k^T A_k + mu/2 sum_d S_d^T S_d
@@ -407,7 +439,9 @@ int lfsr_server_stats(const lfsr_server *s, lfsr_server_stats_t *out);
  * pointers of the current device (Hh*Wh floats each); *pMp (host) receives
  * <p, M p> in float64.  Work is ordered on cuda_stream and the call blocks
  * until it is done.  The message of a failure is readable with
- * lfsr_last_error(NULL). */
+ * lfsr_last_error(NULL).  Only the patch weights are supported here
+ * (LFSR_WEIGHTS_PAPER returns LFSR_EUNSUPPORTED: its occlusion factor is
+ * state that lfsr_create computes). */
 #define LFSR_NOALLOC_MAX_TILES 4096
 #define LFSR_NOALLOC_SCRATCH_BYTES (64 * 1024 + 256)
 

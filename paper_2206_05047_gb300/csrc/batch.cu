@@ -109,12 +109,6 @@ void batch_free(lfsr_batch* b) {
   b->jobs.clear();
 }
 
-// Parameters every light field of a batch must share.
-bool same_solver(const lfsr_params& a, const lfsr_params& c) {
-  return a.lambda1 == c.lambda1 && a.lambda2 == c.lambda2 && a.mu == c.mu &&
-         a.nltv_window == c.nltv_window && a.nltv_patch == c.nltv_patch && a.nltv_h == c.nltv_h &&
-         a.cg_iters == c.cg_iters && a.cg_tol == c.cg_tol && a.precision == c.precision;
-}
 
 // Same operator group: scale and blur taps equal.
 bool same_operator(const Geom& a, const Geom& c) {
@@ -446,6 +440,18 @@ lfsr_batch* lfsr::batch_new_shared(cudaStream_t stream) {
 
 int lfsr::batch_parity(const lfsr_batch* b) { return b->parity; }
 
+// Parameters every light field of a batch (and of a server) must share.
+bool lfsr::same_solver(const lfsr_params& a, const lfsr_params& c) {
+  if (a.weights != c.weights) return false;
+  if (a.weights == LFSR_WEIGHTS_PAPER &&
+      (a.sigma_s != c.sigma_s || a.sigma_e != c.sigma_e || a.sigma_o1 != c.sigma_o1 ||
+       a.sigma_o2 != c.sigma_o2))
+    return false;
+  return a.lambda1 == c.lambda1 && a.lambda2 == c.lambda2 && a.mu == c.mu &&
+         a.nltv_window == c.nltv_window && a.nltv_patch == c.nltv_patch && a.nltv_h == c.nltv_h &&
+         a.cg_iters == c.cg_iters && a.cg_tol == c.cg_tol && a.precision == c.precision;
+}
+
 extern "C" {
 
 int lfsr_batch_create(const lfsr_params* params, int n, void* cuda_stream, lfsr_batch** out) {
@@ -457,7 +463,8 @@ int lfsr_batch_create(const lfsr_params* params, int n, void* cuda_stream, lfsr_
     if (!same_solver(params[0], params[j]))
       return bfail(nullptr, LFSR_EINVAL,
                    "light fields of a batch must share lambda1, lambda2, mu, the NLTV window, "
-                   "patch and h, cg_iters, cg_tol and precision");
+                   "patch and h, cg_iters, cg_tol, precision and the weight scheme with its "
+                   "sigmas");
   lfsr_batch* b = new (std::nothrow) lfsr_batch();
   if (!b) return bfail(nullptr, LFSR_ENOMEM, "host allocation failed");
   b->stream = (cudaStream_t)cuda_stream;

@@ -55,7 +55,7 @@ void free_all(lfsr_handle* h) {
     cudaEventDestroy(ev.b);
   }
   void* bufs[] = {h->disp, h->y, h->x[0], h->x[1], h->wA[0], h->wA[1], h->wS[0],
-                  h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt, h->cb};
+                  h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt, h->cb, h->occ};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->partials) cudaFree(h->partials);
@@ -156,6 +156,7 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
     nbk.out = h->R;
     nbk.wS_old = h->wS[b];
     nbk.wS_new = h->wS[nb];
+    nbk.occ = h->occ;
     nbk.partials = part_slot(h, RED_DW_S);
     nbk.sc = sc;
     return nl_launch(NL_BLOCK, g, h->nl, nbk, s);
@@ -194,6 +195,7 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
       if (h->nlf) return nla2_launch(g, handle_table(h, KD_NLA, b, pb), s);
       NlArgs na{};
       na.x = h->x[b];
+      na.occ = h->occ;
       na.r = h->R;
       na.p_old = h->P[1 - pb];
       na.p_new = h->P[pb];
@@ -312,6 +314,14 @@ int validate(const lfsr_params* pr) {
     return fail(nullptr, LFSR_EINVAL,
                 "precision must be LFSR_FP32, LFSR_FP16_STORAGE or LFSR_BF16_STORAGE, "
                 "optionally | LFSR_KEEP_VIEWS_FP32");
+  if (pr->weights != LFSR_WEIGHTS_PATCH && pr->weights != LFSR_WEIGHTS_PAPER)
+    return fail(nullptr, LFSR_EINVAL, "weights must be LFSR_WEIGHTS_PATCH or LFSR_WEIGHTS_PAPER");
+  if (pr->weights == LFSR_WEIGHTS_PAPER) {
+    const float sg[4] = {pr->sigma_s, pr->sigma_e, pr->sigma_o1, pr->sigma_o2};
+    for (float v : sg)
+      if (!(v >= 0.f) || !std::isfinite(v))
+        return fail(nullptr, LFSR_EINVAL, "sigma_s, sigma_e, sigma_o1, sigma_o2 must be finite and >= 0");
+  }
   if (base == LFSR_FP16_STORAGE && 1.0 / pr->mu > LFSR_FP16_MAX_INV_MU)
     return fail(nullptr, LFSR_EUNSUPPORTED,
                 "LFSR_FP16_STORAGE needs 1/mu <= 8192 (duals are bounded by 1/mu)");
@@ -350,6 +360,7 @@ JobArgs standalone_job(const lfsr_handle* h) {
   j.V = h->g.V;
   j.disp = h->disp;
   j.theta = h->theta;
+  j.occ = h->occ;
   j.sc = h->sc + 1;
   return j;
 }
@@ -372,7 +383,8 @@ int64_t lfsr::estimate_state_bytes(const lfsr_params* pr) {
   const int base = pr->precision & ~LFSR_KEEP_VIEWS_FP32;
   const int64_t es = base == LFSR_FP32 ? 4 : 2;
   const int64_t ey = (base == LFSR_FP32 || (pr->precision & LFSR_KEEP_VIEWS_FP32)) ? 4 : 2;
-  const bool nlf = pr->nltv_window >= 3 && pr->nltv_window <= 7 && pr->nltv_patch <= 5;
+  const bool paper = pr->weights == LFSR_WEIGHTS_PAPER;
+  const bool nlf = pr->nltv_window >= 3 && pr->nltv_window <= 7 && (paper || pr->nltv_patch <= 5);
   int64_t b = 4 * p              // disparity
               + ey * nA          // views
               + 2 * 4 * p        // x ping-pong
@@ -380,6 +392,7 @@ int64_t lfsr::estimate_state_bytes(const lfsr_params* pr) {
               + 2 * es * nS      // regulariser duals
               + 4 * 4 * p;       // P ping-pong, R, Q
   if (nlf) b += es * sh * p + 4 * sh * p;   // stored weights, divergence terms
+  if (paper) b += 4 * p;                    // occlusion factor
   const int64_t nl_tiles = ((Hh + 31) / 32) * ((Wh + 31) / 32);
   b += (int64_t)RED_NUM * 8 * (nl_tiles > 4096 ? nl_tiles : 4096);   // reduction slots (bound)
   b += 2 * (int64_t)sizeof(DevScalars) + (4 * KD_NUM + 4) * (int64_t)sizeof(JobArgs) +
@@ -421,6 +434,7 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
   j.units = kind_units(h, kind);
   j.disp = h->disp;
   j.theta = h->theta;
+  j.occ = h->occ;
   j.sc = h->sc;
   switch (kind) {
     case KD_NLW:   // weights from x^(n-1), regulariser z/w-step, v := 0
@@ -490,6 +504,8 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   std::vector<float> K(pr->blur, pr->blur + (size_t)pr->kb * pr->kb);
   if (!finite_all(K.data(), K.size()) || !finite_all(pr->disparity, p))
     return fail(nullptr, LFSR_EINVAL, "blur or disparity has non-finite values");
+  if (pr->weights == LFSR_WEIGHTS_PAPER && pr->proj_err && !finite_all(pr->proj_err, p))
+    return fail(nullptr, LFSR_EINVAL, "proj_err has non-finite values");
 
   lfsr_handle* h = new (std::nothrow) lfsr_handle();
   if (!h) return fail(nullptr, LFSR_ENOMEM, "host allocation failed");
@@ -497,6 +513,7 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   h->prm.blur = nullptr;
   h->prm.disparity = nullptr;
   h->prm.views = nullptr;
+  h->prm.proj_err = nullptr;
   if (pr->views) h->views.assign(pr->views, pr->views + pr->n_views);
   h->stream = (cudaStream_t)cuda_stream;
   Geom& g = h->g;
@@ -536,6 +553,15 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   }
   g.inv_h2 = (float)(1.0 / (pr->nltv_h * pr->nltv_h));
   g.inv_np = (float)(1.0 / (double)(pr->nltv_patch * pr->nltv_patch));
+  g.wscheme = pr->weights == LFSR_WEIGHTS_PAPER ? WS_PAPER : WS_PATCH;
+  if (g.wscheme == WS_PAPER) {
+    // no patches; the x halo of one pixel feeds the edge factor's central
+    // differences
+    g.patch_r = 1;
+    g.inv_np = 1.f / 9.f;
+    g.inv_sig_s = pr->sigma_s > 0.f ? (float)(1.0 / pr->sigma_s) : 0.f;
+    g.inv_sig_e = pr->sigma_e > 0.f ? (float)(1.0 / pr->sigma_e) : 0.f;
+  }
   g.lambda1 = (float)pr->lambda1;
   g.lambda2 = (float)pr->lambda2;
   g.mu = (float)pr->mu;
@@ -619,6 +645,7 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   h->nlf = nlf_supported(g);
   if (e == cudaSuccess && h->nlf) e = dalloc_st(h, &h->wt, (size_t)g.sh * p, h->esize);
   if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->cb, (size_t)g.sh * p);
+  if (e == cudaSuccess && g.wscheme == WS_PAPER) e = dalloc(h, &h->occ, p);
   if (e == cudaSuccess) e = dalloc(h, &h->partials, (size_t)RED_NUM * h->max_grid);
   if (e == cudaSuccess) e = dalloc(h, &h->sc, 2);
   if (e == cudaSuccess) e = dalloc(h, &h->theta, (size_t)g.sk);
@@ -641,6 +668,19 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
                         cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->disp, pr->disparity, p * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && g.wscheme == WS_PAPER) {
+    // occlusion factor of the disparity map and the projection error (R
+    // holds the projection error until the first load)
+    const float* pe = nullptr;
+    if (pr->proj_err && pr->sigma_o2 > 0.f) {
+      e = cudaMemcpyAsync(h->R, pr->proj_err, p * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+      pe = h->R;
+    }
+    const double s1 = pr->sigma_o1, s2 = pr->sigma_o2;
+    if (e == cudaSuccess)
+      e = occlusion_launch(Hh, Wh, h->disp, pe, s1 > 0.0 ? (float)(0.5 / (s1 * s1)) : 0.f,
+                           s2 > 0.0 ? (float)(0.5 / (s2 * s2)) : 0.f, h->occ, h->stream);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->sc, 0, 2 * sizeof(DevScalars), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->P[0], 0, p * sizeof(float), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->P[1], 0, p * sizeof(float), h->stream);
@@ -945,7 +985,7 @@ int lfsr_weights(lfsr_handle* h, const float* x, float* w, int mem) {
     ws = h->io;
   }
   CK(h, cudaMemsetAsync(ws, 0, h->nS * sizeof(float), h->stream), "clear w");
-  if (h->nlf) {
+  if (h->nlf && h->g.wscheme == WS_PATCH) {
     JobArgs j = standalone_job(h);
     j.tiles_x = h->nl_tiles_x;
     j.units = h->nl_units;
@@ -956,8 +996,11 @@ int lfsr_weights(lfsr_handle* h, const float* x, float* w, int mem) {
     CK(h, nlw2_launch(0, h->g, t, h->stream), "weights");
     CK(h, weights_to_canonical(h->g, h->wt, ws, h->stream), "weights layout");
   } else {
+    // the paper's directed weights (the stored edge weights hold their
+    // root mean square per edge), or windows beyond the stored-weight path
     NlArgs a{};
     a.x = xs;
+    a.occ = h->occ;
     a.out = ws;
     a.sc = h->sc + 1;
     CK(h, nl_launch(NL_WEIGHTS, h->g, h->nl, a, h->stream), "weights");
@@ -1003,6 +1046,7 @@ int lfsr_apply_normal(lfsr_handle* h, const float* xw, const float* p, float* qo
   } else {
     NlArgs na{};
     na.x = xs;
+    na.occ = h->occ;
     na.p_old = ps;
     na.out = qs;
     na.partials = part_slot(h, RED_NLTV);

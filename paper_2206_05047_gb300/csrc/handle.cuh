@@ -36,6 +36,7 @@ struct lfsr_handle {
   int grid_op = 0, grid_vec = 0, max_grid = 0;
   // device buffers
   float* disp = nullptr;
+  float* occ = nullptr;                // paper weights: occlusion factor o (HR)
   float2* theta = nullptr;             // angular offsets of the data's views
   std::vector<int32_t> views;          // the listed subset (empty: the grid)
   float* x[2] = {nullptr, nullptr};
@@ -99,6 +100,8 @@ int64_t estimate_state_bytes(const lfsr_params* params);
 lfsr_batch* batch_new_shared(cudaStream_t stream);
 cudaError_t batch_assign(lfsr_batch* b, const std::vector<lfsr_handle*>& jobs);
 int batch_parity(const lfsr_batch* b);
+// Solver parameters all light fields of one batch or server must share.
+bool same_solver(const lfsr_params& a, const lfsr_params& c);
 // Records an error on h (and the thread) and returns code.
 int handle_fail(lfsr_handle* h, int code, const std::string& msg);
 int handle_cuda_fail(lfsr_handle* h, cudaError_t e, const char* what);

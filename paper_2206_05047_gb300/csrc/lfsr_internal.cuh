@@ -13,6 +13,8 @@ namespace lfsr {
 // Storage kinds of the large streams (values of lfsr_params.precision).
 enum { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
 inline size_t storage_bytes(int st) { return st == ST_F32 ? 4 : 2; }
+// Weight schemes of the regulariser (values of lfsr_params.weights).
+enum { WS_PATCH = 0, WS_PAPER = 1 };
 
 // Geometry and solver constants, passed by value to every kernel (lives in
 // the kernel-parameter constant bank; all reads are warp-uniform).
@@ -34,6 +36,9 @@ struct Geom {
   double tau;            // CG threshold
   int st;                // storage kind of the duals and stored weights (ST_*)
   int st_y;              // storage kind of the LR views
+  int wscheme;           // WS_PATCH or WS_PAPER
+  float inv_sig_s;       // paper weights: 1 / sigma_s (0: spatial factor 1)
+  float inv_sig_e;       // paper weights: 1 / sigma_e (0: edge factor 1)
   float kv[LFSR_MAX_KB], kh[LFSR_MAX_KB];
   float k2[LFSR_MAX_KB * LFSR_MAX_KB];
   float tu[LFSR_MAX_VIEWS], tv[LFSR_MAX_VIEWS];
@@ -102,6 +107,7 @@ struct NlArgs {
   float* out;            // BLOCK: v (stored); APPLY: q (stored); WEIGHTS: w
   const void* wS_old;    // BLOCK: pair-layout duals (read, g.st)
   void* wS_new;          // BLOCK: pair-layout duals (written, g.st)
+  const float* occ;      // paper weights: occlusion factor o (HR)
   double* partials;
   DevScalars* sc;
   int use_beta;          // APPLY: p_new = r + beta p_old (else p_new = src p)
@@ -135,6 +141,7 @@ struct JobArgs {
   void* wS_new;
   void* wt;                   // NLTV: stored edge weights (kind g.st)
   float* cb;                  // NLTV block -> vector init: per-edge divergence terms
+  const float* occ;           // NLTV (paper weights): occlusion factor o (HR)
   const float* r;             // NLTV apply: CG residual
   const float* p_old;         // NLTV apply: previous direction; vector update: p
   float* p_new;               // NLTV apply: new direction
@@ -195,6 +202,13 @@ cudaError_t nlw2_launch(int block, const Geom& g, const TableArgs& t, cudaStream
 constexpr int NLA_CHUNK = 6;
 cudaError_t nla2_launch(const Geom& g, const TableArgs& t, cudaStream_t s, int chunk = NLA_CHUNK);
 cudaError_t cg_init_nltv_launch(const Geom& g, const TableArgs& t, cudaStream_t s);
+// The paper's weights (g.wscheme == WS_PAPER): the stored-weight
+// z/w-step (called by nlw2_launch), and the occlusion factor
+// o = exp(-b^2 inv2_o1) exp(-pe^2 inv2_o2) of the disparity map disp and the
+// projection error pe (NULL: 0), Hh x Wh floats each.
+cudaError_t nlw2p_launch(int block, const Geom& g, const TableArgs& t, cudaStream_t s);
+cudaError_t occlusion_launch(int Hh, int Wh, const float* disp, const float* pe, float inv2_o1,
+                             float inv2_o2, float* occ, cudaStream_t s);
 
 // Specialised operator kernel for separable kernels of common (zeta, kb).
 bool fast_supported(const Geom& g);

@@ -158,6 +158,7 @@ static cudaError_t nlw2_st(int block, const Geom& g, const TableArgs& t, cudaStr
 }
 
 cudaError_t nlw2_launch(int block, const Geom& g, const TableArgs& t, cudaStream_t s) {
+  if (g.wscheme == WS_PAPER) return nlw2p_launch(block, g, t, s);
   if (t.total_units < 1) return cudaErrorInvalidValue;
   switch (g.st) {
     case ST_F32: return nlw2_st<float>(block, g, t, s);

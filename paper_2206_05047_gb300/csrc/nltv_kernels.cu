@@ -8,8 +8,15 @@
 //               optionally first forms the CG direction p = r + beta p_old
 //   NL_WEIGHTS  the weights themselves, canonical [d][u] layout
 //
-// Weights are symmetric in the pixel pair: w_d(u) = w_{-d}(u+d) (the patch
-// distance is symmetric and clamped reads use the same pixel pairs).  The
+// Two weight schemes (g.wscheme): the patch distance below, and the paper's
+// directed weights w_d(u) = w_s(d) g(u) of Sec. 3.4 (g = edge factor of x
+// times the stored occlusion factor, staged over the tile + window halo).
+// The edge (u, u+d) then carries w_a = w_s(d) g(u) and w_b = w_s(d) g(u+d):
+// c = w_a g_a - w_b g_b and, for S^T S, the pair weight (w_a^2 + w_b^2) / 2
+// in place of w^2.
+//
+// Patch weights are symmetric in the pixel pair: w_d(u) = w_{-d}(u+d) (the
+// patch distance is symmetric and clamped reads use the same pixel pairs).  The
 // kernel therefore visits each undirected edge (u, u+d) once, for d in the
 // half window H = {d : d before 0 in raster order}, and keeps both duals
 // of the edge -- direction d at u and direction -d at u+d -- side by side
@@ -50,6 +57,8 @@ k_nltv(const Geom g, const NlPlan P, const NlArgs a) {
   const int NPc = NL_TW + 2 * wr;
   float* sQ = sP + (NL_TH + 2 * wr) * NPc;      // box sums, NQr x NQc
   float* sC = sQ + P.NQr * P.NQc;               // edge quantity, NQr x NQc
+  float* sG = sC + P.NQr * P.NQc;               // paper weights: g over tile + wr
+  const bool paper = g.wscheme == WS_PAPER;     // (then pr = 1: x halo wr + 1)
 
   // stage x (clamped) and, for APPLY, the CG direction (zero outside)
   for (int rr = warp; rr < P.NXr; rr += NL_WARPS) {
@@ -83,6 +92,28 @@ k_nltv(const Geom g, const NlPlan P, const NlArgs a) {
     }
   }
   __syncthreads();
+  if (paper) {
+    // g(v) = exp(-|grad x(v)|^2 / sigma_e) o(v), central differences of the
+    // clamped x; 0 outside the image (read only by dropped edges)
+    for (int rr = warp; rr < NL_TH + 2 * wr; rr += NL_WARPS) {
+      const int vi = i0 - wr + rr;
+      for (int cc = lane; cc < NPc; cc += 32) {
+        const int vj = j0 - wr + cc;
+        float gv = 0.f;
+        if (vi >= 0 && vi < Hh && vj >= 0 && vj < Wh) {
+          gv = __ldg(a.occ + (size_t)vi * Wh + vj);
+          if (g.inv_sig_e > 0.f) {
+            const float* xc = sX + (rr + pr) * NXc + (cc + pr);
+            const float gi = 0.5f * (xc[NXc] - xc[-NXc]);
+            const float gj = 0.5f * (xc[1] - xc[-1]);
+            gv *= expf(-fmaf(gi, gi, gj * gj) * g.inv_sig_e);
+          }
+        }
+        sG[rr * NPc + cc] = gv;
+      }
+    }
+    __syncthreads();
+  }
 
   float acc[NL_PIX];
 #pragma unroll
@@ -95,8 +126,9 @@ k_nltv(const Geom g, const NlPlan P, const NlArgs a) {
     // E_d = tile U (tile - d), origin (er0, ec0) relative to (i0, j0)
     const int er0 = 0, ec0 = min(0, -dj);
     const int ne_r = TRr - di, ne_c = TRc + (dj < 0 ? -dj : dj);
+    const float ws = paper ? expf(-(float)(di * di + dj * dj) * g.inv_sig_s) : 1.f;
     // 1. horizontal box sums of squared patch differences, rows of E_d +- pr
-    const int nq_r = ne_r + 2 * pr;
+    const int nq_r = paper ? 0 : ne_r + 2 * pr;
     for (int qa = warp; qa < nq_r; qa += NL_WARPS) {
       const int xr = er0 - pr + qa + hx;        // row in sX of v
       const float* rowA = sX + xr * NXc;
@@ -117,11 +149,21 @@ k_nltv(const Geom g, const NlPlan P, const NlArgs a) {
       const int vi = i0 + er0 + ea;
       for (int ec = lane; ec < ne_c; ec += 32) {
         const int vj = j0 + ec0 + ec;
-        float pd = 0.f;
-        for (int b = 0; b <= 2 * pr; ++b) pd += sQ[(ea + b) * P.NQc + ec];
         const bool v_in = vi >= 0 && vi < Hh && vj >= 0 && vj < Wh;
         const bool valid = v_in && (vi + di >= 0) && (vi + di < Hh) && (vj + dj >= 0) && (vj + dj < Wh);
-        const float w = valid ? expf(-pd * g.inv_np * g.inv_h2) : 0.f;
+        float w = 0.f, w_a = 0.f, w_b = 0.f;   // patch: w_a = w_b = w
+        if (paper) {
+          if (valid) {
+            const float* gv = sG + (er0 + ea + wr) * NPc + (ec0 + ec + wr);
+            w_a = ws * gv[0];
+            w_b = ws * gv[di * NPc + dj];
+          }
+        } else {
+          float pd = 0.f;
+          for (int b = 0; b <= 2 * pr; ++b) pd += sQ[(ea + b) * P.NQc + ec];
+          w = valid ? expf(-pd * g.inv_np * g.inv_h2) : 0.f;
+          w_a = w_b = w;
+        }
         const bool own = ea < TRr && (ec + ec0) >= 0 && (ec + ec0) < TRc;
         float cval = 0.f;
         if (MODE == NL_BLOCK) {
@@ -131,12 +173,12 @@ k_nltv(const Geom g, const NlPlan P, const NlArgs a) {
             const float wb = ld_kind(a.wS_old, (size_t)(2 * idx + 1) * p + gi, g.st);
             const int xr = er0 + ea + hx, xc = ec0 + ec + hx;
             const float diff = valid ? (sX[xr * NXc + xc] - sX[(xr + di) * NXc + xc + dj]) : 0.f;
-            const float ua = fmaf(w, diff, wa);          // (S_d x)(v) + w
-            const float ub = fmaf(-w, diff, wb);         // (S_-d x)(v+d) + w
+            const float ua = fmaf(w_a, diff, wa);        // (S_d x)(v) + w
+            const float ub = fmaf(-w_b, diff, wb);       // (S_-d x)(v+d) + w
             const float an = fminf(fmaxf(ua, -g.thr), g.thr);
             const float bn = fminf(fmaxf(ub, -g.thr), g.thr);
             const float fa = 2.f * an - wa, fb = 2.f * bn - wb;
-            cval = w * (fa - fb);
+            cval = paper ? fmaf(w_a, fa, -w_b * fb) : w * (fa - fb);
             if (own) {
               st_kind(a.wS_new, (size_t)(2 * idx) * p + gi, g.st, an);
               st_kind(a.wS_new, (size_t)(2 * idx + 1) * p + gi, g.st, bn);
@@ -147,14 +189,14 @@ k_nltv(const Geom g, const NlPlan P, const NlArgs a) {
         } else if (MODE == NL_APPLY) {
           const int pr_ = er0 + ea + wr, pc_ = ec0 + ec + wr;
           const float dp = sP[pr_ * NPc + pc_] - sP[(pr_ + di) * NPc + pc_ + dj];
-          const float w2 = w * w;
+          const float w2 = paper ? 0.5f * fmaf(w_a, w_a, w_b * w_b) : w * w;
           cval = w2 * dp;
           if (own) part += (double)w2 * (double)dp * (double)dp;
         } else {  // NL_WEIGHTS
           if (own) {
             const size_t gi = (size_t)vi * Wh + vj;
-            a.out[(size_t)idx * p + gi] = w;
-            if (valid) a.out[(size_t)(sd - 1 - idx) * p + (size_t)(vi + di) * Wh + (vj + dj)] = w;
+            a.out[(size_t)idx * p + gi] = w_a;
+            if (valid) a.out[(size_t)(sd - 1 - idx) * p + (size_t)(vi + di) * Wh + (vj + dj)] = w_b;
           }
         }
         sC[ea * P.NQc + ec] = cval;
@@ -203,8 +245,12 @@ cudaError_t nl_plan(const Geom& g, NlPlan* P, int smem_limit) {
   P->NXc = NL_TW + 2 * (wr + pr);
   P->NQr = NL_TH + wr + 2 * pr;
   P->NQc = NL_TW + wr;
-  const size_t floats = (size_t)P->NXr * P->NXc + (size_t)(NL_TH + 2 * wr) * (NL_TW + 2 * wr) +
-                        2 * (size_t)P->NQr * P->NQc;
+  size_t floats = (size_t)P->NXr * P->NXc + (size_t)(NL_TH + 2 * wr) * (NL_TW + 2 * wr) +
+                  2 * (size_t)P->NQr * P->NQc;
+  if (g.wscheme == WS_PAPER) {
+    if (pr < 1) return cudaErrorInvalidValue;   // the edge factor reads x at +-1
+    floats += (size_t)(NL_TH + 2 * wr) * (NL_TW + 2 * wr);
+  }
   P->smem_bytes = floats * sizeof(float);
   P->threads = NL_THREADS;
   return P->smem_bytes <= (size_t)smem_limit ? cudaSuccess : cudaErrorInvalidValue;

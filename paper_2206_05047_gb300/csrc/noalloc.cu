@@ -108,6 +108,9 @@ extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_d
       !(pr->nltv_patch & 1) || !(pr->nltv_h > 0.0) || !(pr->mu > 0.0) ||
       !(pr->lambda1 >= 0.0) || !(pr->lambda2 >= 0.0))
     return nfail(LFSR_EINVAL, "invalid size or parameter");
+  if (pr->weights != LFSR_WEIGHTS_PATCH)
+    return nfail(pr->weights == LFSR_WEIGHTS_PAPER ? LFSR_EUNSUPPORTED : LFSR_EINVAL,
+                 "the no-allocation entry point takes the patch weights only");
   const long long Hh = (long long)pr->scale * pr->H, Wh = (long long)pr->scale * pr->W;
   // the NLTV kernel runs one CTA per 32 x 32 HR tile; its partials must fit
   const long long nl_tiles = ((Hh + 31) / 32) * ((Wh + 31) / 32);

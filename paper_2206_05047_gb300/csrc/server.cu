@@ -28,6 +28,7 @@ thread_local std::string t_server_err = "no error";
 struct Request {
   lfsr_params prm{};
   std::vector<float> blur, disp, views, x0;   // owned copies until admission
+  std::vector<float> proj_err;                // (paper weights, optional)
   std::vector<int32_t> view_list;             // the listed subset of the grid, if any
   int64_t bytes = 0;                          // state bytes (estimate, budgeted)
   int state = LFSR_REQ_QUEUED;
@@ -64,12 +65,6 @@ int sfail(lfsr_server* s, int code, const std::string& msg) {
   return code;
 }
 
-bool same_solver(const lfsr_params& a, const lfsr_params& c) {
-  return a.lambda1 == c.lambda1 && a.lambda2 == c.lambda2 && a.mu == c.mu &&
-         a.nltv_window == c.nltv_window && a.nltv_patch == c.nltv_patch && a.nltv_h == c.nltv_h &&
-         a.cg_iters == c.cg_iters && a.cg_tol == c.cg_tol && a.precision == c.precision;
-}
-
 bool dry(const lfsr_server* s) { return (s->cfg.flags & LFSR_SERVER_DRY_RUN) != 0; }
 
 // Frees a request's device state (its slot and budget).
@@ -104,6 +99,7 @@ int admit(lfsr_server* s) {
       p.blur = r.blur.data();
       p.disparity = r.disp.data();
       p.views = r.view_list.empty() ? nullptr : r.view_list.data();
+      p.proj_err = r.proj_err.empty() ? nullptr : r.proj_err.data();
       lfsr_handle* h = nullptr;
       int rc = lfsr_create(&p, s->stream, &h);
       if (rc == LFSR_OK && (!h->op.fast || !h->nlf)) rc = LFSR_EUNSUPPORTED;
@@ -180,7 +176,7 @@ int lfsr_server_submit(lfsr_server* s, const lfsr_params* params, const float* l
   if (s->have_solver && !same_solver(s->solver, *params))
     return sfail(s, LFSR_EINVAL,
                  "requests must share lambda1, lambda2, mu, the NLTV window, patch and h, "
-                 "cg_iters, cg_tol and precision");
+                 "cg_iters, cg_tol, precision and the weight scheme with its sigmas");
   if (!s->have_solver) {
     s->solver = *params;
     s->have_solver = true;
@@ -192,11 +188,14 @@ int lfsr_server_submit(lfsr_server* s, const lfsr_params* params, const float* l
   if (params->views) r.view_list.assign(params->views, params->views + params->n_views);
   r.blur.assign(params->blur, params->blur + (size_t)params->kb * params->kb);
   r.disp.assign(params->disparity, params->disparity + (size_t)(Hh * Wh));
+  if (params->weights == LFSR_WEIGHTS_PAPER && params->proj_err)
+    r.proj_err.assign(params->proj_err, params->proj_err + (size_t)(Hh * Wh));
   r.views.assign(lr_views, lr_views + (size_t)(sk * params->H * params->W));
   r.x0.assign(x0, x0 + (size_t)(Hh * Wh));
   r.prm.blur = nullptr;
   r.prm.disparity = nullptr;
   r.prm.views = nullptr;
+  r.prm.proj_err = nullptr;
   r.bytes = est;
   *id = s->next_id++;
   s->reqs.emplace(*id, std::move(r));

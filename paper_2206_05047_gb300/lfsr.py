@@ -29,6 +29,9 @@ LFSR_BF16_STORAGE = 2
 LFSR_KEEP_VIEWS_FP32 = 256
 LFSR_FP16_MAX_INV_MU = 8192.0
 LFSR_SERVER_DRY_RUN = 1
+LFSR_WEIGHTS_PATCH = 0
+LFSR_WEIGHTS_PAPER = 1
+WEIGHT_SCHEMES = {"patch": LFSR_WEIGHTS_PATCH, "paper": LFSR_WEIGHTS_PAPER}
 LFSR_REQ_QUEUED, LFSR_REQ_ACTIVE, LFSR_REQ_DONE, LFSR_REQ_FETCHED, LFSR_REQ_FAILED = 0, 1, 2, 3, 4
 # precision names accepted by Solver(precision=...) and the benchmark
 PRECISIONS = {"fp32": LFSR_FP32, "fp16": LFSR_FP16_STORAGE, "bf16": LFSR_BF16_STORAGE,
@@ -58,7 +61,10 @@ class lfsr_params(C.Structure):
                 ("lambda1", C.c_double), ("lambda2", C.c_double), ("mu", C.c_double),
                 ("nltv_window", C.c_int32), ("nltv_patch", C.c_int32), ("nltv_h", C.c_double),
                 ("cg_iters", C.c_int32), ("cg_tol", C.c_double), ("precision", C.c_int32),
-                ("views", C.POINTER(C.c_int32)), ("n_views", C.c_int32)]
+                ("views", C.POINTER(C.c_int32)), ("n_views", C.c_int32),
+                ("weights", C.c_int32), ("sigma_s", C.c_float), ("sigma_e", C.c_float),
+                ("sigma_o1", C.c_float), ("sigma_o2", C.c_float),
+                ("proj_err", C.POINTER(C.c_float))]
 
 
 class lfsr_stats_t(C.Structure):
@@ -196,21 +202,31 @@ def _check(rc: int, handle=None):
 
 def _params(U, V, H, W, scale, blur, disparity, lambda1=2.0, lambda2=4.0, mu=300.0,
             nltv_window=5, nltv_patch=3, nltv_h=0.1, cg_iters=5, cg_tol=0.0,
-            precision=LFSR_FP32, views=None):
+            precision=LFSR_FP32, views=None, weights=LFSR_WEIGHTS_PATCH, sigma_s=0.0,
+            sigma_e=0.0, sigma_o1=0.0, sigma_o2=0.0, proj_err=None):
     """(lfsr_params, arrays it points to: keep them alive while it is used).
-    views: optional grid indices k = v*U + u of the views used (ascending)."""
+    views: optional grid indices k = v*U + u of the views used (ascending).
+    weights: "patch" / "paper" (or the LFSR_WEIGHTS_* value); the sigmas and
+    the optional HR projection error proj_err belong to the paper's
+    weights."""
     blur = np.ascontiguousarray(blur, dtype=np.float32)
     disp = np.ascontiguousarray(disparity, dtype=np.float32)
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
+    if isinstance(weights, str):
+        weights = WEIGHT_SCHEMES[weights]
     vw = None if views is None else np.ascontiguousarray(views, dtype=np.int32)
+    pe = None if proj_err is None else np.ascontiguousarray(proj_err, dtype=np.float32)
+    if pe is not None and pe.size != scale * H * scale * W:
+        raise ValueError("proj_err must hold (scale*H) x (scale*W) values")
     prm = lfsr_params(C.sizeof(lfsr_params), U, V, H, W, scale, blur.shape[0],
                       blur.ctypes.data_as(C.POINTER(C.c_float)),
                       disp.ctypes.data_as(C.POINTER(C.c_float)),
                       lambda1, lambda2, mu, nltv_window, nltv_patch, nltv_h, cg_iters, cg_tol,
                       precision, None if vw is None else vw.ctypes.data_as(C.POINTER(C.c_int32)),
-                      0 if vw is None else len(vw))
-    return prm, (blur, disp, vw)
+                      0 if vw is None else len(vw), weights, sigma_s, sigma_e, sigma_o1,
+                      sigma_o2, None if pe is None else pe.ctypes.data_as(C.POINTER(C.c_float)))
+    return prm, (blur, disp, vw, pe)
 
 
 def _stream(stream):
@@ -225,13 +241,15 @@ def _stream(stream):
 
 def create(U, V, H, W, scale, blur, disparity, lambda1=2.0, lambda2=4.0, mu=300.0,
            nltv_window=5, nltv_patch=3, nltv_h=0.1, cg_iters=5, cg_tol=0.0,
-           precision=LFSR_FP32, stream=None, views=None):
+           precision=LFSR_FP32, stream=None, views=None, weights=LFSR_WEIGHTS_PATCH,
+           sigma_s=0.0, sigma_e=0.0, sigma_o1=0.0, sigma_o2=0.0, proj_err=None):
     """lfsr_create; returns an opaque handle.  stream: torch.cuda.Stream,
     an integer cudaStream_t, or None (the current torch stream if torch has
     CUDA, else the legacy default stream)."""
     lib = load_library()
     prm, keep = _params(U, V, H, W, scale, blur, disparity, lambda1, lambda2, mu, nltv_window,
-                        nltv_patch, nltv_h, cg_iters, cg_tol, precision, views)
+                        nltv_patch, nltv_h, cg_iters, cg_tol, precision, views, weights,
+                        sigma_s, sigma_e, sigma_o1, sigma_o2, proj_err)
     h = C.c_void_p()
     _check(lib.lfsr_create(C.byref(prm), C.c_void_p(_stream(stream)), C.byref(h)))
     del keep
@@ -313,7 +331,7 @@ def stats(handle) -> dict:
 
 def apply_normal_noalloc(U, V, H, W, scale, blur, disparity, d_disparity, xw, p, q,
                          lambda1=1.0, lambda2=4.0, mu=1.0, nltv_window=5, nltv_patch=3,
-                         nltv_h=0.1, stream=None) -> float:
+                         nltv_h=0.1, stream=None, weights=LFSR_WEIGHTS_PATCH) -> float:
     """lfsr_apply_normal_noalloc: q = M p and <p, M p> without a handle and
     without device allocation.  For callers that cannot allocate device
     memory (a host framework owns the device heap, a hard memory cap, or no
@@ -327,6 +345,7 @@ def apply_normal_noalloc(U, V, H, W, scale, blur, disparity, d_disparity, xw, p,
                       blur.ctypes.data_as(C.POINTER(C.c_float)),
                       disp.ctypes.data_as(C.POINTER(C.c_float)),
                       lambda1, lambda2, mu, nltv_window, nltv_patch, nltv_h, 0, 0.0, LFSR_FP32)
+    prm.weights = WEIGHT_SCHEMES[weights] if isinstance(weights, str) else int(weights)
     ptrs = [_ptr(t) for t in (d_disparity, xw, p, q)]
     if any(k != LFSR_MEM_DEVICE for _, k in ptrs):
         raise TypeError("d_disparity, xw, p and q must be CUDA tensors")

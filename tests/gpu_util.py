@@ -42,7 +42,7 @@ class Case:
     GPU solver on the same float32 values."""
 
     def __init__(self, wl, seed=0, blur=None, disparity=None, precision="fp32", views=None,
-                 **overrides):
+                 weights="patch", sigmas=None, proj_err=None, **overrides):
         import torch
         from oracle import oracle as om
         from paper_2206_05047_gb300 import lfsr
@@ -57,13 +57,20 @@ class Case:
                            patch=wl.patch, h=wl.h, cg_iters=wl.cg_iters, cg_tol=0.0)
         self.params.update(overrides)
         p = self.params
+        # the paper's weights: sigmas as float32 (the C ABI's type) on both sides
+        sg = {k: float(np.float32(v)) for k, v in (sigmas or {}).items()}
+        self.proj_err = None if proj_err is None else f32(proj_err)
+        wkw = dict(weights=weights, **sg)
         self.oracle = om.Oracle(wl.U, wl.V, wl.H, wl.W, wl.scale, self.blur.astype(np.float64),
-                                self.disp.astype(np.float64), views=self.views, **p)
+                                self.disp.astype(np.float64), views=self.views,
+                                proj_err=None if proj_err is None
+                                else self.proj_err.astype(np.float64), **wkw, **p)
         self.solver = lfsr.Solver(U=wl.U, V=wl.V, H=wl.H, W=wl.W, scale=wl.scale, blur=self.blur,
                                   disparity=self.disp, lambda1=p["lambda1"], lambda2=p["lambda2"],
                                   mu=p["mu"], nltv_window=p["window"], nltv_patch=p["patch"],
                                   nltv_h=p["h"], cg_iters=p["cg_iters"], cg_tol=p["cg_tol"],
-                                  precision=precision, views=self.views)
+                                  precision=precision, views=self.views,
+                                  proj_err=self.proj_err, **wkw)
         self.h = self.solver.handle
         self.torch = torch
         self.dev = torch.device("cuda:0")

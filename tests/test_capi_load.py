@@ -30,8 +30,9 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     import ctypes as C
     # lfsr_params: 7 int32 + 2 pointers + 3 doubles + 2 int32 + double + int32 + double + int32
-    # + views pointer + int32 (padded)
-    assert C.sizeof(lfsr.lfsr_params) == 128
+    # + views pointer + int32 + weights int32 + 4 floats + proj_err pointer
+    assert C.sizeof(lfsr.lfsr_params) == 152
+    assert lfsr.lfsr_params.weights.offset == 124 and lfsr.lfsr_params.proj_err.offset == 144
     assert C.sizeof(lfsr.lfsr_stats_t) == 4 * 4 + 8 * 2 + 8 * 2 + 8 * 8 + 8 * 8
 
 
@@ -52,7 +53,7 @@ def test_header_constants_match_binding():
         if hasattr(lfsr, name):
             assert float(getattr(lfsr, name)) == float(val), name
     for name in ("LFSR_FP32", "LFSR_FP16_STORAGE", "LFSR_BF16_STORAGE", "LFSR_FP16_MAX_INV_MU",
-                 "LFSR_KEEP_VIEWS_FP32",
+                 "LFSR_KEEP_VIEWS_FP32", "LFSR_WEIGHTS_PATCH", "LFSR_WEIGHTS_PAPER",
                  "LFSR_EINVAL", "LFSR_EUNSUPPORTED", "LFSR_MEM_DEVICE"):
         assert name in defs and hasattr(lfsr, name), name
 
@@ -104,3 +105,32 @@ def test_view_subsets_are_validated_without_gpu():
                                      disparity=np.zeros((64, 64), np.float32),
                                      views=[2, 6, 7, 8, 10, 11, 12, 13, 14, 16, 17, 18, 22])
     assert star < base
+
+
+def test_weight_scheme_is_validated_without_gpu():
+    import numpy as np
+    import pytest
+    blur = np.ones((3, 3), np.float32) / 9
+    disp = np.zeros((16, 16), np.float32)
+    bad = [dict(weights=2), dict(weights=-1), dict(weights="paper", sigma_s=-1.0),
+           dict(weights="paper", sigma_e=float("nan")), dict(weights="paper", sigma_o1=float("inf")),
+           dict(weights="paper", sigma_o2=-0.5),
+           dict(weights="paper", sigma_o2=1.0, proj_err=np.full((16, 16), np.nan, np.float32))]
+    for kw in bad:
+        with pytest.raises(lfsr.LfsrError) as e:
+            lfsr.create(3, 3, 8, 8, 2, blur, disp, **kw)
+        assert e.value.code == lfsr.LFSR_EINVAL, kw
+    with pytest.raises(ValueError):
+        lfsr.create(3, 3, 8, 8, 2, blur, disp, weights="paper", proj_err=np.zeros(5))
+    # the occlusion factor is one more HR float map
+    kw = dict(U=5, V=5, H=32, W=32, scale=2, blur=blur, disparity=np.zeros((64, 64), np.float32))
+    assert (lfsr.estimate_state_bytes(weights="paper", **kw) -
+            lfsr.estimate_state_bytes(**kw)) == 4 * 64 * 64
+    # a batch shares the scheme and its sigmas
+    job = dict(U=3, V=3, H=8, W=8, scale=2, blur=blur, disparity=disp, weights="paper",
+               sigma_s=8.0)
+    for other in (dict(job, weights="patch"), dict(job, sigma_s=4.0)):
+        with pytest.raises(lfsr.LfsrError) as e:
+            lfsr.Batch([job, other])
+        assert e.value.code == lfsr.LFSR_EINVAL
+        assert "weight scheme" in lfsr.batch_last_error(None)
