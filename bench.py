@@ -68,6 +68,10 @@ def args():
                     choices=["fp32", "fp16", "bf16", "fp16-views32", "bf16-views32"],
                     help="storage type of views, duals and NLTV weights (arithmetic is f32); "
                          "-views32 keeps the views in f32")
+    ap.add_argument("--weights", default="patch", choices=["patch", "paper"],
+                    help="regulariser weights of the named workloads: the patch distance "
+                         "exp(-pd/h^2), or the paper's spatial * edge * occlusion weights "
+                         "(Sec. 3.4) at synth.PAPER_SIGMAS")
     return ap.parse_args()
 
 
@@ -183,9 +187,14 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle, as it stands, on the host cores
 # --------------------------------------------------------------------------
-def oracle_rate(prob, iters: int):
+def weight_kwargs(weights: str) -> dict:
+    """Solver / oracle keyword arguments of a weight scheme."""
+    return {} if weights == "patch" else dict(weights="paper", **synth.PAPER_SIGMAS)
+
+
+def oracle_rate(prob, iters: int, weights: str = "patch"):
     from oracle import oracle as om
-    o = om.Oracle.from_problem(prob)
+    o = om.Oracle.from_problem(prob, **weight_kwargs(weights))
     t = time.perf_counter()
     o.admm(prob.y, prob.x0, iters)
     dt = time.perf_counter() - t
@@ -224,7 +233,7 @@ def run_reference(a, wl, n_iter):
         return
     prob = synth.make_problem(wl, seed=1000 * 2)
     from oracle import oracle as om
-    o = om.Oracle.from_problem(prob)
+    o = om.Oracle.from_problem(prob, **weight_kwargs(getattr(a, "weights", "patch")))
     # bounded sample per step: one ADMM iteration of the full workload
     x, wA, wS = prob.x0, None, None
     for _ in range(a.warmup):
@@ -640,7 +649,7 @@ def main():
     x0_d = x0_h.to(dev)
     x_d = torch.empty(wl.HR, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    solver = lfsr.Solver(prob, stream=stream, precision=a.precision)
+    solver = lfsr.Solver(prob, stream=stream, precision=a.precision, **weight_kwargs(a.weights))
     h = solver.handle
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
@@ -740,7 +749,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         iters = 3 if wl.name != "lf5x5_64_x2" else 20
-        rate, dt, cores = oracle_rate(prob, iters)
+        rate, dt, cores = oracle_rate(prob, iters, a.weights)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{iters} ADMM iterations (K = {wl.cg_iters}) of {wl.name} from x0, "
                          f"{dt:.1f} s"}
@@ -752,6 +761,9 @@ def main():
                 "dtype": "f32", "data": "synthetic (seeded textured-plane light field)",
                 "config": workload_config(wl, n_iter, {
                     "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                    "weights": "patch distance exp(-pd/h^2)" if a.weights == "patch" else
+                               "paper (Sec. 3.4): " + ", ".join(
+                                   f"{k}={v:g}" for k, v in synth.PAPER_SIGMAS.items()),
                     "storage": {"fp32": "f32", "fp16": "f16 (views, duals, NLTV weights)",
                                 "bf16": "bf16 (views, duals, NLTV weights)",
                                 "fp16-views32": "f16 (duals, NLTV weights), f32 views",
