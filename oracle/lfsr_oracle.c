@@ -27,6 +27,10 @@
  *  - Algorithm 2 as standard CG on M delta = -v, warm-started at x, run
  *    while pi > tau for at most K steps (the printed signs and loop test
  *    are inverted).
+ *  - Per-view disparity maps (Sec. 4.1): omega_k lives on view k's HR grid
+ *    and W_k gathers at z + theta_k omega_k(z).  The paper's backward warp
+ *    samples at u - theta_k omega_0(u) (its printed formula repeats the
+ *    same symbols on both sides).
  */
 #include "lfsr_oracle.h"
 
@@ -107,14 +111,21 @@ void orc_view_theta(const orc_problem *P, int j, double *tu, double *tv) {
 /* W_k: disparity warp (Sec. 4.1, forward warping function)             */
 /* (W_k x)(i,j) = bilinear sample of x at (i + tv*w(i,j), j + tu*w(i,j)) */
 /* ------------------------------------------------------------------ */
+/* The disparity map W_k samples with: omega_k (disp_views) or the shared
+ * reference map. */
+static const double *warp_map(const orc_problem *P, int k) {
+  return P->disp_views ? P->disp_views + (long)k * HR_H(P) * HR_W(P) : P->disp;
+}
+
 void orc_warp(const orc_problem *P, int k, const double *x, double *out) {
   const int Hh = HR_H(P), Wh = HR_W(P);
+  const double *omk = warp_map(P, k);
   double tu, tv;
   orc_view_theta(P, k, &tu, &tv);
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < Hh; ++i)
     for (int j = 0; j < Wh; ++j) {
-      double om = P->disp[(long)i * Wh + j];
+      double om = omk[(long)i * Wh + j];
       double sy = i + tv * om, sx = j + tu * om;
       double fy0 = floor(sy), fx0 = floor(sx);
       int i0 = (int)fy0, j0 = (int)fx0;
@@ -135,12 +146,13 @@ void orc_warp(const orc_problem *P, int k, const double *x, double *out) {
  * scatter targets overlap). */
 void orc_warp_T(const orc_problem *P, int k, const double *g, double *out) {
   const int Hh = HR_H(P), Wh = HR_W(P);
+  const double *omk = warp_map(P, k);
   double tu, tv;
   orc_view_theta(P, k, &tu, &tv);
   memset(out, 0, sizeof(double) * (size_t)Hh * Wh);
   for (int i = 0; i < Hh; ++i)
     for (int j = 0; j < Wh; ++j) {
-      double om = P->disp[(long)i * Wh + j];
+      double om = omk[(long)i * Wh + j];
       double sy = i + tv * om, sx = j + tu * om;
       double fy0 = floor(sy), fx0 = floor(sx);
       int i0 = (int)fy0, j0 = (int)fx0;
@@ -153,6 +165,33 @@ void orc_warp_T(const orc_problem *P, int k, const double *g, double *out) {
           double wgt = (a ? fy : 1.0 - fy) * (b ? fx : 1.0 - fx);
           out[(long)ii * Wh + jj] += wgt * val;
         }
+    }
+}
+
+/* The paper's backward warp (Sec. 4.1): the reference pixel u is seen in
+ * view k at u - theta_k omega_0(u); (W_k^* g)(u) samples g there with the
+ * bilinear taps of orc_warp, zero outside the image. */
+void orc_warp_bw(const orc_problem *P, int k, const double *g, double *out) {
+  const int Hh = HR_H(P), Wh = HR_W(P);
+  double tu, tv;
+  orc_view_theta(P, k, &tu, &tv);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < Hh; ++i)
+    for (int j = 0; j < Wh; ++j) {
+      double om = P->disp[(long)i * Wh + j];
+      double sy = i - tv * om, sx = j - tu * om;
+      double fy0 = floor(sy), fx0 = floor(sx);
+      int i0 = (int)fy0, j0 = (int)fx0;
+      double fy = sy - fy0, fx = sx - fx0;
+      double acc = 0.0;
+      for (int a = 0; a <= 1; ++a)
+        for (int b = 0; b <= 1; ++b) {
+          int ii = i0 + a, jj = j0 + b;
+          if (ii < 0 || ii >= Hh || jj < 0 || jj >= Wh) continue;
+          double wgt = (a ? fy : 1.0 - fy) * (b ? fx : 1.0 - fx);
+          acc += wgt * g[(long)ii * Wh + jj];
+        }
+      out[(long)i * Wh + j] = acc;
     }
 }
 
@@ -418,12 +457,29 @@ void orc_prox(long n, const double *u, double t, double *z) {
 /* out = sum_k A_k^T g_k.  Views run in parallel (each operator call is
  * serial inside, nested parallelism is off), per-view buffers are summed in
  * view order. */
+/* A_k^* g: the exact adjoint A_k^T g, or with the paper's backward warp
+ * (adjoint == 1) W_k^* B^T D^T g. */
+static void A_star(const orc_problem *P, int k, const double *g, double *out) {
+  if (P->adjoint != 1) {
+    orc_A_T(P, k, g, out);
+    return;
+  }
+  long p = (long)HR_H(P) * HR_W(P);
+  double *t1 = dalloc(p), *t2 = dalloc(p);
+  orc_up(P, g, t1);
+  orc_blur_T(P, t1, t2);
+  orc_warp_bw(P, k, t2, out);
+  free(t1);
+  free(t2);
+}
+
+/* out = sum_k A_k^* g_k (the x-step's transposed data operator). */
 static void sum_AT(const orc_problem *P, const double *g, double *out) {
   const int sk = orc_num_views(P);
   const long p = (long)HR_H(P) * HR_W(P), q = (long)P->H * P->W;
   double *buf = dalloc(p * sk);
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int k = 0; k < sk; ++k) orc_A_T(P, k, g + k * q, buf + k * p);
+  for (int k = 0; k < sk; ++k) A_star(P, k, g + k * q, buf + k * p);
 #pragma omp parallel for schedule(static)
   for (long i = 0; i < p; ++i) {
     double acc = 0.0;
@@ -442,7 +498,9 @@ static void all_A(const orc_problem *P, const double *x, double *out) {
 }
 
 /* M p with M = (lambda2 + mu lambda1^2/2) sum_k A_k^T A_k + mu/2 S^T S,
- * the normal matrix G^T G of the x-step least squares (Sec. 4.2). */
+ * the normal matrix G^T G of the x-step least squares (Sec. 4.2); with the
+ * paper's backward warp A_k^T becomes A_k^* and M is not symmetric where
+ * the disparity varies (CG then runs as printed, on that M). */
 void orc_normal_apply(const orc_problem *P, const double *w, const double *p, double *q) {
   const int sk = orc_num_views(P), sd = orc_num_dirs(P);
   const long np = (long)HR_H(P) * HR_W(P), nq = (long)P->H * P->W;

@@ -41,6 +41,14 @@ typedef struct orc_problem {
   double sigma_s, sigma_e;   /* spatial exp(-|d|^2/s_s), edge exp(-|grad x|^2/s_e) */
   double sigma_o1, sigma_o2; /* occlusion: boundary b, projection error p   */
   const double *proj_err;    /* HR projection error p(u); NULL: p = 0        */
+  /* warps (Sec. 4.1): disp_views (optional, s_k x HR, data order) gives
+   * W_k its own map omega_k on view k's grid (NULL: every W_k uses disp);
+   * adjoint 0: W_k^T is the exact adjoint (scatter); 1: the paper's
+   * backward warp by the reference map, (W_k^* g)(u) = g(u - theta_k
+   * omega_0(u)) sampled bilinearly, which is not W_k's adjoint where the
+   * disparity varies */
+  const double *disp_views;
+  int adjoint;
 } orc_problem;
 
 int    orc_num_threads(void);
@@ -57,12 +65,15 @@ void   orc_view_theta(const orc_problem *P, int j, double *tu, double *tv);
 /* degradation operators (Eq. sr_model_op, Sec. 4.1) and their adjoints */
 void   orc_warp  (const orc_problem *P, int k, const double *x, double *out);
 void   orc_warp_T(const orc_problem *P, int k, const double *g, double *out);
+/* the paper's backward warp W_k^* (used for A_k^* when adjoint == 1) */
+void   orc_warp_bw(const orc_problem *P, int k, const double *g, double *out);
 void   orc_blur  (const orc_problem *P, const double *x, double *out);
 void   orc_blur_T(const orc_problem *P, const double *g, double *out);
 void   orc_down  (const orc_problem *P, const double *x, double *out);
 void   orc_up    (const orc_problem *P, const double *g, double *out);
 void   orc_A     (const orc_problem *P, int k, const double *x, double *out);
 void   orc_A_T   (const orc_problem *P, int k, const double *g, double *out);
+/* A_k's counterpart in the x-step: A_k^T, or W_k^* B^T D^T (adjoint == 1) */
 
 /* weighted non-local TV (Eq. sr_reg, Sec. 4.1 wdg / wdd) */
 void   orc_weights(const orc_problem *P, const double *x, double *w);

@@ -44,7 +44,8 @@ class _Problem(C.Structure):
                 ("views", C.POINTER(C.c_int)),
                 ("weight_scheme", C.c_int), ("sigma_s", C.c_double), ("sigma_e", C.c_double),
                 ("sigma_o1", C.c_double), ("sigma_o2", C.c_double),
-                ("proj_err", C.POINTER(C.c_double))]
+                ("proj_err", C.POINTER(C.c_double)),
+                ("disp_views", C.POINTER(C.c_double)), ("adjoint", C.c_int)]
 
 
 _lib = None
@@ -62,6 +63,7 @@ def _load():
             "orc_dirs": (None, [P, np.ctypeslib.ndpointer(np.int32), np.ctypeslib.ndpointer(np.int32)]),
             "orc_warp": (None, [P, C.c_int, _dp, _dp]),
             "orc_warp_T": (None, [P, C.c_int, _dp, _dp]),
+            "orc_warp_bw": (None, [P, C.c_int, _dp, _dp]),
             "orc_blur": (None, [P, _dp, _dp]),
             "orc_blur_T": (None, [P, _dp, _dp]),
             "orc_down": (None, [P, _dp, _dp]),
@@ -105,7 +107,8 @@ class Oracle:
     def __init__(self, U, V, H, W, zeta, blur, disparity, lambda1=1.0, lambda2=4.0,
                  mu=1.0, window=5, patch=3, h=0.1, cg_iters=5, cg_tol=0.0,
                  freeze_weights=False, views=None, weights="patch", sigma_s=0.0, sigma_e=0.0,
-                 sigma_o1=0.0, sigma_o2=0.0, proj_err=None):
+                 sigma_o1=0.0, sigma_o2=0.0, proj_err=None, disparity_views=None,
+                 adjoint="exact"):
         self._lib = _load()
         self.blur = _f64(blur)
         kb = self.blur.shape[0]
@@ -128,6 +131,13 @@ class Oracle:
         self.proj_err = None if proj_err is None else _f64(proj_err)
         if self.proj_err is not None:
             assert self.proj_err.shape == (zeta * H, zeta * W)
+        # warps (Sec. 4.1): disparity_views = per-view maps omega_k (s_k x HR,
+        # data order; None: the shared map); adjoint "exact" (scatter) or
+        # "backward" (the paper's backward warp by the reference map)
+        assert adjoint in ("exact", "backward")
+        self.disp_views = None if disparity_views is None else _f64(disparity_views)
+        if self.disp_views is not None:
+            assert self.disp_views.shape == (self.s_k, zeta * H, zeta * W)
         self.hr = (zeta * H, zeta * W)
         self.p = zeta * H * zeta * W
         self.q = H * W
@@ -141,7 +151,10 @@ class Oracle:
                            else self.views.ctypes.data_as(C.POINTER(C.c_int)),
                            int(weights == "paper"), sigma_s, sigma_e, sigma_o1, sigma_o2,
                            None if self.proj_err is None
-                           else self.proj_err.ctypes.data_as(C.POINTER(C.c_double)))
+                           else self.proj_err.ctypes.data_as(C.POINTER(C.c_double)),
+                           None if self.disp_views is None
+                           else self.disp_views.ctypes.data_as(C.POINTER(C.c_double)),
+                           int(adjoint == "backward"))
         self.s_d = self._lib.orc_num_dirs(C.byref(self._P))
 
     @classmethod
@@ -186,6 +199,9 @@ class Oracle:
 
     def warp_T(self, k, g):
         out = self._hr(); self._lib.orc_warp_T(self._p, k, _f64(g), out); return out
+
+    def warp_bw(self, k, g):
+        out = self._hr(); self._lib.orc_warp_bw(self._p, k, _f64(g), out); return out
 
     def blur_op(self, x):
         out = self._hr(); self._lib.orc_blur(self._p, _f64(x), out); return out

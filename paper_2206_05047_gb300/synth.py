@@ -326,6 +326,7 @@ class Problem:
     x0: np.ndarray          # HR float64
     gt: np.ndarray          # HR float64
     theta: np.ndarray       # s_k x 2 (tu, tv)
+    planes: Optional[List[_Plane]] = None   # the scene (for per-view disparity maps)
 
 
 def make_problem(wl: Workload, seed: int = 0,
@@ -364,7 +365,25 @@ def make_problem(wl: Workload, seed: int = 0,
     c = wl.s_k // 2 if (wl.U % 2 == 1 and wl.V % 2 == 1) else 0
     x0 = bicubic_upsample(y[c], z)
     return Problem(wl=wl, seed=seed, blur=gaussian_blur_kernel(wl.kb, wl.blur_sigma),
-                   disparity=disp, y=y, x0=x0, gt=gt, theta=theta)
+                   disparity=disp, y=y, x0=x0, gt=gt, theta=theta, planes=planes)
+
+
+def view_disparity_maps(prob: Problem, views=None) -> np.ndarray:
+    """Per-view disparity maps omega_k (Sec. 4.1): the disparity of the front
+    plane seen at each HR grid point of view k, for the views listed (grid
+    indices, ascending; None: all), s_k x HR float64.  At occlusion
+    boundaries they differ from the reference map shifted: a view sees
+    around the front planes."""
+    wl = prob.wl
+    HH, WW = wl.HR
+    Yg, Xg = np.meshgrid(np.arange(HH, dtype=np.float64), np.arange(WW, dtype=np.float64),
+                         indexing="ij")
+    ks = range(wl.s_k) if views is None else [int(k) for k in views]
+    out = np.empty((len(ks), HH, WW))
+    for j, k in enumerate(ks):
+        tu, tv = prob.theta[k]
+        out[j] = _render(prob.planes, Yg, Xg, tu, tv)[1]
+    return out
 
 
 def psnr(x: np.ndarray, ref: np.ndarray) -> float:
