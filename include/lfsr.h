@@ -120,6 +120,27 @@ extern "C" {
 #define LFSR_WEIGHTS_PATCH 0
 #define LFSR_WEIGHTS_PAPER 1
 
+/* Warps (Sec. 4.1).
+ *
+ * Per-view disparity maps (lfsr_params.disparity_views): W_k samples x at
+ * z + theta_k omega_k(z) with omega_k the disparity map of view k on its own
+ * HR grid (the paper associates a map with each perspective); without them
+ * every W_k uses the reference map `disparity`.
+ *
+ * lfsr_params.adjoint selects what the x-step uses for A_k^T:
+ * LFSR_ADJOINT_EXACT (0): the exact adjoint of A_k (W_k^T scatters the
+ *   bilinear taps), so the x-step's matrix is symmetric and CG applies.
+ * LFSR_ADJOINT_BACKWARD_WARP (1): the paper's backward warp W_k^*, which
+ *   samples bilinearly at u - theta_k omega_0(u) with the reference map
+ *   omega_0 = `disparity`.  It equals W_k^T where the disparity is locally
+ *   constant and differs near disparity edges (and with per-view maps); the
+ *   x-step then runs Algorithm 2 on that matrix, as the paper does.
+ *   lfsr_apply_AT applies W_k^* B^T D^T, lfsr_apply_normal the same matrix.
+ * Both options run on the generic operator kernel (not in batches, servers
+ * or lfsr_apply_normal_noalloc: LFSR_EUNSUPPORTED). */
+#define LFSR_ADJOINT_EXACT 0
+#define LFSR_ADJOINT_BACKWARD_WARP 1
+
 /* Problem and solver parameters (copied by lfsr_create).  struct_size must
  * be sizeof(lfsr_params). */
 typedef struct lfsr_params {
@@ -152,6 +173,10 @@ typedef struct lfsr_params {
   const float *proj_err;   /* host, optional: Hh*Wh projection error p of the
                               occlusion factor; NULL: p = 0.  Read by
                               lfsr_create only.                             */
+  const float *disparity_views; /* host, optional: s_k*Hh*Wh per-view maps
+                              omega_k (view k's HR grid, the data's view
+                              order); NULL: W_k uses disparity.  Copied.    */
+  int32_t adjoint;         /* LFSR_ADJOINT_EXACT or LFSR_ADJOINT_BACKWARD_WARP */
 } lfsr_params;
 
 typedef struct lfsr_handle lfsr_handle;
@@ -439,9 +464,9 @@ int lfsr_server_stats(const lfsr_server *s, lfsr_server_stats_t *out);
  * pointers of the current device (Hh*Wh floats each); *pMp (host) receives
  * <p, M p> in float64.  Work is ordered on cuda_stream and the call blocks
  * until it is done.  The message of a failure is readable with
- * lfsr_last_error(NULL).  Only the patch weights are supported here
- * (LFSR_WEIGHTS_PAPER returns LFSR_EUNSUPPORTED: its occlusion factor is
- * state that lfsr_create computes). */
+ * lfsr_last_error(NULL).  Only the patch weights, the shared disparity map
+ * and the exact adjoint are supported here (LFSR_WEIGHTS_PAPER,
+ * disparity_views and LFSR_ADJOINT_BACKWARD_WARP return LFSR_EUNSUPPORTED). */
 #define LFSR_NOALLOC_MAX_TILES 4096
 #define LFSR_NOALLOC_SCRATCH_BYTES (64 * 1024 + 256)
 

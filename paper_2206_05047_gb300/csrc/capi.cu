@@ -55,7 +55,8 @@ void free_all(lfsr_handle* h) {
     cudaEventDestroy(ev.b);
   }
   void* bufs[] = {h->disp, h->y, h->x[0], h->x[1], h->wA[0], h->wA[1], h->wS[0],
-                  h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt, h->cb, h->occ};
+                  h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt, h->cb, h->occ,
+                  h->disp_views, h->hlr};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->partials) cudaFree(h->partials);
@@ -111,6 +112,30 @@ int check_mem(lfsr_handle* h, int mem) {
 // Launch helpers ------------------------------------------------------------
 
 double* part_slot(lfsr_handle* h, int slot) { return h->partials + (size_t)slot * h->max_grid; }
+
+// W_k's disparity maps in a generic-operator launch: the per-view maps
+// omega_k when given (Sec. 4.1), else the shared map.
+void set_warp_maps(const lfsr_handle* h, OpArgs* a) {
+  a->disp = h->disp_views ? h->disp_views : h->disp;
+  a->disp_stride = h->disp_views ? h->p : 0;
+}
+
+// The backward-warp x-step's operator part (a = the OP_NORMAL arguments):
+// h_k = A_k p into the LR buffer, then q += cA sum_k W_k^* B^T D^T h_k with
+// <p, .> and the CG step length.
+cudaError_t bw_normal(lfsr_handle* h, const OpArgs& a, cudaStream_t s) {
+  OpArgs f = a;
+  f.out = h->hlr;
+  f.partials = nullptr;
+  cudaError_t e = op_launch(OP_FWD, h->g, h->op, f, h->grid_op, s);
+  if (e != cudaSuccess) return e;
+  OpArgs b = a;
+  b.src = h->hlr;
+  b.disp = h->disp;
+  b.disp_stride = 0;
+  b.pdot = a.src;
+  return bw_launch(h->g, h->bw, b, s);
+}
 
 // Runs `launch` (one kernel) with profiling events around it when enabled.
 template <class F>
@@ -169,8 +194,8 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
                          &h->jobs_host[(2 * b) * KD_NUM + KD_DATA]);
     OpArgs od{};
     od.src = h->x[b];
-    od.disp = h->disp;
-    od.out = h->R;
+    set_warp_maps(h, &od);
+    od.out = g.adjoint_bw ? h->hlr : h->R;
     od.y = h->y;
     od.wA_old = h->wA[b];
     od.wA_new = h->wA[nb];
@@ -180,9 +205,24 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
     od.units = h->op.n_tiles * g.sk;
     od.partials = part_slot(h, RED_DW_A);
     od.sc = sc;
-    return op_launch(OP_DATA, g, h->op, od, h->grid_op, s);
+    return op_launch(g.adjoint_bw ? OP_DATA_LR : OP_DATA, g, h->op, od, h->grid_op, s);
   });
   if (e != cudaSuccess) return e;
+  if (g.adjoint_bw) {
+    // v += sum_k W_k^* B^T D^T h_k (the paper's backward warp)
+    e = timed(h, s, KD_DATA, [&] {
+      OpArgs ob{};
+      ob.src = h->hlr;
+      ob.disp = h->disp;
+      ob.out = h->R;
+      ob.scale = 1.f;
+      ob.view0 = 0;
+      ob.nviews = g.sk;
+      ob.sc = sc;
+      return bw_launch(g, h->bw, ob, s);
+    });
+    if (e != cudaSuccess) return e;
+  }
   // x-step (Algorithm 2): r = -v, x' = x, pi = <r, r>
   e = timed(h, s, KD_INIT, [&] {
     const TableArgs t = handle_table(h, KD_INIT, b, 0);
@@ -213,7 +253,7 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
                            &h->jobs_host[(2 * b + pb) * KD_NUM + KD_NORMAL]);
       OpArgs on{};
       on.src = h->P[pb];
-      on.disp = h->disp;
+      set_warp_maps(h, &on);
       on.out = h->Q;
       on.scale = g.cA;
       on.view0 = 0;
@@ -222,6 +262,7 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
       on.partials = part_slot(h, RED_OP);
       on.sc = sc;
       on.check_done = 1;
+      if (g.adjoint_bw) return bw_normal(h, on, s);
       return op_launch(OP_NORMAL, g, h->op, on, h->grid_op, s);
     });
     if (e != cudaSuccess) return e;
@@ -232,7 +273,11 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
   return cudaSuccess;
 }
 
-int launches_per_iteration(const lfsr_handle* h) { return 3 + 3 * h->prm.cg_iters; }
+int launches_per_iteration(const lfsr_handle* h) {
+  // the backward warp adds its gather launch to the data block and each CG step
+  const int bw = h->g.adjoint_bw ? 1 : 0;
+  return 3 + bw + (3 + bw) * h->prm.cg_iters;
+}
 
 cudaError_t build_graph(lfsr_handle* h, int first_parity, int n, cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
@@ -314,6 +359,8 @@ int validate(const lfsr_params* pr) {
     return fail(nullptr, LFSR_EINVAL,
                 "precision must be LFSR_FP32, LFSR_FP16_STORAGE or LFSR_BF16_STORAGE, "
                 "optionally | LFSR_KEEP_VIEWS_FP32");
+  if (pr->adjoint != LFSR_ADJOINT_EXACT && pr->adjoint != LFSR_ADJOINT_BACKWARD_WARP)
+    return fail(nullptr, LFSR_EINVAL, "adjoint must be LFSR_ADJOINT_EXACT or LFSR_ADJOINT_BACKWARD_WARP");
   if (pr->weights != LFSR_WEIGHTS_PATCH && pr->weights != LFSR_WEIGHTS_PAPER)
     return fail(nullptr, LFSR_EINVAL, "weights must be LFSR_WEIGHTS_PATCH or LFSR_WEIGHTS_PAPER");
   if (pr->weights == LFSR_WEIGHTS_PAPER) {
@@ -393,6 +440,8 @@ int64_t lfsr::estimate_state_bytes(const lfsr_params* pr) {
               + 4 * 4 * p;       // P ping-pong, R, Q
   if (nlf) b += es * sh * p + 4 * sh * p;   // stored weights, divergence terms
   if (paper) b += 4 * p;                    // occlusion factor
+  if (pr->disparity_views) b += 4 * sk * p;  // per-view disparity maps
+  if (pr->adjoint == LFSR_ADJOINT_BACKWARD_WARP) b += 4 * nA;   // LR buffer
   const int64_t nl_tiles = ((Hh + 31) / 32) * ((Wh + 31) / 32);
   b += (int64_t)RED_NUM * 8 * (nl_tiles > 4096 ? nl_tiles : 4096);   // reduction slots (bound)
   b += 2 * (int64_t)sizeof(DevScalars) + (4 * KD_NUM + 4) * (int64_t)sizeof(JobArgs) +
@@ -506,6 +555,9 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
     return fail(nullptr, LFSR_EINVAL, "blur or disparity has non-finite values");
   if (pr->weights == LFSR_WEIGHTS_PAPER && pr->proj_err && !finite_all(pr->proj_err, p))
     return fail(nullptr, LFSR_EINVAL, "proj_err has non-finite values");
+  const size_t n_views = pr->views ? (size_t)pr->n_views : (size_t)pr->U * pr->V;
+  if (pr->disparity_views && !finite_all(pr->disparity_views, n_views * p))
+    return fail(nullptr, LFSR_EINVAL, "disparity_views has non-finite values");
 
   lfsr_handle* h = new (std::nothrow) lfsr_handle();
   if (!h) return fail(nullptr, LFSR_ENOMEM, "host allocation failed");
@@ -514,6 +566,7 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   h->prm.disparity = nullptr;
   h->prm.views = nullptr;
   h->prm.proj_err = nullptr;
+  h->prm.disparity_views = nullptr;
   if (pr->views) h->views.assign(pr->views, pr->views + pr->n_views);
   h->stream = (cudaStream_t)cuda_stream;
   Geom& g = h->g;
@@ -533,6 +586,15 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   for (size_t i = 0; i < p; ++i) max_disp = std::fmax(max_disp, std::fabs((double)pr->disparity[i]));
   const double max_theta = 0.5 * (double)((pr->U > pr->V ? pr->U : pr->V) - 1);
   g.S = (int)std::ceil(max_disp * max_theta);
+  g.warp_views = pr->disparity_views ? 1 : 0;
+  g.adjoint_bw = pr->adjoint == LFSR_ADJOINT_BACKWARD_WARP ? 1 : 0;
+  if (pr->disparity_views) {
+    // W_k reads omega_k: the shift bound covers every per-view map too
+    double mv = 0.0;
+    for (size_t i = 0; i < n_views * p; ++i) mv = std::fmax(mv, std::fabs((double)pr->disparity_views[i]));
+    const int sv = (int)std::ceil(mv * max_theta);
+    if (sv > g.S) g.S = sv;
+  }
   // angular offsets of the views of the data (the grid, or the listed subset)
   for (int j = 0; j < g.sk; ++j) {
     const int k = pr->views ? pr->views[j] : j;
@@ -593,6 +655,7 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   }
   e = op_prepare(g, optin);
   if (e == cudaSuccess) e = nl_prepare(optin);
+  if (e == cudaSuccess && g.adjoint_bw) e = bw_prepare(optin);
   if (e != cudaSuccess) {
     rc = cuda_fail(nullptr, e, "kernel attributes");
     delete h;
@@ -608,6 +671,11 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   if (nl_plan(g, &h->nl, smem_limit) != cudaSuccess) {
     delete h;
     return fail(nullptr, LFSR_EUNSUPPORTED, "NLTV window / patch too large");
+  }
+  if (g.adjoint_bw && bw_plan(g, &h->bw, smem_limit) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, LFSR_EUNSUPPORTED,
+                "disparity * angular offset too large for the backward-warp tile");
   }
   h->op_units = h->op.n_tiles * ((g.sk + FAST_VIEWS - 1) / FAST_VIEWS);
   h->grid_op = op_grid(h->op, h->op.fast ? h->op_units : h->op.n_tiles * g.sk, h->sm_count);
@@ -628,6 +696,7 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   if (h->nl_units > h->max_grid) h->max_grid = h->nl_units;
   if (h->grid_vec > h->max_grid) h->max_grid = h->grid_vec;
   if (h->vec_units > h->max_grid) h->max_grid = h->vec_units;
+  if (g.adjoint_bw && h->bw.n_tiles > h->max_grid) h->max_grid = h->bw.n_tiles;
   h->io_floats = h->nA > h->nS ? h->nA : h->nS;
   if (h->io_floats < p) h->io_floats = p;
 
@@ -646,6 +715,8 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   if (e == cudaSuccess && h->nlf) e = dalloc_st(h, &h->wt, (size_t)g.sh * p, h->esize);
   if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->cb, (size_t)g.sh * p);
   if (e == cudaSuccess && g.wscheme == WS_PAPER) e = dalloc(h, &h->occ, p);
+  if (e == cudaSuccess && g.warp_views) e = dalloc(h, &h->disp_views, (size_t)g.sk * p);
+  if (e == cudaSuccess && g.adjoint_bw) e = dalloc(h, &h->hlr, h->nA);
   if (e == cudaSuccess) e = dalloc(h, &h->partials, (size_t)RED_NUM * h->max_grid);
   if (e == cudaSuccess) e = dalloc(h, &h->sc, 2);
   if (e == cudaSuccess) e = dalloc(h, &h->theta, (size_t)g.sk);
@@ -668,6 +739,9 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
                         cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->disp, pr->disparity, p * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && g.warp_views)
+    e = cudaMemcpyAsync(h->disp_views, pr->disparity_views, (size_t)g.sk * p * sizeof(float),
+                        cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess && g.wscheme == WS_PAPER) {
     // occlusion factor of the disparity map and the projection error (R
     // holds the projection error until the first load)
@@ -912,7 +986,7 @@ int lfsr_apply_A(lfsr_handle* h, int view, const float* x, float* out, int mem) 
   } else {
     OpArgs a{};
     a.src = xs;
-    a.disp = h->disp;
+    set_warp_maps(h, &a);
     a.out = os - (size_t)(view < 0 ? 0 : view) * h->q;  // kernel indexes out by view
     a.view0 = view < 0 ? 0 : view;
     a.nviews = nv;
@@ -957,15 +1031,22 @@ int lfsr_apply_AT(lfsr_handle* h, int view, const float* gin, float* out, int me
   } else {
     OpArgs a{};
     a.src = gs - (size_t)(view < 0 ? 0 : view) * h->q;
-    a.disp = h->disp;
+    set_warp_maps(h, &a);
     a.out = os;
     a.scale = 1.f;
     a.view0 = view < 0 ? 0 : view;
     a.nviews = nv;
     a.units = h->op.n_tiles * nv;
     a.sc = h->sc + 1;
-    CK(h, op_launch(OP_ADJ, h->g, h->op, a, op_grid(h->op, a.units, h->sm_count), h->stream),
-       "apply A^T");
+    if (h->g.adjoint_bw) {
+      // the solver's A_k^*: the backward warp by the reference map
+      a.disp = h->disp;
+      a.disp_stride = 0;
+      CK(h, bw_launch(h->g, h->bw, a, h->stream), "apply A^*");
+    } else {
+      CK(h, op_launch(OP_ADJ, h->g, h->op, a, op_grid(h->op, a.units, h->sm_count), h->stream),
+         "apply A^T");
+    }
   }
   if (mem == LFSR_MEM_HOST) CK(h, from_dev(h, out, h->Q, h->p, mem), "download");
   CK(h, cudaStreamSynchronize(h->stream), "synchronize");
@@ -1069,7 +1150,7 @@ int lfsr_apply_normal(lfsr_handle* h, const float* xw, const float* p, float* qo
   } else {
     OpArgs on{};
     on.src = ps;
-    on.disp = h->disp;
+    set_warp_maps(h, &on);
     on.out = qs;
     on.scale = h->g.cA;
     on.view0 = 0;
@@ -1077,7 +1158,11 @@ int lfsr_apply_normal(lfsr_handle* h, const float* xw, const float* p, float* qo
     on.units = h->op.n_tiles * h->g.sk;
     on.partials = part_slot(h, RED_OP);
     on.sc = sc;
-    CK(h, op_launch(OP_NORMAL, h->g, h->op, on, h->grid_op, h->stream), "normal (operator part)");
+    if (h->g.adjoint_bw) {
+      CK(h, bw_normal(h, on, h->stream), "normal (operator part)");
+    } else {
+      CK(h, op_launch(OP_NORMAL, h->g, h->op, on, h->grid_op, h->stream), "normal (operator part)");
+    }
   }
   if (mem == LFSR_MEM_HOST) CK(h, from_dev(h, qo, qs, h->p, mem), "download q");
   DevScalars hs;

@@ -37,6 +37,9 @@ struct lfsr_handle {
   // device buffers
   float* disp = nullptr;
   float* occ = nullptr;                // paper weights: occlusion factor o (HR)
+  float* disp_views = nullptr;         // per-view disparity maps omega_k (s_k x p)
+  float* hlr = nullptr;                // backward warp: LR buffer of h_k (s_k x q)
+  lfsr::BwPlan bw{};                   // backward warp: plan of its gather kernel
   float2* theta = nullptr;             // angular offsets of the data's views
   std::vector<int32_t> views;          // the listed subset (empty: the grid)
   float* x[2] = {nullptr, nullptr};

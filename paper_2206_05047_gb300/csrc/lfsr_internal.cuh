@@ -39,6 +39,8 @@ struct Geom {
   int wscheme;           // WS_PATCH or WS_PAPER
   float inv_sig_s;       // paper weights: 1 / sigma_s (0: spatial factor 1)
   float inv_sig_e;       // paper weights: 1 / sigma_e (0: edge factor 1)
+  int warp_views;        // W_k uses per-view disparity maps (generic operator kernel)
+  int adjoint_bw;        // x-step uses the backward warp W_k^* (generic operator kernel)
   float kv[LFSR_MAX_KB], kh[LFSR_MAX_KB];
   float k2[LFSR_MAX_KB * LFSR_MAX_KB];
   float tu[LFSR_MAX_VIEWS], tv[LFSR_MAX_VIEWS];
@@ -65,7 +67,9 @@ struct DevScalars {
 enum { RED_NLTV = 0, RED_OP = 1, RED_PI = 2, RED_DW_A = 3, RED_DW_S = 4, RED_NUM = 5 };
 
 // Operator-kernel modes.
-enum { OP_NORMAL = 0, OP_DATA = 1, OP_FWD = 2, OP_ADJ = 3 };
+// OP_DATA_LR: the data block's per-LR-pixel step, its result h_k stored to
+// an LR buffer (the backward-warp x-step applies its adjoint separately).
+enum { OP_NORMAL = 0, OP_DATA = 1, OP_FWD = 2, OP_ADJ = 3, OP_DATA_LR = 4 };
 // NLTV-kernel modes.
 enum { NL_BLOCK = 0, NL_APPLY = 1, NL_WEIGHTS = 2 };
 
@@ -86,7 +90,9 @@ struct OpPlan {
 
 struct OpArgs {
   const float* src;      // HR source (x or p) for FWD/NORMAL/DATA; LR g for ADJ
-  const float* disp;     // HR disparity
+  const float* disp;     // HR disparity (view 0's map when disp_stride != 0)
+  size_t disp_stride;    // floats between the per-view maps of W_k (0: one shared map)
+  const float* pdot;     // backward-warp adjoint: <pdot, result> reduced and alpha formed
   float* out;            // HR accumulator target (atomics) or LR output (FWD)
   const void* y;         // DATA: LR views (storage kind g.st_y)
   const void* wA_old;    // DATA: data duals (read, g.st)
@@ -209,6 +215,23 @@ cudaError_t cg_init_nltv_launch(const Geom& g, const TableArgs& t, cudaStream_t 
 cudaError_t nlw2p_launch(int block, const Geom& g, const TableArgs& t, cudaStream_t s);
 cudaError_t occlusion_launch(int Hh, int Wh, const float* disp, const float* pe, float inv2_o1,
                              float inv2_o2, float* occ, cudaStream_t s);
+
+// The paper's backward warp (Sec. 4.1) in the x-step: out += scale sum_k
+// W_k^* B^T D^T g_k with g the LR buffer a.src (s_k x q), gathered at
+// u - theta_k omega_0(u) (a.disp); one CTA per 32 x 32 tile over all views,
+// no atomics.  With a.pdot, also <pdot, sum_k ...> into RED_OP and the CG
+// step length (as OP_NORMAL).
+struct BwPlan {
+  int tiles_x, tiles_y, n_tiles;
+  int NEr, NEc;          // adjoint-blurred region: tile + 2 (S + 1)
+  int NLr, NLc;          // LR pixels whose blur touches it
+  int off_G, off_H, off_T;
+  size_t smem_bytes;
+};
+constexpr int BW_TILE = 32;
+cudaError_t bw_plan(const Geom& g, BwPlan* plan, int smem_limit);
+cudaError_t bw_prepare(int smem_optin);
+cudaError_t bw_launch(const Geom& g, const BwPlan& plan, const OpArgs& a, cudaStream_t s);
 
 // Specialised operator kernel for separable kernels of common (zeta, kb).
 bool fast_supported(const Geom& g);

@@ -111,6 +111,10 @@ extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_d
   if (pr->weights != LFSR_WEIGHTS_PATCH)
     return nfail(pr->weights == LFSR_WEIGHTS_PAPER ? LFSR_EUNSUPPORTED : LFSR_EINVAL,
                  "the no-allocation entry point takes the patch weights only");
+  if (pr->disparity_views || pr->adjoint != LFSR_ADJOINT_EXACT)
+    return nfail(pr->adjoint == LFSR_ADJOINT_BACKWARD_WARP || pr->disparity_views
+                     ? LFSR_EUNSUPPORTED : LFSR_EINVAL,
+                 "the no-allocation entry point takes one disparity map and the exact adjoint");
   const long long Hh = (long long)pr->scale * pr->H, Wh = (long long)pr->scale * pr->W;
   // the NLTV kernel runs one CTA per 32 x 32 HR tile; its partials must fit
   const long long nl_tiles = ((Hh + 31) / 32) * ((Wh + 31) / 32);

@@ -46,7 +46,7 @@ static cudaError_t fast_launch_zk(int mode, const Geom& g, const OpPlan& P, cons
 }
 
 bool fast_supported(const Geom& g) {
-  if (!g.separable) return false;
+  if (!g.separable || g.warp_views || g.adjoint_bw) return false;
 #define X(z, k) if (g.zeta == z && g.kb == k) return true;
   LFSR_FAST_CASES(X)
 #undef X

@@ -7,6 +7,11 @@
 //              update of the data rows, v += A_k^T (l2 r_k + mu/2 l1 f_k)
 //   OP_FWD     out_k = A_k x
 //   OP_ADJ     out += A_k^T g_k
+//   OP_DATA_LR the data block's steps 1-3, h_k stored to the LR buffer out
+//              (the backward-warp x-step adds its adjoint in op_bw.cu)
+//
+// W_k reads view k's own disparity map when a.disp_stride != 0 (per-view
+// maps, Sec. 4.1), else the shared map.
 //
 // One CTA runs a contiguous range of (tile, view) work units of a
 // persistent grid.  For a tile R of HR pixels it stages the source image
@@ -80,14 +85,15 @@ k_operator(const Geom g, const OpPlan P, const OpArgs a) {
   int p_r0 = 0, p_c0 = 0;
   int a_r0 = 0, a_c0 = 0, NAr = 0, NAc = 0;
 
-  if (MODE != OP_FWD)
+  constexpr bool ACC = MODE != OP_FWD && MODE != OP_DATA_LR;   // HR accumulator in use
+  if (ACC)
     for (int idx = tid; idx < P.NAr * P.NAc; idx += OP_THREADS) sA[idx] = 0.f;
 
   for (int u = u_begin; u < u_end; ++u) {
     const int tile = u / a.nviews;
     const int k = a.view0 + (u - tile * a.nviews);
     if (tile != cur_tile) {
-      if (cur_tile >= 0 && MODE != OP_FWD) {
+      if (cur_tile >= 0 && ACC) {
         // flush the accumulator of the previous tile
         __syncthreads();
         for (int ar = warp; ar < NAr; ar += OP_WARPS) {
@@ -139,6 +145,7 @@ k_operator(const Geom g, const OpPlan P, const OpArgs a) {
     }
 
     const float tu = g.tu[k], tv = g.tv[k];
+    const float* __restrict__ disp_k = a.disp + (size_t)k * a.disp_stride;
     if (MODE != OP_ADJ) {
       // 1. warped samples on the blur support of the touching LR pixels
       for (int er = warp; er < NEr; er += OP_WARPS) {
@@ -148,7 +155,7 @@ k_operator(const Geom g, const OpPlan P, const OpArgs a) {
           const int hj = e_c0 + ec;
           float val = 0.f;
           if (row_in && hj >= 0 && hj < g.Wh) {
-            const float om = __ldg(a.disp + (size_t)hi * g.Wh + hj);
+            const float om = __ldg(disp_k + (size_t)hi * g.Wh + hj);
             val = bilerp_smem(sP, P.NPc, P.NPr, P.NPc, er + S, ec + S, tv * om, tu * om);
           }
           sW[er * P.NEc + ec] = val;
@@ -184,7 +191,7 @@ k_operator(const Geom g, const OpPlan P, const OpArgs a) {
           float h = acc;
           if (MODE == OP_NORMAL) {
             if (owned) part += (double)acc * (double)acc;
-          } else if (MODE == OP_DATA) {
+          } else if (MODE == OP_DATA || MODE == OP_DATA_LR) {
             const size_t gi = (size_t)k * q_lr + (size_t)gr * g.W + gc;
             const float yv = ld_kind(a.y, gi, g.st_y), wa = ld_kind(a.wA_old, gi, g.st);
             const float res = acc - yv;                      // a = A x - b
@@ -196,6 +203,7 @@ k_operator(const Geom g, const OpPlan P, const OpArgs a) {
               st_kind(a.wA_new, gi, g.st, wn);
               const double dd = (double)wn - (double)wa;
               part += dd * dd;
+              if (MODE == OP_DATA_LR) a.out[gi] = h;
             }
           } else if (MODE == OP_FWD) {
             if (owned) a.out[(size_t)k * q_lr + (size_t)gr * g.W + gc] = acc;
@@ -209,7 +217,7 @@ k_operator(const Geom g, const OpPlan P, const OpArgs a) {
               __ldg(a.src + (size_t)k * q_lr + (size_t)(lr_lo + lr) * g.W + (lc_lo + lc));
     }
     __syncthreads();
-    if (MODE == OP_FWD) continue;
+    if (!ACC) continue;
 
     // 4. adjoint blur of the zero-filled LR values onto the tile
     if (g.separable) {
@@ -245,14 +253,14 @@ k_operator(const Geom g, const OpPlan P, const OpArgs a) {
               t = fmaf(g.k2[(hi - Z * l + r) * kb + (hj - Z * m + r)],
                        sG[(l - lr_lo) * P.NLc + (m - lc_lo)], t);
         }
-        const float om = __ldg(a.disp + (size_t)hi * g.Wh + hj);
+        const float om = __ldg(disp_k + (size_t)hi * g.Wh + hj);
         scatter_smem(sA, P.NAc, P.NAr, P.NAc, i + S, j + S, tv * om, tu * om, t);
       }
     }
     __syncthreads();
   }
 
-  if (MODE != OP_FWD && cur_tile >= 0) {
+  if (ACC && cur_tile >= 0) {
     __syncthreads();
     for (int ar = warp; ar < NAr; ar += OP_WARPS) {
       const int hi = a_r0 + ar;
@@ -266,7 +274,7 @@ k_operator(const Geom g, const OpPlan P, const OpArgs a) {
     }
   }
 
-  if (MODE == OP_NORMAL || MODE == OP_DATA) {
+  if (MODE == OP_NORMAL || MODE == OP_DATA || MODE == OP_DATA_LR) {
     const int slot = (MODE == OP_NORMAL) ? RED_OP : RED_DW_A;
     double total = 0.0;
     if (grid_sum_last<OP_THREADS>(part, a.partials, &a.sc->counter[slot], &total) &&
@@ -333,6 +341,7 @@ static cudaError_t op_prepare_z(int optin) {
   if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator<OP_DATA, Z>, optin);
   if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator<OP_FWD, Z>, optin);
   if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator<OP_ADJ, Z>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(k_operator<OP_DATA_LR, Z>, optin);
   return e;
 }
 
@@ -371,6 +380,7 @@ cudaError_t op_launch(int mode, const Geom& g, const OpPlan& P, const OpArgs& a,
     case OP_DATA: return op_launch_m<OP_DATA>(g, P, a, grid, s);
     case OP_FWD: return op_launch_m<OP_FWD>(g, P, a, grid, s);
     case OP_ADJ: return op_launch_m<OP_ADJ>(g, P, a, grid, s);
+    case OP_DATA_LR: return op_launch_m<OP_DATA_LR>(g, P, a, grid, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -32,6 +32,9 @@ LFSR_SERVER_DRY_RUN = 1
 LFSR_WEIGHTS_PATCH = 0
 LFSR_WEIGHTS_PAPER = 1
 WEIGHT_SCHEMES = {"patch": LFSR_WEIGHTS_PATCH, "paper": LFSR_WEIGHTS_PAPER}
+LFSR_ADJOINT_EXACT = 0
+LFSR_ADJOINT_BACKWARD_WARP = 1
+ADJOINTS = {"exact": LFSR_ADJOINT_EXACT, "backward": LFSR_ADJOINT_BACKWARD_WARP}
 LFSR_REQ_QUEUED, LFSR_REQ_ACTIVE, LFSR_REQ_DONE, LFSR_REQ_FETCHED, LFSR_REQ_FAILED = 0, 1, 2, 3, 4
 # precision names accepted by Solver(precision=...) and the benchmark
 PRECISIONS = {"fp32": LFSR_FP32, "fp16": LFSR_FP16_STORAGE, "bf16": LFSR_BF16_STORAGE,
@@ -64,7 +67,8 @@ class lfsr_params(C.Structure):
                 ("views", C.POINTER(C.c_int32)), ("n_views", C.c_int32),
                 ("weights", C.c_int32), ("sigma_s", C.c_float), ("sigma_e", C.c_float),
                 ("sigma_o1", C.c_float), ("sigma_o2", C.c_float),
-                ("proj_err", C.POINTER(C.c_float))]
+                ("proj_err", C.POINTER(C.c_float)),
+                ("disparity_views", C.POINTER(C.c_float)), ("adjoint", C.c_int32)]
 
 
 class lfsr_stats_t(C.Structure):
@@ -203,18 +207,27 @@ def _check(rc: int, handle=None):
 def _params(U, V, H, W, scale, blur, disparity, lambda1=2.0, lambda2=4.0, mu=300.0,
             nltv_window=5, nltv_patch=3, nltv_h=0.1, cg_iters=5, cg_tol=0.0,
             precision=LFSR_FP32, views=None, weights=LFSR_WEIGHTS_PATCH, sigma_s=0.0,
-            sigma_e=0.0, sigma_o1=0.0, sigma_o2=0.0, proj_err=None):
+            sigma_e=0.0, sigma_o1=0.0, sigma_o2=0.0, proj_err=None, disparity_views=None,
+            adjoint=LFSR_ADJOINT_EXACT):
     """(lfsr_params, arrays it points to: keep them alive while it is used).
     views: optional grid indices k = v*U + u of the views used (ascending).
     weights: "patch" / "paper" (or the LFSR_WEIGHTS_* value); the sigmas and
     the optional HR projection error proj_err belong to the paper's
-    weights."""
+    weights.  disparity_views: optional per-view maps (s_k x HR); adjoint:
+    "exact" / "backward" (or the LFSR_ADJOINT_* value)."""
     blur = np.ascontiguousarray(blur, dtype=np.float32)
     disp = np.ascontiguousarray(disparity, dtype=np.float32)
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     if isinstance(weights, str):
         weights = WEIGHT_SCHEMES[weights]
+    if isinstance(adjoint, str):
+        adjoint = ADJOINTS[adjoint]
+    s_k = U * V if views is None else len(views)
+    dv = None if disparity_views is None else np.ascontiguousarray(disparity_views,
+                                                                   dtype=np.float32)
+    if dv is not None and dv.size != s_k * scale * H * scale * W:
+        raise ValueError("disparity_views must hold s_k x (scale*H) x (scale*W) values")
     vw = None if views is None else np.ascontiguousarray(views, dtype=np.int32)
     pe = None if proj_err is None else np.ascontiguousarray(proj_err, dtype=np.float32)
     if pe is not None and pe.size != scale * H * scale * W:
@@ -225,8 +238,9 @@ def _params(U, V, H, W, scale, blur, disparity, lambda1=2.0, lambda2=4.0, mu=300
                       lambda1, lambda2, mu, nltv_window, nltv_patch, nltv_h, cg_iters, cg_tol,
                       precision, None if vw is None else vw.ctypes.data_as(C.POINTER(C.c_int32)),
                       0 if vw is None else len(vw), weights, sigma_s, sigma_e, sigma_o1,
-                      sigma_o2, None if pe is None else pe.ctypes.data_as(C.POINTER(C.c_float)))
-    return prm, (blur, disp, vw, pe)
+                      sigma_o2, None if pe is None else pe.ctypes.data_as(C.POINTER(C.c_float)),
+                      None if dv is None else dv.ctypes.data_as(C.POINTER(C.c_float)), adjoint)
+    return prm, (blur, disp, vw, pe, dv)
 
 
 def _stream(stream):
@@ -242,14 +256,15 @@ def _stream(stream):
 def create(U, V, H, W, scale, blur, disparity, lambda1=2.0, lambda2=4.0, mu=300.0,
            nltv_window=5, nltv_patch=3, nltv_h=0.1, cg_iters=5, cg_tol=0.0,
            precision=LFSR_FP32, stream=None, views=None, weights=LFSR_WEIGHTS_PATCH,
-           sigma_s=0.0, sigma_e=0.0, sigma_o1=0.0, sigma_o2=0.0, proj_err=None):
+           sigma_s=0.0, sigma_e=0.0, sigma_o1=0.0, sigma_o2=0.0, proj_err=None,
+           disparity_views=None, adjoint=LFSR_ADJOINT_EXACT):
     """lfsr_create; returns an opaque handle.  stream: torch.cuda.Stream,
     an integer cudaStream_t, or None (the current torch stream if torch has
     CUDA, else the legacy default stream)."""
     lib = load_library()
     prm, keep = _params(U, V, H, W, scale, blur, disparity, lambda1, lambda2, mu, nltv_window,
                         nltv_patch, nltv_h, cg_iters, cg_tol, precision, views, weights,
-                        sigma_s, sigma_e, sigma_o1, sigma_o2, proj_err)
+                        sigma_s, sigma_e, sigma_o1, sigma_o2, proj_err, disparity_views, adjoint)
     h = C.c_void_p()
     _check(lib.lfsr_create(C.byref(prm), C.c_void_p(_stream(stream)), C.byref(h)))
     del keep

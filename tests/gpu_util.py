@@ -42,7 +42,8 @@ class Case:
     GPU solver on the same float32 values."""
 
     def __init__(self, wl, seed=0, blur=None, disparity=None, precision="fp32", views=None,
-                 weights="patch", sigmas=None, proj_err=None, **overrides):
+                 weights="patch", sigmas=None, proj_err=None, disparity_views=None,
+                 adjoint="exact", **overrides):
         import torch
         from oracle import oracle as om
         from paper_2206_05047_gb300 import lfsr
@@ -60,17 +61,21 @@ class Case:
         # the paper's weights: sigmas as float32 (the C ABI's type) on both sides
         sg = {k: float(np.float32(v)) for k, v in (sigmas or {}).items()}
         self.proj_err = None if proj_err is None else f32(proj_err)
-        wkw = dict(weights=weights, **sg)
+        self.disp_views = None if disparity_views is None else f32(disparity_views)
+        wkw = dict(weights=weights, adjoint=adjoint, **sg)
         self.oracle = om.Oracle(wl.U, wl.V, wl.H, wl.W, wl.scale, self.blur.astype(np.float64),
                                 self.disp.astype(np.float64), views=self.views,
                                 proj_err=None if proj_err is None
-                                else self.proj_err.astype(np.float64), **wkw, **p)
+                                else self.proj_err.astype(np.float64),
+                                disparity_views=None if disparity_views is None
+                                else self.disp_views.astype(np.float64), **wkw, **p)
         self.solver = lfsr.Solver(U=wl.U, V=wl.V, H=wl.H, W=wl.W, scale=wl.scale, blur=self.blur,
                                   disparity=self.disp, lambda1=p["lambda1"], lambda2=p["lambda2"],
                                   mu=p["mu"], nltv_window=p["window"], nltv_patch=p["patch"],
                                   nltv_h=p["h"], cg_iters=p["cg_iters"], cg_tol=p["cg_tol"],
                                   precision=precision, views=self.views,
-                                  proj_err=self.proj_err, **wkw)
+                                  proj_err=self.proj_err, disparity_views=self.disp_views,
+                                  **wkw)
         self.h = self.solver.handle
         self.torch = torch
         self.dev = torch.device("cuda:0")

@@ -31,8 +31,10 @@ def test_struct_layouts_match_header():
     import ctypes as C
     # lfsr_params: 7 int32 + 2 pointers + 3 doubles + 2 int32 + double + int32 + double + int32
     # + views pointer + int32 + weights int32 + 4 floats + proj_err pointer
-    assert C.sizeof(lfsr.lfsr_params) == 152
+    # + disparity_views pointer + adjoint int32 (padded)
+    assert C.sizeof(lfsr.lfsr_params) == 168
     assert lfsr.lfsr_params.weights.offset == 124 and lfsr.lfsr_params.proj_err.offset == 144
+    assert lfsr.lfsr_params.disparity_views.offset == 152 and lfsr.lfsr_params.adjoint.offset == 160
     assert C.sizeof(lfsr.lfsr_stats_t) == 4 * 4 + 8 * 2 + 8 * 2 + 8 * 8 + 8 * 8
 
 
@@ -54,6 +56,7 @@ def test_header_constants_match_binding():
             assert float(getattr(lfsr, name)) == float(val), name
     for name in ("LFSR_FP32", "LFSR_FP16_STORAGE", "LFSR_BF16_STORAGE", "LFSR_FP16_MAX_INV_MU",
                  "LFSR_KEEP_VIEWS_FP32", "LFSR_WEIGHTS_PATCH", "LFSR_WEIGHTS_PAPER",
+                 "LFSR_ADJOINT_EXACT", "LFSR_ADJOINT_BACKWARD_WARP",
                  "LFSR_EINVAL", "LFSR_EUNSUPPORTED", "LFSR_MEM_DEVICE"):
         assert name in defs and hasattr(lfsr, name), name
 
@@ -134,3 +137,29 @@ def test_weight_scheme_is_validated_without_gpu():
             lfsr.Batch([job, other])
         assert e.value.code == lfsr.LFSR_EINVAL
         assert "weight scheme" in lfsr.batch_last_error(None)
+
+
+def test_warp_options_are_validated_without_gpu():
+    import numpy as np
+    import pytest
+    blur = np.ones((3, 3), np.float32) / 9
+    disp = np.zeros((16, 16), np.float32)
+    for bad in (2, -1):
+        with pytest.raises(lfsr.LfsrError) as e:
+            lfsr.create(3, 3, 8, 8, 2, blur, disp, adjoint=bad)
+        assert e.value.code == lfsr.LFSR_EINVAL
+    maps = np.zeros((9, 16, 16), np.float32)
+    maps[4, 3, 3] = np.inf
+    with pytest.raises(lfsr.LfsrError) as e:
+        lfsr.create(3, 3, 8, 8, 2, blur, disp, disparity_views=maps)
+    assert e.value.code == lfsr.LFSR_EINVAL
+    assert "disparity_views" in lfsr.last_error(None)
+    with pytest.raises(ValueError):
+        lfsr.create(3, 3, 8, 8, 2, blur, disp, disparity_views=np.zeros((8, 16, 16)))
+    # a subset of views takes one map per listed view
+    with pytest.raises(ValueError):
+        lfsr.create(3, 3, 8, 8, 2, blur, disp, views=[1, 4, 7], disparity_views=maps)
+    kw = dict(U=3, V=3, H=8, W=8, scale=2, blur=blur, disparity=disp)
+    base = lfsr.estimate_state_bytes(**kw)
+    assert lfsr.estimate_state_bytes(disparity_views=np.zeros((9, 16, 16)), **kw) - base == 4 * 9 * 256
+    assert lfsr.estimate_state_bytes(adjoint="backward", **kw) - base == 4 * 9 * 64
