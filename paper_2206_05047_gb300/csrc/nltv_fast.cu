@@ -55,6 +55,11 @@ k_nla2(const Geom g, const TableArgs tb) {
   const int ju = lane, uj = j0 + ju;
   const int iu0 = NF_PIX * warp;
   const bool col_in = uj < Wh;
+  // 32-bit offset of the strip's first pixel (p < 2^31); in an interior
+  // tile every owned pixel and its backward neighbours u - d (di <= 0) lie
+  // inside the image, so the loads need no bounds checks
+  const int off0 = (i0 + iu0) * Wh + uj;
+  const bool interior = i0 + T + WR <= Hh && j0 >= WR && j0 + T + WR <= Wh;
   float acc[NF_PIX];
 #pragma unroll
   for (int m = 0; m < NF_PIX; ++m) acc[m] = 0.f;
@@ -69,15 +74,24 @@ k_nla2(const Geom g, const TableArgs tb) {
       const int idx = i0d + e;
       if (idx >= D::SH) break;
       const int di = D::di(idx), dj = D::dj(idx);
-      const ST* wd = wt + (size_t)idx * p;
+      const ST* wd = wt + (size_t)idx * p + off0;   // this direction's plane at the strip
+      const int bo = di * Wh + dj;                  // u - d is bo floats before u
+      if (interior) {
 #pragma unroll
-      for (int m = 0; m < NF_PIX; ++m) {
-        const int ui = i0 + iu0 + m;
-        const int bi = ui - di, bj = uj - dj;
-        const bool in = ui < Hh && col_in;
-        wf[e][m] = in ? B::ld(wd + (size_t)ui * Wh + uj) : typename B::R(0);
-        wb[e][m] = (in && bi < Hh && bj >= 0 && bj < Wh) ? B::ld(wd + (size_t)bi * Wh + bj)
-                                                          : typename B::R(0);
+        for (int m = 0; m < NF_PIX; ++m) {
+          wf[e][m] = B::ld(wd + m * Wh);
+          wb[e][m] = B::ld(wd + (m * Wh - bo));
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < NF_PIX; ++m) {
+          const int ui = i0 + iu0 + m;
+          const int bi = ui - di, bj = uj - dj;
+          const bool in = ui < Hh && col_in;
+          wf[e][m] = in ? B::ld(wd + m * Wh) : typename B::R(0);
+          wb[e][m] = (in && bi < Hh && bj >= 0 && bj < Wh) ? B::ld(wd + (m * Wh - bo))
+                                                            : typename B::R(0);
+        }
       }
     }
 #pragma unroll
@@ -127,17 +141,19 @@ k_cg_init_nltv(const Geom g, const TableArgs tb) {
   // this CTA's chunk of HR pixels: unit blockIdx.x of the table
   const JobArgs* jp = tb.jobs + table_job(tb, blockIdx.x);
   const int Hh = jp->Hh, Wh = jp->Wh;
-  const size_t n = (size_t)Hh * Wh;
+  const int n = Hh * Wh;                      // p < 2^31: 32-bit pixel offsets
   float* __restrict__ rv = jp->out;
   const float* __restrict__ cb = jp->cb;
   const float* __restrict__ x = jp->src;
   float* __restrict__ x_next = jp->x_next;
-  const size_t c0 = (size_t)(blockIdx.x - jp->unit0) * jp->chunk;
-  const size_t c1 = min(n, c0 + (size_t)jp->chunk);
+  const int c0 = (blockIdx.x - jp->unit0) * jp->chunk;
+  const int c1 = min(n, c0 + jp->chunk);
   const float half_mu = 0.5f * g.mu;
   double part = 0.0;
-  for (size_t i = c0 + threadIdx.x; i < c1; i += VEC_THREADS) {
-    const int ui = (int)(i / Wh), uj = (int)(i - (size_t)ui * Wh);
+  for (int i = c0 + threadIdx.x; i < c1; i += VEC_THREADS) {
+    const int ui = i / Wh, uj = i - ui * Wh;
+    // away from the border every backward neighbour u - d is in the image
+    const bool inner = ui + WR < Hh && uj >= WR && uj + WR < Wh;
     float div = 0.f;
     constexpr int DB = 8;
 #pragma unroll
@@ -147,10 +163,11 @@ k_cg_init_nltv(const Geom g, const TableArgs tb) {
       for (int e = 0; e < DB; ++e) {
         const int idx = i0d + e;
         if (idx >= D::SH) break;
-        const float* cd = cb + (size_t)idx * n;
+        const float* cd = cb + (size_t)idx * n + i;
         const int bi = ui - D::di(idx), bj = uj - D::dj(idx);
-        cf[e] = __ldg(cd + i);
-        cbk[e] = (bi < Hh && bj >= 0 && bj < Wh) ? __ldg(cd + (size_t)bi * Wh + bj) : 0.f;
+        const int bo = D::di(idx) * Wh + D::dj(idx);
+        cf[e] = __ldg(cd);
+        cbk[e] = (inner || (bi < Hh && bj >= 0 && bj < Wh)) ? __ldg(cd - bo) : 0.f;
       }
 #pragma unroll
       for (int e = 0; e < DB; ++e)

@@ -45,15 +45,38 @@ k_cg_update(const Geom g, const TableArgs tb) {
   DevScalars* sc = jp->sc;
   double part = 0.0;
   if (!((volatile int*)&sc->cg_done)[0]) {
-    const size_t n = (size_t)jp->Hh * jp->Wh;
+    const int n = jp->Hh * jp->Wh;            // p < 2^31: 32-bit offsets
     const float* __restrict__ p = jp->p_old;
     const float* __restrict__ q = jp->q;
     float* __restrict__ r = jp->rr;
     float* __restrict__ x_next = jp->x_next;
     const float alpha = (float)sc->alpha;
-    const size_t c0 = (size_t)(blockIdx.x - jp->unit0) * jp->chunk;
-    const size_t c1 = min(n, c0 + (size_t)jp->chunk);
-    for (size_t i = c0 + threadIdx.x; i < c1; i += VEC_THREADS) {
+    const int c0 = (blockIdx.x - jp->unit0) * jp->chunk;
+    const int c1 = min(n, c0 + jp->chunk);
+    // chunks are whole multiples of 32 floats and every buffer starts on a
+    // 256-byte boundary: [c0, c1 & ~3) in float4 steps, then the tail
+    const int v0 = c0 >> 2, v1 = c1 >> 2;
+    for (int v = v0 + (int)threadIdx.x; v < v1; v += VEC_THREADS) {
+      const float4 pv = __ldg(reinterpret_cast<const float4*>(p) + v);
+      const float4 qv = __ldg(reinterpret_cast<const float4*>(q) + v);
+      float4 rv = reinterpret_cast<const float4*>(r)[v];
+      float4 xv = reinterpret_cast<const float4*>(x_next)[v];
+      xv.x = fmaf(alpha, pv.x, xv.x);
+      xv.y = fmaf(alpha, pv.y, xv.y);
+      xv.z = fmaf(alpha, pv.z, xv.z);
+      xv.w = fmaf(alpha, pv.w, xv.w);
+      rv.x = fmaf(-alpha, qv.x, rv.x);
+      rv.y = fmaf(-alpha, qv.y, rv.y);
+      rv.z = fmaf(-alpha, qv.z, rv.z);
+      rv.w = fmaf(-alpha, qv.w, rv.w);
+      reinterpret_cast<float4*>(x_next)[v] = xv;
+      reinterpret_cast<float4*>(r)[v] = rv;
+      part += (double)rv.x * (double)rv.x;
+      part += (double)rv.y * (double)rv.y;
+      part += (double)rv.z * (double)rv.z;
+      part += (double)rv.w * (double)rv.w;
+    }
+    for (int i = 4 * v1 + (int)threadIdx.x; i < c1; i += VEC_THREADS) {
       x_next[i] = fmaf(alpha, p[i], x_next[i]);
       const float rn = fmaf(-alpha, q[i], r[i]);
       r[i] = rn;
