@@ -60,7 +60,9 @@ k_nlw2(const Geom g, const TableArgs tb) {
   const float* xs = sX + (iu0 + WR) * NXp + (ju + WR);
   // directions in chunks of DB: the chunk's dual loads are issued first
   constexpr int DB = 3;
-#pragma unroll
+  // the chunk loop stays rolled: fully unrolled, the 24 edges of a 7 x 7
+  // window overflow the instruction cache (warps stalled on fetch)
+#pragma unroll 1
   for (int i0d = 0; i0d < D::SH; i0d += DB) {
     using B = SBits<ST>;
     typename B::R wa_[DB][NF_PIX], wb_[DB][NF_PIX];

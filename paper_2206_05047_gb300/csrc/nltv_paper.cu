@@ -107,7 +107,9 @@ k_nlw2p(const Geom g, const TableArgs tb) {
   const float* gs = sG + (iu0 + WR) * NGp + (ju + WR);   // g(u) of the strip's first pixel
   const float* xs = sX + (iu0 + HX) * NXp + (ju + HX);   // x(u) of the strip's first pixel
   constexpr int DB = 3;
-#pragma unroll
+  // the chunk loop stays rolled: fully unrolled, the 24 edges of a 7 x 7
+  // window overflow the instruction cache (warps stalled on fetch)
+#pragma unroll 1
   for (int i0d = 0; i0d < D::SH; i0d += DB) {
     using B = SBits<ST>;
     typename B::R wa_[DB][NF_PIX], wb_[DB][NF_PIX];
