@@ -59,7 +59,7 @@ extern "C" {
 #define LFSR_EINVAL       (-1)  /* bad size, parameter or pointer            */
 #define LFSR_ENOMEM       (-2)  /* device allocation failed                  */
 #define LFSR_ECUDA        (-3)  /* CUDA runtime error (message has details)  */
-#define LFSR_ENUMERIC     (-4)  /* non-finite or non-positive CG curvature   */
+#define LFSR_ENUMERIC     (-4)  /* non-finite or negative CG curvature       */
 #define LFSR_ETIMEOUT     (-5)  /* a bounded device wait gave up             */
 #define LFSR_EUNSUPPORTED (-6)  /* valid but not implemented on this path    */
 
@@ -211,7 +211,8 @@ int lfsr_create(const lfsr_params *params, void *cuda_stream, lfsr_handle **out)
  * and running the K-step CG x-step of Algorithm 2.  lr_views holds s_k*q
  * floats ([k][i][j]), x0 and x_out p floats.  Blocks until x_out is
  * written.  Returns LFSR_ENUMERIC if the CG curvature became non-finite
- * or non-positive, LFSR_EINVAL if a view value does not fit the storage
+ * or negative (a curvature of exactly 0 ends the x-step: its direction has
+ * vanished), LFSR_EINVAL if a view value does not fit the storage
  * type (16-bit precisions). */
 int lfsr_solve(lfsr_handle *h, const float *lr_views, int iterations,
                const float *x0, float *x_out, int mem_kind);

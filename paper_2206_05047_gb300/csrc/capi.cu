@@ -847,7 +847,7 @@ static int read_status(lfsr_handle* h, DevScalars* hs) {
   if (hs->status == LFSR_EINVAL)
     return fail(h, LFSR_EINVAL, "a view or data-dual value given to the solver is not finite or outside the storage type's range");
   if (hs->status != 0)
-    return fail(h, hs->status, "non-finite or non-positive curvature in the CG x-step");
+    return fail(h, hs->status, "non-finite or negative curvature in the CG x-step");
   return LFSR_OK;
 }
 

@@ -83,6 +83,22 @@ __device__ __forceinline__ void set_status(DevScalars* sc, int code) {
   atomicCAS(&sc->status, 0, code);
 }
 
+// CG step length (Algorithm 2): alpha = pi / <p, M p>.  A curvature of
+// exactly 0 means the direction has vanished below float resolution (the
+// x-step has converged, e.g. a problem of one unknown after its first step)
+// or lies where M is singular: the x-step stops there.  A negative or
+// non-finite curvature is a numeric failure (LFSR_ENUMERIC).
+__device__ __forceinline__ void cg_set_alpha(DevScalars* sc, double pAp) {
+  sc->pAp = pAp;
+  if (pAp > 0.0 && isfinite(pAp)) {
+    sc->alpha = sc->pi / pAp;
+    return;
+  }
+  sc->alpha = 0.0;
+  sc->cg_done = 1;
+  if (!(pAp == 0.0)) set_status(sc, -4);  // LFSR_ENUMERIC
+}
+
 // Floor / ceil division for a possibly negative numerator and positive d.
 __host__ __device__ __forceinline__ int floor_div(int n, int d) {
   return (n >= 0) ? (n / d) : -((-n + d - 1) / d);

@@ -139,15 +139,7 @@ k_adjoint_bw(const Geom g, const BwPlan P, const OpArgs a) {
         threadIdx.x == 0) {
       a.sc->red[RED_OP] = total;
       // alpha = pi / <p, M p>  (Algorithm 2), M with the backward warp
-      const double pAp = (double)g.cA * total + (double)g.mu * a.sc->red[RED_NLTV];
-      a.sc->pAp = pAp;
-      if (!(pAp > 0.0) || !isfinite(pAp)) {
-        set_status(a.sc, -4);  // LFSR_ENUMERIC
-        a.sc->cg_done = 1;
-        a.sc->alpha = 0.0;
-      } else {
-        a.sc->alpha = a.sc->pi / pAp;
-      }
+      cg_set_alpha(a.sc, (double)g.cA * total + (double)g.mu * a.sc->red[RED_NLTV]);
     }
   }
 }

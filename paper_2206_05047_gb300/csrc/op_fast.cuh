@@ -597,15 +597,7 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
       if (lane != 0) continue;
       if (MODE == OP_NORMAL) {
         sc->red[RED_OP] = total;
-        const double pAp = (double)g.cA * total + (double)g.mu * sc->red[RED_NLTV];
-        sc->pAp = pAp;
-        if (!(pAp > 0.0) || !isfinite(pAp)) {
-          set_status(sc, -4);  // LFSR_ENUMERIC
-          sc->cg_done = 1;
-          sc->alpha = 0.0;
-        } else {
-          sc->alpha = sc->pi / pAp;
-        }
+        cg_set_alpha(sc, (double)g.cA * total + (double)g.mu * sc->red[RED_NLTV]);
       } else {
         sc->red[RED_DW_A] = total;
         sc->dwA = total;

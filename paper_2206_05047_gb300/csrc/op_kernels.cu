@@ -282,15 +282,7 @@ k_operator(const Geom g, const OpPlan P, const OpArgs a) {
       a.sc->red[slot] = total;
       if (MODE == OP_NORMAL) {
         // alpha = pi / <p, M p>  (Algorithm 2)
-        const double pAp = (double)g.cA * total + (double)g.mu * a.sc->red[RED_NLTV];
-        a.sc->pAp = pAp;
-        if (!(pAp > 0.0) || !isfinite(pAp)) {
-          set_status(a.sc, -4);  // LFSR_ENUMERIC
-          a.sc->cg_done = 1;
-          a.sc->alpha = 0.0;
-        } else {
-          a.sc->alpha = a.sc->pi / pAp;
-        }
+        cg_set_alpha(a.sc, (double)g.cA * total + (double)g.mu * a.sc->red[RED_NLTV]);
       } else {
         a.sc->dwA = total;
       }

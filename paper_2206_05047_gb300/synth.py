@@ -228,8 +228,9 @@ def _make_scene(wl: Workload, rng: np.random.Generator) -> List[_Plane]:
             planes.append(_Plane(d, "rect", (y0, x0, y0 + h, x0 + w), tex))
         else:
             r = math.sqrt(area / math.pi)
-            cy = rng.uniform(r * 0.5, HH - r * 0.5)
-            cx = rng.uniform(r * 0.5, WW - r * 0.5)
+            # (images thinner than the disc: centred on that axis)
+            cy = rng.uniform(r * 0.5, HH - r * 0.5) if HH > r else 0.5 * HH
+            cx = rng.uniform(r * 0.5, WW - r * 0.5) if WW > r else 0.5 * WW
             planes.append(_Plane(d, "disc", (cy, cx, r), tex))
     return planes
 
