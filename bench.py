@@ -774,6 +774,9 @@ def main():
                 "hbm_roofline": {"frac": hbm_frac,
                                  "alg_bytes_per_iter": alg_bytes_per_iter(wl, esize, esize_y),
                                  "peak_gbs": hbm, "note": hbm_note},
+                # the reference view alone: HR Mpix * ADMM iterations per second
+                "sai_rate": {"value": p * n_iter * a.steps * world / (t_ms / 1e3) / 1e6,
+                             "unit": "HR Mpix*iter/s (reference view)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(a.steps * n_iter * (3 + 3 * wl.cg_iters)),
                 "clocks": clk}
