@@ -412,9 +412,11 @@ int lfsr_server_create(const lfsr_server_config *cfg, void *cuda_stream, lfsr_se
 void lfsr_server_destroy(lfsr_server *s);
 const char *lfsr_server_last_error(const lfsr_server *s);
 
-/* Queues a request: params as for lfsr_create (host blur and disparity),
- * views (s_k*q floats) and x0 (p floats) in host memory; all are copied.
- * *id receives the request's id (0, 1, 2, ... in submission order). */
+/* Queues a request: params as for lfsr_create (host blur and disparity,
+ * optional view list and projection error), views (s_k*q floats) and x0
+ * (p floats) in host memory; all are copied.  *id receives the request's
+ * id (0, 1, 2, ... in submission order).  Per-view disparity maps and the
+ * backward-warp adjoint are not served (LFSR_EUNSUPPORTED). */
 int lfsr_server_submit(lfsr_server *s, const lfsr_params *params, const float *lr_views,
                        const float *x0, int64_t *id);
 

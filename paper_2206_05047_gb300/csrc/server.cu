@@ -173,6 +173,12 @@ int lfsr_server_submit(lfsr_server* s, const lfsr_params* params, const float* l
     return sfail(s, LFSR_EINVAL, "params, lr_views, x0 and id are required");
   const int64_t est = lfsr_estimate_state_bytes(params);
   if (est < 0) return sfail(s, LFSR_EINVAL, std::string("invalid request: ") + lfsr_last_error(nullptr));
+  // served light fields run the batched (specialised) kernels, which take
+  // one disparity map and the exact adjoint
+  if (params->disparity_views || params->adjoint != LFSR_ADJOINT_EXACT)
+    return sfail(s, LFSR_EUNSUPPORTED,
+                 "served requests take one disparity map and the exact adjoint "
+                 "(disparity_views and the backward warp run on the generic kernels)");
   if (s->have_solver && !same_solver(s->solver, *params))
     return sfail(s, LFSR_EINVAL,
                  "requests must share lambda1, lambda2, mu, the NLTV window, patch and h, "
@@ -196,6 +202,7 @@ int lfsr_server_submit(lfsr_server* s, const lfsr_params* params, const float* l
   r.prm.disparity = nullptr;
   r.prm.views = nullptr;
   r.prm.proj_err = nullptr;
+  r.prm.disparity_views = nullptr;
   r.bytes = est;
   *id = s->next_id++;
   s->reqs.emplace(*id, std::move(r));

@@ -55,3 +55,34 @@ def test_estimate_bounds_the_allocation():
         got = lfsr.stats(s.handle)["state_bytes"]
         assert got <= est <= got + (1 << 20), (got, est)
         s.close()
+
+
+def test_paper_weight_requests_are_the_same_alone_and_in_the_mix():
+    """Requests with the paper's weights and a projection error (copied at
+    submission), one joining at odd parity."""
+    reqs = []
+    for i, (pr, kw) in enumerate(_requests()[:3]):
+        pe = np.random.default_rng(60 + i).standard_normal(pr.wl.HR).astype(np.float32)
+        reqs.append((pr, dict(kw, weights="paper", **synth.PAPER_SIGMAS, proj_err=pe)))
+    for pr, kw in reqs:
+        kw["sigma_o2"] = 0.5
+    n_iter = 7
+    srv = lfsr.Server(8 << 30, max_active=3, iterations=n_iter, iterations_per_step=3)
+    ids = [srv.submit(f32(pr.y), f32(pr.x0), **kw) for pr, kw in reqs[:2]]
+    srv.step()                                   # 3 iterations: the next joins at odd parity
+    ids.append(srv.submit(f32(reqs[2][0].y), f32(reqs[2][0].x0), **reqs[2][1]))
+    for _ in range(50):
+        if srv.stats()["done"] == len(reqs):
+            break
+        srv.step()
+    assert srv.stats()["done"] == len(reqs)
+    for rid, (pr, kw) in zip(ids, reqs):
+        x = np.zeros(pr.wl.HR, np.float32)
+        srv.fetch(rid, x)
+        assert rel_err(x, _alone(kw, pr, n_iter)) <= 1e-5, rid
+    srv.close()
+    est = lfsr.estimate_state_bytes(**reqs[0][1])
+    s = lfsr.Solver(**reqs[0][1])
+    got = lfsr.stats(s.handle)["state_bytes"]
+    assert got <= est <= got + (1 << 20), (got, est)
+    s.close()

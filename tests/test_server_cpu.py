@@ -93,3 +93,19 @@ def test_requests_share_the_solver_constants():
     with pytest.raises(lfsr.LfsrError):
         lfsr.Server(0, dry_run=True)             # no budget
     srv.close()
+
+
+def test_served_requests_take_one_map_and_the_exact_adjoint():
+    srv = lfsr.Server(1 << 40, dry_run=True)
+    for extra in (dict(adjoint="backward"),
+                  dict(disparity_views=np.zeros((9, 32, 32), np.float32))):
+        with pytest.raises(lfsr.LfsrError) as e:
+            _submit(srv, **extra)
+        assert e.value.code == lfsr.LFSR_EUNSUPPORTED
+    # the paper's weights (with a projection error, copied at submission) are served
+    pe = np.zeros((32, 32), np.float32)
+    rid = _submit(srv, weights="paper", sigma_s=8.0, sigma_e=0.1, sigma_o1=1.0, sigma_o2=0.5,
+                  proj_err=pe)
+    del pe
+    assert rid == 0
+    srv.close()
