@@ -144,3 +144,30 @@ def test_quality_improves_over_iterations(oracle_mod):
     p0, p20, p40 = (synth.psnr(v, prob.gt) for v in (prob.x0, x20, x40))
     assert p20 > p0 + 1.5
     assert p40 > p20 + 1.0
+
+
+def test_pure_l2_data_term_keeps_the_data_duals_zero(oracle_mod):
+    """lambda1 = 0 (the l2-only data term of Sec. 6.1's comparison): the data
+    rows of F vanish, u_A = w_A = 0 stays inside the prox threshold, so the
+    data duals stay exactly zero while the regulariser duals move."""
+    wl = synth.custom(U=3, V=3, H=8, W=9, scale=2, kb=5, blur_sigma=1.0, window=3)
+    prob = synth.make_problem(wl, seed=3)
+    o = oracle_mod.Oracle.from_problem(prob, lambda1=0.0, lambda2=4.0, mu=300.0)
+    x, wA, wS = o.admm(prob.y, prob.x0, 4)
+    assert not wA.any() and wS.any()
+    assert np.isfinite(x).all()
+
+
+def test_pure_l1_data_term_solves_the_l1_problem(oracle_mod):
+    """lambda2 = 0 (the l1-only data term, as in the paper's MISR runs): the
+    compact form without the 1/sqrt(lambda2) scaling stays defined, and with
+    identity operators x = y is recovered (exact-penalty argument as in
+    test_exact_recovery_identity_operators)."""
+    rng = np.random.default_rng(1)
+    H = W = 6
+    gt = rng.random((H, W))
+    o = oracle_mod.Oracle(3, 3, H, W, 1, np.array([[1.0]]), np.zeros((H, W)), lambda1=2.0,
+                          lambda2=0.0, mu=1.0, window=3, patch=3, h=0.3, cg_iters=5)
+    y = np.repeat(gt[None], 9, axis=0)
+    x, _, _ = o.admm(y, gt + 0.1 * rng.standard_normal((H, W)), 400)
+    assert np.linalg.norm(x - gt) <= 1e-4 * np.linalg.norm(gt)
