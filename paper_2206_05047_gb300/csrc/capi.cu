@@ -465,6 +465,7 @@ int lfsr::kind_units(const lfsr_handle* h, int kind) {
     case KD_NLA: return h->nl_units;
     case KD_DATA:
     case KD_NORMAL: return h->op_units;
+    case KD_UPDATE: return h->upd_units;
     default: return h->vec_units;
   }
 }
@@ -531,7 +532,7 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
       j.out = h->Q;
       break;
     default:       // KD_UPDATE: x += alpha p, r -= alpha q
-      j.chunk = h->vec_chunk;
+      j.chunk = h->upd_chunk;
       j.p_old = h->P[pb];
       j.q = h->Q;
       j.rr = h->R;
@@ -690,6 +691,14 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
     if (chunk < 256) chunk = 256;
     h->vec_chunk = (int)chunk;
     h->vec_units = (int)((p + chunk - 1) / chunk);
+    // the CG update streams four vectors with little work per pixel: one
+    // CTA per SM (measured faster than two; the initialisation, with its 48
+    // divergence loads per pixel, keeps two)
+    size_t uc = (p + (size_t)h->sm_count - 1) / (size_t)h->sm_count;
+    uc = (uc + 31) / 32 * 32;
+    if (uc < 256) uc = 256;
+    h->upd_chunk = (int)uc;
+    h->upd_units = (int)((p + uc - 1) / uc);
   }
   h->max_grid = h->grid_op;
   if (h->nl.n_tiles > h->max_grid) h->max_grid = h->nl.n_tiles;

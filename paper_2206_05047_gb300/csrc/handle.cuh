@@ -76,6 +76,7 @@ struct lfsr_handle {
   int nl_tiles_x = 0, nl_units = 0;         // 32 x 32 NLTV tiles
   int op_units = 0;                         // (64 x 64 tile, view pair) units
   int vec_chunk = 0, vec_units = 0;         // HR pixels per vector-kernel CTA, CTAs
+  int upd_chunk = 0, upd_units = 0;         // the same for the CG update (one CTA per SM)
   bool profiling = false;
   std::vector<lfsr::ProfEvent> prof;
   double prof_ms[8] = {0};
