@@ -13,12 +13,12 @@ namespace lfsr {
 // DB: directions per chunk of weight loads (the stencil blocking the batch
 // autotuner chooses: 6 or 3).
 template <int WR, class ST, int DB>
-__global__ void __launch_bounds__(NF_THREADS)
+__global__ void __launch_bounds__(NA_THREADS, 2)
 k_nla2(const Geom g, const TableArgs tb) {
   using D = HalfDirs<WR>;
   constexpr int T = NF_T, NP = T + 2 * WR, NPp = NP | 1;
   __shared__ float sP[NP * NPp];
-  __shared__ double s_red[NF_THREADS / 32];
+  __shared__ double s_red[NA_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // this CTA's tile: unit blockIdx.x of the table
   const JobArgs* jp = tb.jobs + table_job(tb, blockIdx.x);
@@ -35,7 +35,7 @@ k_nla2(const Geom g, const TableArgs tb) {
   const int TRr = min(T, Hh - i0), TRc = min(T, Wh - j0);
   const int first = sc->cg_first;
   const float beta = (float)sc->beta;
-  for (int t = tid; t < NP * NP; t += NF_THREADS) {
+  for (int t = tid; t < NP * NP; t += NA_THREADS) {
     const int rr = t / NP, cc = t - rr * NP;
     const int hi = i0 - WR + rr, hj = j0 - WR + cc;
     float v = 0.f;
@@ -53,22 +53,22 @@ k_nla2(const Geom g, const TableArgs tb) {
   }
   __syncthreads();
   const int ju = lane, uj = j0 + ju;
-  const int iu0 = NF_PIX * warp;
+  const int iu0 = NA_PIX * warp;
   const bool col_in = uj < Wh;
   // 32-bit offset of the strip's first pixel (p < 2^31); in an interior
   // tile every owned pixel and its backward neighbours u - d (di <= 0) lie
   // inside the image, so the loads need no bounds checks
   const int off0 = (i0 + iu0) * Wh + uj;
   const bool interior = i0 + T + WR <= Hh && j0 >= WR && j0 + T + WR <= Wh;
-  float acc[NF_PIX];
+  float acc[NA_PIX];
 #pragma unroll
-  for (int m = 0; m < NF_PIX; ++m) acc[m] = 0.f;
+  for (int m = 0; m < NA_PIX; ++m) acc[m] = 0.f;
   // directions in chunks of DB: all weight loads of a chunk are issued
   // before any is used (memory-level parallelism)
 #pragma unroll
   for (int i0d = 0; i0d < D::SH; i0d += DB) {
     using B = SBits<ST>;
-    typename B::R wf[DB][NF_PIX], wb[DB][NF_PIX];
+    typename B::R wf[DB][NA_PIX], wb[DB][NA_PIX];
 #pragma unroll
     for (int e = 0; e < DB; ++e) {
       const int idx = i0d + e;
@@ -78,13 +78,13 @@ k_nla2(const Geom g, const TableArgs tb) {
       const int bo = di * Wh + dj;                  // u - d is bo floats before u
       if (interior) {
 #pragma unroll
-        for (int m = 0; m < NF_PIX; ++m) {
+        for (int m = 0; m < NA_PIX; ++m) {
           wf[e][m] = B::ld(wd + m * Wh);
           wb[e][m] = B::ld(wd + (m * Wh - bo));
         }
       } else {
 #pragma unroll
-        for (int m = 0; m < NF_PIX; ++m) {
+        for (int m = 0; m < NA_PIX; ++m) {
           const int ui = i0 + iu0 + m;
           const int bi = ui - di, bj = uj - dj;
           const bool in = ui < Hh && col_in;
@@ -100,7 +100,7 @@ k_nla2(const Geom g, const TableArgs tb) {
       if (idx >= D::SH) break;
       const int di = D::di(idx), dj = D::dj(idx);
 #pragma unroll
-      for (int m = 0; m < NF_PIX; ++m) {
+      for (int m = 0; m < NA_PIX; ++m) {
         const float* pu = sP + (iu0 + m + WR) * NPp + (ju + WR);
         const float p0 = pu[0];
         const float df = p0 - pu[di * NPp + dj];
@@ -113,16 +113,16 @@ k_nla2(const Geom g, const TableArgs tb) {
     }
   }
 #pragma unroll
-  for (int m = 0; m < NF_PIX; ++m) {
+  for (int m = 0; m < NA_PIX; ++m) {
     const int ui = i0 + iu0 + m;
     if (ui < Hh && col_in) jp->out[(size_t)ui * Wh + uj] = g.mu * acc[m];
   }
   }  // !skip
   // NLTV part of <p, M p> per light field: one slot per tile
-  const double bs = block_sum<NF_THREADS>((double)psum, s_red);
+  const double bs = block_sum<NA_THREADS>((double)psum, s_red);
   if (tid == 0) tb.partials[blockIdx.x] = bs;
   if (table_arrive_last(tb.counter)) {
-    for (int j = warp; j < tb.n_jobs; j += NF_THREADS / 32) {
+    for (int j = warp; j < tb.n_jobs; j += NA_THREADS / 32) {
       const JobArgs* jj = tb.jobs + j;
       const double total = warp_sum_slots(tb.partials + jj->unit0, jj->units);
       if (lane == 0) jj->sc->red[RED_NLTV] = total;
@@ -215,9 +215,9 @@ bool nlf_supported(const Geom& g) {
 template <class ST, int DB>
 static cudaError_t nla2_st(const Geom& g, const TableArgs& t, cudaStream_t s) {
   switch (g.win_r) {
-    case 1: k_nla2<1, ST, DB><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
-    case 2: k_nla2<2, ST, DB><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
-    case 3: k_nla2<3, ST, DB><<<t.total_units, NF_THREADS, 0, s>>>(g, t); break;
+    case 1: k_nla2<1, ST, DB><<<t.total_units, NA_THREADS, 0, s>>>(g, t); break;
+    case 2: k_nla2<2, ST, DB><<<t.total_units, NA_THREADS, 0, s>>>(g, t); break;
+    case 3: k_nla2<3, ST, DB><<<t.total_units, NA_THREADS, 0, s>>>(g, t); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

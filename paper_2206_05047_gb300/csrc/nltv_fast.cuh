@@ -10,6 +10,11 @@ namespace lfsr {
 constexpr int NF_THREADS = 256;
 constexpr int NF_T = 32;
 constexpr int NF_PIX = NF_T * NF_T / NF_THREADS;
+// The weighted-divergence kernel (k_nla2) is bound by the latency of its
+// weight loads: it runs the same tiles with twice the threads (strips of 2
+// rows), 27 warps per SM instead of 13.
+constexpr int NA_THREADS = 512;
+constexpr int NA_PIX = NF_T * NF_T / NA_THREADS;
 
 enum { NLW_BLOCK = 0, NLW_ONLY = 1 };
 
