@@ -171,3 +171,43 @@ def test_pure_l1_data_term_solves_the_l1_problem(oracle_mod):
     y = np.repeat(gt[None], 9, axis=0)
     x, _, _ = o.admm(y, gt + 0.1 * rng.standard_normal((H, W)), 400)
     assert np.linalg.norm(x - gt) <= 1e-4 * np.linalg.norm(gt)
+
+
+def test_rotated_order_equals_textbook_admm(oracle_mod):
+    """Algorithm 1 runs ADMM in the order z, w, x and hands the x-step the
+    over-relaxed dual f = 2w_n - w_{n-1}.  Written the textbook way instead
+    -- x-update by a dense solve of the augmented Lagrangian's normal
+    equations, soft threshold, dual ascent, with z = F x - b', F = [l1 A; S],
+    b' = [l1 y; 0] -- and started from the (z, w) that x0 gives, the same
+    problem produces the same iterates (frozen weights, exact x-step)."""
+    rng = np.random.default_rng(7)
+    l1, l2, mu = 0.7, 1.5, 2.0
+    o = oracle_mod.Oracle(3, 3, 3, 3, 2, synth.gaussian_blur_kernel(3, 0.8),
+                          rng.uniform(-1, 1, (6, 6)), lambda1=l1, lambda2=l2, mu=mu,
+                          window=3, patch=3, h=0.3, cg_iters=400, cg_tol=1e-30,
+                          freeze_weights=True)
+    y = rng.random((9, 3, 3))
+    x0 = rng.random((6, 6))
+    p = 36
+    w0 = o.weights(x0)
+    eye = np.eye(p)
+    A = np.array([np.concatenate([o.A(k, e.reshape(6, 6)).ravel() for k in range(9)])
+                  for e in eye]).T
+    S = np.array([o.S(w0, e.reshape(6, 6)).ravel() for e in eye]).T
+    F = np.vstack([l1 * A, S])
+    b = np.concatenate([l1 * y.ravel(), np.zeros(S.shape[0])])
+    soft = lambda u: np.sign(u) * np.maximum(np.abs(u) - 1.0 / mu, 0.0)
+    N = 6
+    # textbook ADMM for  l2 |Ax - y|^2 + |z|_1  s.t.  z = F x - b'
+    u = F @ x0.ravel() - b
+    z = soft(u)
+    w = u - z
+    M = 2 * l2 * A.T @ A + mu * F.T @ F
+    for k in range(N):
+        x = np.linalg.solve(M, 2 * l2 * A.T @ y.ravel() + mu * F.T @ (b + z - w))
+        if k < N - 1:
+            u = F @ x - b + w
+            z = soft(u)
+            w = u - z
+    xr, _, _ = o.admm(y, x0, N)
+    np.testing.assert_allclose(xr.ravel(), x, rtol=0, atol=1e-9 * np.abs(x).max())
