@@ -74,6 +74,26 @@ def test_forward_and_adjoint_operators(name):
 
 
 @pytest.mark.parametrize("name", [c[0] for c in SMALL])
+def test_adjoint_identity_in_float32(name):
+    """<A x, g> = <x, A^T g> from the kernels' own float32 outputs (summed in
+    float64), to 1e-5 relative."""
+    c = _case(name)
+    o, wl = c.oracle, c.wl
+    rng = np.random.default_rng(11)
+    for _ in range(2):
+        x = f32(rng.standard_normal(o.hr))
+        g = f32(rng.standard_normal((o.s_k, wl.H, wl.W)))
+        ax = c.empty(o.s_k, wl.H, wl.W)
+        atg = c.empty(*o.hr)
+        lfsr.apply_A(c.h, -1, c.t(x), ax)
+        lfsr.apply_AT(c.h, -1, c.t(g), atg)
+        lhs = float(np.vdot(c.np(ax), g.astype(np.float64)))
+        rhs = float(np.vdot(x.astype(np.float64), c.np(atg)))
+        scale = np.linalg.norm(c.np(ax)) * np.linalg.norm(g)
+        assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("name", [c[0] for c in SMALL])
 def test_weights(name):
     c = _case(name)
     o = c.oracle
