@@ -67,6 +67,16 @@ int sfail(lfsr_server* s, int code, const std::string& msg) {
 
 bool dry(const lfsr_server* s) { return (s->cfg.flags & LFSR_SERVER_DRY_RUN) != 0; }
 
+// Frees a request's host copies of its inputs (admitted or failed).
+void release_inputs(Request& r) {
+  for (std::vector<float>* v : {&r.blur, &r.disp, &r.views, &r.x0, &r.proj_err}) {
+    v->clear();
+    v->shrink_to_fit();
+  }
+  r.view_list.clear();
+  r.view_list.shrink_to_fit();
+}
+
 // Frees a request's device state (its slot and budget).
 void release(lfsr_server* s, Request& r) {
   if (r.h) lfsr_destroy(r.h);
@@ -88,8 +98,7 @@ int admit(lfsr_server* s) {
       s->queue.pop_front();
       r.state = LFSR_REQ_FAILED;
       r.error = LFSR_ENOMEM;
-      r.views.clear();
-      r.x0.clear();
+      release_inputs(r);
       continue;
     }
     if (s->bytes_in_use + r.bytes > s->cfg.hbm_budget_bytes) break;
@@ -110,16 +119,13 @@ int admit(lfsr_server* s) {
         if (h) lfsr_destroy(h);
         r.state = LFSR_REQ_FAILED;
         r.error = rc;
-        r.views.clear();
-        r.x0.clear();
+        release_inputs(r);
         continue;
       }
       r.h = h;
     }
-    r.views.clear();
-    r.views.shrink_to_fit();
-    r.x0.clear();
-    r.x0.shrink_to_fit();
+    // the handle holds what the solve needs: drop the host copies
+    release_inputs(r);
     r.state = LFSR_REQ_ACTIVE;
     r.iters = 0;
     s->bytes_in_use += r.bytes;

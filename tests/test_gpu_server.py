@@ -86,3 +86,32 @@ def test_paper_weight_requests_are_the_same_alone_and_in_the_mix():
     got = lfsr.stats(s.handle)["state_bytes"]
     assert got <= est <= got + (1 << 20), (got, est)
     s.close()
+
+
+def test_a_request_failing_at_admission_leaves_the_others_running():
+    """A request the served kernels cannot take (a non-separable blur needs
+    the generic operator kernel) fails when admitted, with its error code;
+    the requests around it complete as if it had not been there."""
+    reqs = _requests()[:3]
+    pr_bad, kw_bad = reqs[1]
+    K = np.random.default_rng(9).random((5, 5)) ** 3
+    kw_bad = dict(kw_bad, blur=f32(K / K.sum()))
+    n_iter = 5
+    srv = lfsr.Server(8 << 30, max_active=3, iterations=n_iter, iterations_per_step=2)
+    ids = [srv.submit(f32(reqs[0][0].y), f32(reqs[0][0].x0), **reqs[0][1]),
+           srv.submit(f32(pr_bad.y), f32(pr_bad.x0), **kw_bad),
+           srv.submit(f32(reqs[2][0].y), f32(reqs[2][0].x0), **reqs[2][1])]
+    for _ in range(20):
+        st = srv.stats()
+        if st["done"] + st["failed"] == 3:
+            break
+        srv.step()
+    st = srv.stats()
+    assert st["done"] == 2 and st["failed"] == 1 and st["bytes_in_use"] == 0
+    state, _, rc = srv.status(ids[1])
+    assert state == lfsr.LFSR_REQ_FAILED and rc == lfsr.LFSR_EUNSUPPORTED
+    for rid, (pr, kw) in ((ids[0], reqs[0]), (ids[2], reqs[2])):
+        x = np.zeros(pr.wl.HR, np.float32)
+        srv.fetch(rid, x)
+        assert rel_err(x, _alone(kw, pr, n_iter)) <= 1e-5, rid
+    srv.close()
