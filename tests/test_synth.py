@@ -34,3 +34,24 @@ def test_bicubic_interpolates_lr_samples():
     lr = rng.random((6, 5))
     hr = synth.bicubic_upsample(lr, 2)
     np.testing.assert_allclose(hr[::2, ::2], lr, atol=1e-15)
+
+
+def test_degenerate_shapes_generate():
+    """One LR pixel, one row, one column: the scene generator still places
+    its planes (discs wider than the image are centred on that axis)."""
+    for kw in (dict(H=1, W=1, scale=4), dict(H=1, W=40, scale=2), dict(H=37, W=1, scale=3)):
+        wl = synth.custom(U=3, V=3, kb=5, blur_sigma=1.0, disparities=(-1.0, 0.0, 0.7), **kw)
+        pr = synth.make_problem(wl, seed=0)
+        assert pr.y.shape == (9, wl.H, wl.W) and pr.gt.shape == wl.HR
+        assert np.isfinite(pr.y).all() and np.isfinite(pr.x0).all()
+
+
+def test_view_disparity_maps_match_the_rendered_planes():
+    wl = synth.custom(U=5, V=3, H=10, W=12, scale=2, disparities=(-1.0, 0.0, 0.8))
+    pr = synth.make_problem(wl, seed=3)
+    maps = synth.view_disparity_maps(pr)
+    assert maps.shape == (wl.s_k,) + wl.HR
+    assert np.array_equal(maps[wl.s_k // 2], pr.disparity)        # centre view = reference
+    assert set(np.unique(maps)) <= set(wl.disparities)
+    sub = synth.view_disparity_maps(pr, views=[0, 7, 14])
+    assert np.array_equal(sub, maps[[0, 7, 14]])
