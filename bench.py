@@ -43,7 +43,17 @@ BATCH_WORKLOAD = "batch_uneven"
 SERVE_WORKLOAD = "serve_poisson"
 UNIT = "Mpix*iter/s"
 FP32_LANES_PER_SM = 128
-SM_COUNT = 152
+# the arithmetic type of the path with the storage kind of its large streams
+DTYPE = {"fp32": "f32", "fp16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)",
+         "fp16-views32": "f32 (f16 storage, f32 views)",
+         "bf16-views32": "f32 (bf16 storage, f32 views)"}
+
+
+def sm_count(dev=None) -> int:
+    """Streaming multiprocessors of the device (the FP32 peak's SM factor)."""
+    import torch
+    return int(torch.cuda.get_device_properties(dev if dev is not None else 0)
+               .multi_processor_count)
 
 
 def args():
@@ -393,7 +403,8 @@ def run_batch(a):
     flops = sum(normal_flops_per_launch(w) for w in wls)         # one CG step, all light fields
     normal_ms_per_step = per_class["normal_apply"]["ms"] / max(n_iter * wls[0].cg_iters, 1)
     sm_clk = (clk.get("sm_max_mhz") or 2070.0)
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_clk * 1e6 / 1e12
+    n_sm = sm_count()
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_clk * 1e6 / 1e12
     achieved = flops / (normal_ms_per_step / 1e3) / 1e12
     launches = batch.launches_per_iteration()
     roofline = {"bound": "alu",
@@ -401,7 +412,7 @@ def run_batch(a):
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
                 "normal_ms_per_cg_step": normal_ms_per_step, "flops_per_cg_step": flops,
-                "peak_note": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                "peak_note": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                              f"{sm_clk:.0f} MHz",
                 "per_kernel_ms_per_step": {k: v["ms"] for k, v in per_class.items()}}
     batch.close()
@@ -453,7 +464,7 @@ def run_batch(a):
     groups = sorted({(w.scale, w.kb) for w in wls})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": t_batch / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[a.precision],
             "data": "synthetic (seeded textured-plane light fields)",
             "config": {"workload": BATCH_WORKLOAD, "light_fields": len(wls),
                        "iterations": n_iter, "cg_iters": wls[0].cg_iters,
@@ -598,7 +609,7 @@ def run_serve(a):
     d2h = int(sum(xs[r].nbytes for r in xs))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": 1e3 * (t_end - arrivals[0]), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[a.precision],
             "data": "synthetic (seeded textured-plane light fields)",
             "config": {"workload": SERVE_WORKLOAD, "arrivals_per_s": a.serve_rate,
                        "arrival_window_s": a.serve_seconds, "requests": len(arrivals),
@@ -748,14 +759,15 @@ def main():
     avg_ms = dom["ms"] / max(dom["launches"], 1)
     flops = normal_flops_per_launch(wl)
     sm_clk = (clk.get("sm_max_mhz") or 2070.0)
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_clk * 1e6 / 1e12
+    n_sm = sm_count(dev)
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_clk * 1e6 / 1e12
     achieved = flops / (avg_ms / 1e3) / 1e12
     traffic = traffic_from_profile(wl)
     roofline = {"bound": "alu", "kernel": "k_operator_fast<OP_NORMAL> (sum_k A_k^T A_k p)",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "avg_launch_ms": avg_ms, "flops_per_launch": flops,
-                "peak_note": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                "peak_note": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                              f"{sm_clk:.0f} MHz",
                 "share_of_step": dom["ms"] / total_prof if total_prof else None,
                 "per_kernel_ms_per_step": {k: v["ms"] for k, v in per_class.items()}}
@@ -782,7 +794,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_ms / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic (seeded textured-plane light field)",
+                "dtype": DTYPE[a.precision],
+                "data": "synthetic (seeded textured-plane light field)",
                 "config": workload_config(wl, n_iter, {
                     "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                     "weights": "patch distance exp(-pd/h^2)" if a.weights == "patch" else

@@ -462,14 +462,21 @@ int lfsr_server_stats(const lfsr_server *s, lfsr_server_stats_t *out);
  *     hold at most LFSR_NOALLOC_MAX_TILES tiles of 32 x 32 pixels (e.g.
  *     2048 x 2048).
  *
- * params: as for lfsr_create (host blur; host disparity, read only for the
- * shift bound).  d_disparity, d_xw (weights source), d_p and d_q are device
- * pointers of the current device (Hh*Wh floats each); *pMp (host) receives
- * <p, M p> in float64.  Work is ordered on cuda_stream and the call blocks
- * until it is done.  The message of a failure is readable with
- * lfsr_last_error(NULL).  Only the patch weights, the shared disparity map
- * and the exact adjoint are supported here (LFSR_WEIGHTS_PAPER,
- * disparity_views and LFSR_ADJOINT_BACKWARD_WARP return LFSR_EUNSUPPORTED). */
+ * params: validated as by lfsr_create (host blur; host disparity, which
+ * must hold the same map as d_disparity); precision must be LFSR_FP32.
+ * d_disparity, d_xw (weights source), d_p and d_q are device pointers of
+ * the current device (Hh*Wh floats each); *pMp (host) receives <p, M p> in
+ * float64.  The kernels warp by d_disparity: before they run, a check kernel
+ * reads it, refuses NaN or infinite values (LFSR_EINVAL) and sizes the warp
+ * halo over the larger of the two maps' magnitudes, so a device map that
+ * differs from the host one cannot move a tap outside the staged tile.  Work
+ * is ordered on cuda_stream; the call synchronises that stream twice (after
+ * the check and at the end) and returns when <p, M p> is on the host.  The
+ * message of a failure is readable with lfsr_last_error(NULL).  Only the
+ * patch weights, the shared disparity map and the exact adjoint are
+ * supported here (LFSR_WEIGHTS_PAPER, disparity_views,
+ * LFSR_ADJOINT_BACKWARD_WARP and 16-bit precision return
+ * LFSR_EUNSUPPORTED). */
 #define LFSR_NOALLOC_MAX_TILES 4096
 #define LFSR_NOALLOC_SCRATCH_BYTES (64 * 1024 + 256)
 

@@ -414,6 +414,93 @@ JobArgs standalone_job(const lfsr_handle* h) {
 
 }  // namespace
 
+int lfsr::geom_from_params(const lfsr_params* pr, Geom* out) {
+  int rc = validate(pr);
+  if (rc != LFSR_OK) return rc;
+  const int Hh = pr->scale * pr->H, Wh = pr->scale * pr->W;
+  const size_t p = (size_t)Hh * Wh;
+  std::vector<float> K(pr->blur, pr->blur + (size_t)pr->kb * pr->kb);
+  if (!finite_all(K.data(), K.size()) || !finite_all(pr->disparity, p))
+    return fail(nullptr, LFSR_EINVAL, "blur or disparity has non-finite values");
+  if (pr->weights == LFSR_WEIGHTS_PAPER && pr->proj_err && !finite_all(pr->proj_err, p))
+    return fail(nullptr, LFSR_EINVAL, "proj_err has non-finite values");
+  const size_t n_views = pr->views ? (size_t)pr->n_views : (size_t)pr->U * pr->V;
+  if (pr->disparity_views && !finite_all(pr->disparity_views, n_views * p))
+    return fail(nullptr, LFSR_EINVAL, "disparity_views has non-finite values");
+  Geom& g = *out;
+  g = Geom{};
+  g.U = pr->U;
+  g.V = pr->V;
+  g.sk = pr->views ? pr->n_views : pr->U * pr->V;
+  g.H = pr->H;
+  g.W = pr->W;
+  g.Hh = Hh;
+  g.Wh = Wh;
+  g.zeta = pr->scale;
+  g.kb = pr->kb;
+  g.r = (pr->kb - 1) / 2;
+  for (int i = 0; i < pr->kb * pr->kb; ++i) g.k2[i] = K[i];
+  g.separable = separable_factor(K, pr->kb, g.kv, g.kh);
+  double max_disp = 0.0;
+  for (size_t i = 0; i < p; ++i) max_disp = std::fmax(max_disp, std::fabs((double)pr->disparity[i]));
+  g.S = shift_bound(max_disp, pr->U, pr->V);
+  g.warp_views = pr->disparity_views ? 1 : 0;
+  g.adjoint_bw = pr->adjoint == LFSR_ADJOINT_BACKWARD_WARP ? 1 : 0;
+  if (pr->disparity_views) {
+    // W_k reads omega_k: the shift bound covers every per-view map too
+    double mv = 0.0;
+    for (size_t i = 0; i < n_views * p; ++i) mv = std::fmax(mv, std::fabs((double)pr->disparity_views[i]));
+    const int sv = shift_bound(mv, pr->U, pr->V);
+    if (sv > g.S) g.S = sv;
+  }
+  // angular offsets of the views of the data (the grid, or the listed subset)
+  for (int j = 0; j < g.sk; ++j) {
+    const int k = pr->views ? pr->views[j] : j;
+    g.tu[j] = (float)((k % pr->U) - 0.5 * (pr->U - 1));
+    g.tv[j] = (float)((k / pr->U) - 0.5 * (pr->V - 1));
+  }
+  g.win_r = (pr->nltv_window - 1) / 2;
+  g.patch_r = (pr->nltv_patch - 1) / 2;
+  g.sh = (pr->nltv_window * pr->nltv_window - 1) / 2;
+  {
+    int n = 0;
+    for (int a = -g.win_r; a <= g.win_r && n < g.sh; ++a)
+      for (int b = -g.win_r; b <= g.win_r && n < g.sh; ++b) {
+        g.di[n] = (int8_t)a;
+        g.dj[n] = (int8_t)b;
+        ++n;
+      }
+  }
+  g.inv_h2 = (float)(1.0 / (pr->nltv_h * pr->nltv_h));
+  g.inv_np = (float)(1.0 / (double)(pr->nltv_patch * pr->nltv_patch));
+  g.wscheme = pr->weights == LFSR_WEIGHTS_PAPER ? WS_PAPER : WS_PATCH;
+  if (g.wscheme == WS_PAPER) {
+    // no patches; the x halo of one pixel feeds the edge factor's central
+    // differences
+    g.patch_r = 1;
+    g.inv_np = 1.f / 9.f;
+    g.inv_sig_s = pr->sigma_s > 0.f ? (float)(1.0 / pr->sigma_s) : 0.f;
+    g.inv_sig_e = pr->sigma_e > 0.f ? (float)(1.0 / pr->sigma_e) : 0.f;
+  }
+  g.lambda1 = (float)pr->lambda1;
+  g.lambda2 = (float)pr->lambda2;
+  g.mu = (float)pr->mu;
+  g.cA = (float)(pr->lambda2 + 0.5 * pr->mu * pr->lambda1 * pr->lambda1);
+  g.thr = (float)(1.0 / pr->mu);
+  g.tau = pr->cg_tol;
+  {
+    const int base = pr->precision & ~LFSR_KEEP_VIEWS_FP32;
+    g.st = base == LFSR_FP16_STORAGE ? ST_F16 : base == LFSR_BF16_STORAGE ? ST_BF16 : ST_F32;
+    g.st_y = (pr->precision & LFSR_KEEP_VIEWS_FP32) ? ST_F32 : g.st;
+  }
+  return LFSR_OK;
+}
+
+int lfsr::shift_bound(double max_abs_disparity, int U, int V) {
+  const double max_theta = 0.5 * (double)((U > V ? U : V) - 1);
+  return (int)std::ceil(max_abs_disparity * max_theta);
+}
+
 void lfsr::set_thread_error(const char* msg) { t_err = msg; }
 
 int lfsr::handle_fail(lfsr_handle* h, int code, const std::string& msg) { return fail(h, code, msg); }
@@ -547,18 +634,11 @@ extern "C" {
 int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   if (!out) return fail(nullptr, LFSR_EINVAL, "out is NULL");
   *out = nullptr;
-  int rc = validate(pr);
+  Geom geom{};
+  int rc = geom_from_params(pr, &geom);
   if (rc != LFSR_OK) return rc;
-  const int Hh = pr->scale * pr->H, Wh = pr->scale * pr->W;
+  const int Hh = geom.Hh, Wh = geom.Wh;
   const size_t p = (size_t)Hh * Wh, q = (size_t)pr->H * pr->W;
-  std::vector<float> K(pr->blur, pr->blur + (size_t)pr->kb * pr->kb);
-  if (!finite_all(K.data(), K.size()) || !finite_all(pr->disparity, p))
-    return fail(nullptr, LFSR_EINVAL, "blur or disparity has non-finite values");
-  if (pr->weights == LFSR_WEIGHTS_PAPER && pr->proj_err && !finite_all(pr->proj_err, p))
-    return fail(nullptr, LFSR_EINVAL, "proj_err has non-finite values");
-  const size_t n_views = pr->views ? (size_t)pr->n_views : (size_t)pr->U * pr->V;
-  if (pr->disparity_views && !finite_all(pr->disparity_views, n_views * p))
-    return fail(nullptr, LFSR_EINVAL, "disparity_views has non-finite values");
 
   lfsr_handle* h = new (std::nothrow) lfsr_handle();
   if (!h) return fail(nullptr, LFSR_ENOMEM, "host allocation failed");
@@ -570,72 +650,8 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   h->prm.disparity_views = nullptr;
   if (pr->views) h->views.assign(pr->views, pr->views + pr->n_views);
   h->stream = (cudaStream_t)cuda_stream;
-  Geom& g = h->g;
-  g.U = pr->U;
-  g.V = pr->V;
-  g.sk = pr->views ? pr->n_views : pr->U * pr->V;
-  g.H = pr->H;
-  g.W = pr->W;
-  g.Hh = Hh;
-  g.Wh = Wh;
-  g.zeta = pr->scale;
-  g.kb = pr->kb;
-  g.r = (pr->kb - 1) / 2;
-  for (int i = 0; i < pr->kb * pr->kb; ++i) g.k2[i] = K[i];
-  g.separable = separable_factor(K, pr->kb, g.kv, g.kh);
-  double max_disp = 0.0;
-  for (size_t i = 0; i < p; ++i) max_disp = std::fmax(max_disp, std::fabs((double)pr->disparity[i]));
-  const double max_theta = 0.5 * (double)((pr->U > pr->V ? pr->U : pr->V) - 1);
-  g.S = (int)std::ceil(max_disp * max_theta);
-  g.warp_views = pr->disparity_views ? 1 : 0;
-  g.adjoint_bw = pr->adjoint == LFSR_ADJOINT_BACKWARD_WARP ? 1 : 0;
-  if (pr->disparity_views) {
-    // W_k reads omega_k: the shift bound covers every per-view map too
-    double mv = 0.0;
-    for (size_t i = 0; i < n_views * p; ++i) mv = std::fmax(mv, std::fabs((double)pr->disparity_views[i]));
-    const int sv = (int)std::ceil(mv * max_theta);
-    if (sv > g.S) g.S = sv;
-  }
-  // angular offsets of the views of the data (the grid, or the listed subset)
-  for (int j = 0; j < g.sk; ++j) {
-    const int k = pr->views ? pr->views[j] : j;
-    g.tu[j] = (float)((k % pr->U) - 0.5 * (pr->U - 1));
-    g.tv[j] = (float)((k / pr->U) - 0.5 * (pr->V - 1));
-  }
-  g.win_r = (pr->nltv_window - 1) / 2;
-  g.patch_r = (pr->nltv_patch - 1) / 2;
-  g.sh = (pr->nltv_window * pr->nltv_window - 1) / 2;
-  {
-    int n = 0;
-    for (int a = -g.win_r; a <= g.win_r && n < g.sh; ++a)
-      for (int b = -g.win_r; b <= g.win_r && n < g.sh; ++b) {
-        g.di[n] = (int8_t)a;
-        g.dj[n] = (int8_t)b;
-        ++n;
-      }
-  }
-  g.inv_h2 = (float)(1.0 / (pr->nltv_h * pr->nltv_h));
-  g.inv_np = (float)(1.0 / (double)(pr->nltv_patch * pr->nltv_patch));
-  g.wscheme = pr->weights == LFSR_WEIGHTS_PAPER ? WS_PAPER : WS_PATCH;
-  if (g.wscheme == WS_PAPER) {
-    // no patches; the x halo of one pixel feeds the edge factor's central
-    // differences
-    g.patch_r = 1;
-    g.inv_np = 1.f / 9.f;
-    g.inv_sig_s = pr->sigma_s > 0.f ? (float)(1.0 / pr->sigma_s) : 0.f;
-    g.inv_sig_e = pr->sigma_e > 0.f ? (float)(1.0 / pr->sigma_e) : 0.f;
-  }
-  g.lambda1 = (float)pr->lambda1;
-  g.lambda2 = (float)pr->lambda2;
-  g.mu = (float)pr->mu;
-  g.cA = (float)(pr->lambda2 + 0.5 * pr->mu * pr->lambda1 * pr->lambda1);
-  g.thr = (float)(1.0 / pr->mu);
-  g.tau = pr->cg_tol;
-  {
-    const int base = pr->precision & ~LFSR_KEEP_VIEWS_FP32;
-    g.st = base == LFSR_FP16_STORAGE ? ST_F16 : base == LFSR_BF16_STORAGE ? ST_BF16 : ST_F32;
-    g.st_y = (pr->precision & LFSR_KEEP_VIEWS_FP32) ? ST_F32 : g.st;
-  }
+  h->g = geom;
+  const Geom& g = h->g;
   h->esize = storage_bytes(g.st);
   h->esize_y = storage_bytes(g.st_y);
   h->p = p;

@@ -106,6 +106,13 @@ cudaError_t batch_assign(lfsr_batch* b, const std::vector<lfsr_handle*>& jobs);
 int batch_parity(const lfsr_batch* b);
 // Solver parameters all light fields of one batch or server must share.
 bool same_solver(const lfsr_params& a, const lfsr_params& c);
+// Validates params (sizes, parameters, finiteness of the blur and of every
+// disparity map) and fills the geometry and solver constants every kernel
+// takes; the message of a failure goes to the thread (lfsr_last_error(NULL)).
+int geom_from_params(const lfsr_params* params, Geom* g);
+// Integer bound S on |theta_k * omega| over a U x V grid (the halo of the
+// warp) for a disparity map whose largest magnitude is max_abs_disparity.
+int shift_bound(double max_abs_disparity, int U, int V);
 // Records an error on h (and the thread) and returns code.
 int handle_fail(lfsr_handle* h, int code, const std::string& msg);
 int handle_cuda_fail(lfsr_handle* h, cudaError_t e, const char* what);

@@ -11,9 +11,11 @@
 // device (with that device current) and passed to the kernels.
 #include <cmath>
 #include <cstddef>
+#include <cstring>
 #include <mutex>
 
 #include "lfsr.h"
+#include "handle.cuh"
 #include "lfsr_internal.cuh"
 
 using namespace lfsr;
@@ -33,6 +35,8 @@ constexpr int kMaxOpCtas = 1024;
 struct NoallocScratch {
   DevScalars sc;
   unsigned int counter;            // the specialised operator kernel's arrival counter
+  unsigned int disp_absmax_bits;   // max |d_disparity| (float bits), then
+  unsigned int disp_nonfinite;     // 1 if d_disparity holds a NaN or an infinity
   float2 theta[LFSR_MAX_VIEWS];    // angular offsets of the views
   double nl_partials[kMaxCtas];    // NLTV part, one per 32 x 32 tile
   double op_partials[kMaxOpCtas];  // operator part, one per CTA
@@ -84,6 +88,30 @@ int setup_device(int dev, const Geom& g, DeviceSetup* out, const char** err) {
   return LFSR_OK;
 }
 
+// Largest |d| over n values (as the bits of a non-negative float, whose
+// unsigned order is the float order) into bits[0]; bits[1] := 1 if some
+// value is not finite.
+__global__ void k_disp_absmax(const float* __restrict__ d, long long n, unsigned int* bits) {
+  float m = 0.f;
+  unsigned int bad = 0u;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float a = fabsf(d[i]);
+    if (a <= 3.402823466e38f)
+      m = fmaxf(m, a);
+    else
+      bad = 1u;   // NaN or infinity
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(bits, __float_as_uint(m));
+    if (bad) atomicOr(bits + 1, 1u);
+  }
+}
+
 // the message is readable with lfsr_last_error(NULL)
 int nfail(int code, const char* msg) {
   set_thread_error(msg);
@@ -95,102 +123,27 @@ int nfail(int code, const char* msg) {
 extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_disparity,
                                          const float* d_xw, const float* d_p, float* d_q,
                                          double* pMp, void* cuda_stream) {
-  if (!pr || pr->struct_size != sizeof(lfsr_params))
-    return nfail(LFSR_EINVAL, "params missing or struct_size mismatch");
+  // the same validation and geometry as lfsr_create
+  Geom g{};
+  {
+    const int rc = geom_from_params(pr, &g);
+    if (rc != LFSR_OK) return rc;   // the message is already on the thread
+  }
   if (!d_disparity || !d_xw || !d_p || !d_q)
     return nfail(LFSR_EINVAL, "device pointers d_disparity, d_xw, d_p, d_q are required");
-  if (!pr->blur || !pr->disparity) return nfail(LFSR_EINVAL, "params blur and disparity are required");
-  if (pr->U < 1 || pr->V < 1 || !(pr->U & 1) || !(pr->V & 1) || pr->U * pr->V > LFSR_MAX_VIEWS)
-    return nfail(LFSR_EINVAL, "U and V must be odd, >= 1, with U*V <= 289");
-  if (pr->H < 1 || pr->W < 1 || pr->scale < 1 || pr->scale > 4 || pr->kb < 1 || !(pr->kb & 1) ||
-      pr->kb > LFSR_MAX_KB || pr->nltv_window < 3 || pr->nltv_window > 15 ||
-      !(pr->nltv_window & 1) || pr->nltv_patch < 1 || pr->nltv_patch > 7 ||
-      !(pr->nltv_patch & 1) || !(pr->nltv_h > 0.0) || !(pr->mu > 0.0) ||
-      !(pr->lambda1 >= 0.0) || !(pr->lambda2 >= 0.0))
-    return nfail(LFSR_EINVAL, "invalid size or parameter");
   if (pr->weights != LFSR_WEIGHTS_PATCH)
-    return nfail(pr->weights == LFSR_WEIGHTS_PAPER ? LFSR_EUNSUPPORTED : LFSR_EINVAL,
-                 "the no-allocation entry point takes the patch weights only");
+    return nfail(LFSR_EUNSUPPORTED, "the no-allocation entry point takes the patch weights only");
   if (pr->disparity_views || pr->adjoint != LFSR_ADJOINT_EXACT)
-    return nfail(pr->adjoint == LFSR_ADJOINT_BACKWARD_WARP || pr->disparity_views
-                     ? LFSR_EUNSUPPORTED : LFSR_EINVAL,
+    return nfail(LFSR_EUNSUPPORTED,
                  "the no-allocation entry point takes one disparity map and the exact adjoint");
-  const long long Hh = (long long)pr->scale * pr->H, Wh = (long long)pr->scale * pr->W;
+  if (pr->precision != LFSR_FP32)
+    return nfail(LFSR_EUNSUPPORTED,
+                 "the no-allocation entry point computes in float32 only (precision LFSR_FP32)");
   // the NLTV kernel runs one CTA per 32 x 32 HR tile; its partials must fit
-  const long long nl_tiles = ((Hh + 31) / 32) * ((Wh + 31) / 32);
+  const long long nl_tiles = ((g.Hh + 31LL) / 32) * ((g.Wh + 31LL) / 32);
   if (nl_tiles > kMaxCtas)
     return nfail(LFSR_EINVAL,
                  "HR image too large for the no-allocation scratch (at most 4096 tiles of 32x32)");
-
-  Geom g{};
-  g.U = pr->U;
-  g.V = pr->V;
-  if (pr->views && (pr->n_views < 1 || pr->n_views > pr->U * pr->V))
-    return nfail(LFSR_EINVAL, "n_views must be in [1, U*V]");
-  for (int j = 0; pr->views && j < pr->n_views; ++j)
-    if (pr->views[j] < 0 || pr->views[j] >= pr->U * pr->V || (j && pr->views[j] <= pr->views[j - 1]))
-      return nfail(LFSR_EINVAL, "views must be strictly ascending grid indices in [0, U*V)");
-  g.sk = pr->views ? pr->n_views : pr->U * pr->V;
-  g.H = pr->H;
-  g.W = pr->W;
-  g.Hh = (int)Hh;
-  g.Wh = (int)Wh;
-  g.zeta = pr->scale;
-  g.kb = pr->kb;
-  g.r = (pr->kb - 1) / 2;
-  {
-    const int kb = pr->kb;
-    int am = 0, bm = 0;
-    double best = -1.0;
-    for (int i = 0; i < kb * kb; ++i) {
-      g.k2[i] = pr->blur[i];
-      if (std::fabs((double)pr->blur[i]) > best) {
-        best = std::fabs((double)pr->blur[i]);
-        am = i / kb;
-        bm = i % kb;
-      }
-    }
-    g.separable = 0;
-    if (best > 0.0) {
-      const double pivot = pr->blur[am * kb + bm];
-      double err = 0.0;
-      for (int a = 0; a < kb; ++a)
-        for (int b = 0; b < kb; ++b)
-          err = std::fmax(err, std::fabs((double)pr->blur[a * kb + bm] *
-                                             (double)pr->blur[am * kb + b] / pivot -
-                                         (double)pr->blur[a * kb + b]));
-      if (err <= 1e-7 * best) {
-        g.separable = 1;
-        for (int a = 0; a < kb; ++a) g.kv[a] = pr->blur[a * kb + bm];
-        for (int b = 0; b < kb; ++b) g.kh[b] = (float)((double)pr->blur[am * kb + b] / pivot);
-      }
-    }
-  }
-  double max_disp = 0.0;
-  for (long long i = 0; i < Hh * Wh; ++i)
-    max_disp = std::fmax(max_disp, std::fabs((double)pr->disparity[i]));
-  g.S = (int)std::ceil(max_disp * 0.5 * (double)((pr->U > pr->V ? pr->U : pr->V) - 1));
-  for (int j = 0; j < g.sk; ++j) {
-    const int k = pr->views ? pr->views[j] : j;
-    g.tu[j] = (float)((k % pr->U) - 0.5 * (pr->U - 1));
-    g.tv[j] = (float)((k / pr->U) - 0.5 * (pr->V - 1));
-  }
-  g.win_r = (pr->nltv_window - 1) / 2;
-  g.patch_r = (pr->nltv_patch - 1) / 2;
-  g.sh = (pr->nltv_window * pr->nltv_window - 1) / 2;
-  for (int a = -g.win_r, n = 0; a <= g.win_r && n < g.sh; ++a)
-    for (int b = -g.win_r; b <= g.win_r && n < g.sh; ++b, ++n) {
-      g.di[n] = (int8_t)a;
-      g.dj[n] = (int8_t)b;
-    }
-  g.inv_h2 = (float)(1.0 / (pr->nltv_h * pr->nltv_h));
-  g.inv_np = (float)(1.0 / (double)(pr->nltv_patch * pr->nltv_patch));
-  g.lambda1 = (float)pr->lambda1;
-  g.lambda2 = (float)pr->lambda2;
-  g.mu = (float)pr->mu;
-  g.cA = (float)(pr->lambda2 + 0.5 * pr->mu * pr->lambda1 * pr->lambda1);
-  g.thr = (float)(1.0 / pr->mu);
-  g.tau = pr->cg_tol;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -199,6 +152,30 @@ extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_d
   const char* err = "no error";
   const int rc = setup_device(dev, g, &ds, &err);
   if (rc != LFSR_OK) return nfail(rc, err);
+
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  NoallocScratch* scr = ds.scratch;
+  // The kernels warp by d_disparity while the halo S above comes from the
+  // host map: take S over the device map too (and refuse non-finite values),
+  // so that every tap stays inside the staged tile whatever the caller
+  // passed.
+  {
+    unsigned int words[2] = {0u, 0u};
+    if (cudaMemsetAsync(&scr->disp_absmax_bits, 0, 2 * sizeof(unsigned int), s) != cudaSuccess)
+      return nfail(LFSR_ECUDA, "clearing the disparity check failed");
+    k_disp_absmax<<<ds.sm_count * 2, 256, 0, s>>>(d_disparity, (long long)g.Hh * g.Wh,
+                                                  &scr->disp_absmax_bits);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(words, &scr->disp_absmax_bits, sizeof(words), cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return nfail(LFSR_ECUDA, "checking d_disparity failed");
+    if (words[1]) return nfail(LFSR_EINVAL, "d_disparity has non-finite values");
+    float dmax;
+    std::memcpy(&dmax, &words[0], sizeof(float));
+    const int sd = shift_bound((double)dmax, pr->U, pr->V);
+    if (sd > g.S) g.S = sd;
+  }
 
   OpPlan op{};
   NlPlan nl{};
@@ -213,8 +190,6 @@ extern "C" int lfsr_apply_normal_noalloc(const lfsr_params* pr, const float* d_d
   if (grid > kMaxOpCtas || nl.n_tiles > kMaxCtas)
     return nfail(LFSR_EINVAL, "launch larger than the no-allocation scratch");
 
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  NoallocScratch* scr = ds.scratch;
   {
     float2 th[LFSR_MAX_VIEWS];
     for (int j = 0; j < g.sk; ++j) th[j] = make_float2(g.tu[j], g.tv[j]);

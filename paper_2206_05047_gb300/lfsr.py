@@ -346,32 +346,38 @@ def stats(handle) -> dict:
 
 def apply_normal_noalloc(U, V, H, W, scale, blur, disparity, d_disparity, xw, p, q,
                          lambda1=1.0, lambda2=4.0, mu=1.0, nltv_window=5, nltv_patch=3,
-                         nltv_h=0.1, stream=None, weights=LFSR_WEIGHTS_PATCH) -> float:
+                         nltv_h=0.1, stream=None, weights=LFSR_WEIGHTS_PATCH, views=None,
+                         precision=LFSR_FP32) -> float:
     """lfsr_apply_normal_noalloc: q = M p and <p, M p> without a handle and
     without device allocation.  For callers that cannot allocate device
     memory (a host framework owns the device heap, a hard memory cap, or no
     tolerance for the synchronisation cudaMalloc implies).  disparity is
-    the host map (for the shift bound); d_disparity, xw, p, q are CUDA
-    tensors of the current device."""
+    the host map (the same map as d_disparity); d_disparity, xw, p, q are
+    contiguous float32 CUDA tensors of the current device with at least
+    (scale*H) * (scale*W) elements; views: optional grid indices of the
+    views used."""
+    import torch
     lib = load_library()
-    blur = np.ascontiguousarray(blur, dtype=np.float32)
-    disp = np.ascontiguousarray(disparity, dtype=np.float32)
-    prm = lfsr_params(C.sizeof(lfsr_params), U, V, H, W, scale, blur.shape[0],
-                      blur.ctypes.data_as(C.POINTER(C.c_float)),
-                      disp.ctypes.data_as(C.POINTER(C.c_float)),
-                      lambda1, lambda2, mu, nltv_window, nltv_patch, nltv_h, 0, 0.0, LFSR_FP32)
-    prm.weights = WEIGHT_SCHEMES[weights] if isinstance(weights, str) else int(weights)
+    Hh, Wh = scale * H, scale * W
+    b = np.asarray(blur)
+    if b.ndim != 2 or b.shape[0] != b.shape[1]:
+        raise ValueError("blur must be a square kb x kb array")
+    if np.asarray(disparity).shape != (Hh, Wh):
+        raise ValueError(f"disparity must have shape {(Hh, Wh)}, got "
+                         f"{np.asarray(disparity).shape}")
+    for name, t in (("d_disparity", d_disparity), ("xw", xw), ("p", p), ("q", q)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.float32 or not t.is_contiguous() or t.numel() < Hh * Wh:
+            raise ValueError(f"{name} must be a contiguous float32 tensor of at least "
+                             f"{Hh * Wh} elements")
+    prm, keep = _params(U, V, H, W, scale, blur, disparity, lambda1, lambda2, mu, nltv_window,
+                        nltv_patch, nltv_h, 0, 0.0, precision, views, weights)
     ptrs = [_ptr(t) for t in (d_disparity, xw, p, q)]
-    if any(k != LFSR_MEM_DEVICE for _, k in ptrs):
-        raise TypeError("d_disparity, xw, p and q must be CUDA tensors")
-    if stream is None:
-        import torch
-        s = torch.cuda.current_stream().cuda_stream
-    else:
-        s = stream if isinstance(stream, int) else stream.cuda_stream
     out = C.c_double(0.0)
     _check(lib.lfsr_apply_normal_noalloc(C.byref(prm), *[a for a, _ in ptrs], C.byref(out),
-                                         C.c_void_p(s)))
+                                         C.c_void_p(_stream(stream))))
+    del keep
     return out.value
 
 

@@ -89,3 +89,24 @@ class Case:
     @staticmethod
     def np(t):
         return t.detach().cpu().numpy().astype(np.float64)
+
+
+def golden(name, seed, n):
+    """The stored FP64 oracle iterate of tests/golden/ for (workload, seed,
+    N), written by tests/golden/make_golden.py, as a dict."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        f"{name}_seed{seed}_n{n}.npz")
+    with np.load(path) as z:
+        return {k: z[k] for k in z.files}
+
+
+def check_golden_inputs(c, g):
+    """The case regenerated the inputs the golden iterate was computed from
+    (float64 checksums; tolerant of last-bit differences of the host's libm,
+    which move the iterate far below the parity tolerances)."""
+    for name, a in (("y", c.y), ("x0", c.x0), ("disp", c.disp), ("blur", c.blur)):
+        a64 = np.asarray(a, np.float64)
+        for key, val in ((f"sum_{name}", a64.sum()), (f"sumsq_{name}", (a64 * a64).sum())):
+            ref = float(g[key])
+            assert abs(val - ref) <= 1e-6 * max(abs(ref), 1.0), (key, val, ref)

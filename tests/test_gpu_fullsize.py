@@ -3,18 +3,18 @@ times (graph-captured lfsr_load + lfsr_iterate on the same plan).
 
 * every operator of one ADMM iteration at full size against the oracle;
 * the first iterations of the 9x9-view x2 and x3 light fields against the
-  oracle, and the whole 100-iteration solve of the 9x9-view x2 light field
-  at its configured h = 0.1 (the x3 one opt-in as slow: minutes of oracle);
+  oracle (x, both dual blocks), the whole 100-iteration solve of the
+  9x9-view x2 light field at its configured h = 0.1 against the oracle run
+  here, and of the x3 light field against the oracle's stored iterate
+  (tests/golden/, written by make_golden.py: minutes of oracle);
 * properties that hold at any N: a constant image stays fixed, duals stay in
   [-1/mu, 1/mu].
 """
-import os
-
 import numpy as np
 import pytest
 
 from paper_2206_05047_gb300 import lfsr, synth
-from tests.gpu_util import Case, f32, max_err, rel_err
+from tests.gpu_util import Case, check_golden_inputs, f32, golden, max_err, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -61,10 +61,12 @@ def test_full_size_first_iterations(full_case):
     lfsr.iterate(c.h, n)
     x = c.empty(*c.oracle.hr)
     wA = c.empty(c.oracle.s_k, c.wl.H, c.wl.W)
-    lfsr.get_state(c.h, x, wA, None)
-    rx, rA, _ = c.oracle.admm(c.y.astype(np.float64), c.x0.astype(np.float64), n)
+    wS = c.empty(c.oracle.s_d, *c.oracle.hr)
+    lfsr.get_state(c.h, x, wA, wS)
+    rx, rA, rS = c.oracle.admm(c.y.astype(np.float64), c.x0.astype(np.float64), n)
     assert rel_err(c.np(x), rx) <= 1e-4
     assert rel_err(c.np(wA), rA) <= 1e-4
+    assert rel_err(c.np(wS), rS) <= 1e-4
 
 
 def test_full_size_constant_image_and_dual_bounds():
@@ -109,7 +111,18 @@ def test_full_size_full_N_lf9x9_256_x2():
     _full_n("lf9x9_256_x2", 2000)
 
 
-@pytest.mark.slow
-@pytest.mark.skipif(os.environ.get("LFSR_SLOW") != "1", reason="set LFSR_SLOW=1 (minutes of oracle)")
 def test_full_size_full_N_lf9x9_200_x3():
-    _full_n("lf9x9_200_x3", 3000)
+    """The x3 task (Sec. 6): 9x9 views, 200^2 -> 600^2, 9x9 blur, all 100
+    iterations, against the oracle's stored float64 iterate."""
+    name, seed = "lf9x9_200_x3", 3000
+    wl = synth.WORKLOADS[name]
+    g = golden(name, seed, wl.iterations)
+    c = Case(wl, seed=seed)
+    check_golden_inputs(c, g)
+    x = c.empty(*c.oracle.hr)
+    lfsr.solve(c.h, c.t(c.y), wl.iterations, c.t(c.x0), x)
+    gx, ref = c.np(x), g["x"]
+    assert rel_err(gx, ref) <= 1e-4
+    assert abs(synth.psnr(gx, c.prob.gt) - float(g["psnr_x"])) <= 0.01
+    assert float(g["psnr_x"]) > float(g["psnr_x0"]) + 3.0
+    c.solver.close()

@@ -1,6 +1,6 @@
 """The continuous-batching server on the GPU: requests admitted while others
-run (at either state parity) give the same result as each solved alone, and
-the device memory returns to zero."""
+run (at either state parity) give the same result as each solved alone and
+match the FP64 oracle, and the device memory returns to zero."""
 import numpy as np
 import pytest
 
@@ -20,6 +20,17 @@ def _requests():
                   disparity=f32(pr.disparity), **SOLVER)
         out.append((pr, kw))
     return out
+
+
+def _oracle_x(pr, kw, n_iter):
+    from oracle import oracle as om
+    o = om.Oracle(kw["U"], kw["V"], kw["H"], kw["W"], kw["scale"],
+                  f32(kw["blur"]).astype(np.float64), f32(kw["disparity"]).astype(np.float64),
+                  lambda1=SOLVER["lambda1"], lambda2=SOLVER["lambda2"], mu=SOLVER["mu"],
+                  window=SOLVER["nltv_window"], patch=SOLVER["nltv_patch"], h=SOLVER["nltv_h"],
+                  cg_iters=SOLVER["cg_iters"], cg_tol=SOLVER["cg_tol"])
+    ref, _, _ = o.admm(f32(pr.y).astype(np.float64), f32(pr.x0).astype(np.float64), n_iter)
+    return ref
 
 
 def test_results_are_the_same_alone_and_in_the_mix():
@@ -45,6 +56,11 @@ def test_results_are_the_same_alone_and_in_the_mix():
         x = np.zeros(pr.wl.HR, np.float32)
         srv.fetch(rid, x)
         assert rel_err(x, _alone(kw, pr, n_iter)) <= 1e-5, rid
+        # requests that joined mid-run (at odd and even state parity) against
+        # the FP64 oracle, at the float32 path's parity tolerance
+        ref = _oracle_x(pr, kw, n_iter)
+        assert rel_err(x, ref) <= 1e-4, rid
+        assert abs(synth.psnr(x, pr.gt) - synth.psnr(ref, pr.gt)) <= 0.01, rid
     srv.close()
 
 

@@ -117,8 +117,43 @@ def test_fixed_point_is_minimiser_of_J(oracle_mod):
     J_qp = o.cost(y, w, res.x[:p].reshape(o.hr))
     x, _, _ = o.admm(y, x0, 1000)
     J_admm = o.cost(y, w, x)
+    # orc_cost against the SLSQP objective, which sums the slacks of the
+    # dense operators' rows (tight at the solution): a wrong lambda, a missing
+    # square or a dropped term of J moves one and not the other
+    assert abs(J_qp - f(res.x)) <= 1e-7 * J_qp
     assert abs(J_admm - J_qp) <= 1e-7 * J_qp
     assert np.abs(x.ravel() - res.x[:p]).max() < 1e-4
+
+
+def test_cost_closed_forms(oracle_mod):
+    """J (Eq. sr_fin) on inputs where each term has a closed form.
+    (a) A constant image has S x = 0; views y_k = A_k c except one LR pixel
+        moved by delta: J = lambda1 |delta| + lambda2 delta^2.
+    (b) Noise-free views of a vertical unit step with every weight 1: the
+        data terms vanish and the regulariser counts the in-image pairs
+        (u, u + d) across the step, (Hh - |d_i|) |d_j| of them for each
+        direction d = (d_i, d_j) of the window (the step far from the
+        borders)."""
+    rng = np.random.default_rng(8)
+    H, W, z = 6, 7, 2
+    l1, l2 = 0.7, 3.0
+    o = oracle_mod.Oracle(3, 3, H, W, z, synth.gaussian_blur_kernel(3, 0.9),
+                          rng.uniform(-0.8, 0.8, (z * H, z * W)), lambda1=l1, lambda2=l2,
+                          window=5)
+    c = np.full(o.hr, 0.3)
+    y = np.stack([o.A(k, c) for k in range(o.s_k)])
+    delta = -0.125
+    y[4, 2, 3] -= delta                     # residual A x - y = +delta there
+    w = rng.random((o.s_d,) + o.hr)         # any weights: S c = 0
+    assert abs(o.cost(y, w, c) - (l1 * abs(delta) + l2 * delta * delta)) <= 1e-12
+    Hh, Wh = o.hr
+    step = np.zeros(o.hr)
+    step[:, Wh // 2:] = 1.0
+    ys = np.stack([o.A(k, step) for k in range(o.s_k)])
+    di, dj = o.dirs()
+    count = sum((Hh - abs(int(a))) * abs(int(b)) for a, b in zip(di, dj))
+    assert o.s_d == 24 and count > 0
+    assert abs(o.cost(ys, np.ones((o.s_d,) + o.hr), step) - count) <= 1e-9 * count
 
 
 def test_diagnostics_and_fixed_K(oracle_mod):
