@@ -74,6 +74,8 @@ def args():
     ap.add_argument("--iterations", type=int, default=None, help="ADMM iterations per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch-record", action="store_true",
+                    help="skip the bounded batched-vs-plain record of the default line")
     ap.add_argument("--precision", default="fp32",
                     choices=["fp32", "fp16", "bf16", "fp16-views32", "bf16-views32"],
                     help="storage type of views, duals and NLTV weights (arithmetic is f32); "
@@ -439,6 +441,7 @@ def run_batch(a):
     if a.warmup >= 1:
         plain_step()
     t_plain = timed(plain_step, a.steps)
+    launches_plain = sum(int(lfsr.stats(sv.handle)["launches"]) for sv in solvers) // n_iter
     value_plain = work * a.steps / (t_plain / 1e3) / 1e6
     xp = plain_x()
     gts = [p[4] for p in probs]
@@ -479,7 +482,7 @@ def run_batch(a):
                        "generation_s": round(t_gen, 1)},
             "plain_serial": {"value": value_plain, "unit": UNIT,
                              "ms_per_step": t_plain / a.steps,
-                             "launches_per_iteration": len(wls) * (3 + 3 * wls[0].cg_iters)},
+                             "launches_per_iteration": launches_plain},
             "batch_vs_plain": value / value_plain,
             "equal_psnr": {"batch_vs_plain": {"max_abs_db": max(abs(d) for d in dpsnr),
                                               "mean_db": float(np.mean(dpsnr)),
@@ -492,6 +495,96 @@ def run_batch(a):
             "gpu_launches": int(a.steps * n_iter * launches),
             "launches_per_iteration": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
+
+
+def batch_subrecord(dev, stream, n_lf: int = 16, n_iter: int = 10, steps: int = 3,
+                    warmup: int = 1):
+    """Bounded batched-vs-plain record for the default line: the first n_lf
+    light fields of the batched configuration (seed 4000), n_iter ADMM
+    iterations per step, one autotuned batch (one launch per phase and
+    operator group, graph-replayed) against the same light fields solved
+    one after another by the plain path, in float32 and in 16-bit (fp16)
+    storage, with the PSNR of every light field compared between the two."""
+    import torch
+    from paper_2206_05047_gb300 import lfsr
+    t_gen = time.perf_counter()
+    wls, probs = batch_problems(n_lf)
+    t_gen = time.perf_counter() - t_gen
+    y_d = [torch.from_numpy(p[0]).to(dev) for p in probs]
+    x0_d = [torch.from_numpy(p[1]).to(dev) for p in probs]
+    gts = [p[4] for p in probs]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    work = sum(w.s_k * w.HR[0] * w.HR[1] for w in wls) * n_iter
+
+    def timed(step):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        total = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        return total
+
+    def xs_of(get, hrs):
+        out = []
+        for j, hr in enumerate(hrs):
+            x = torch.empty(hr, dtype=torch.float32, device=dev)
+            get(j, x)
+            out.append(x.cpu().numpy().astype(np.float64))
+        return out
+
+    rec = {"workload": f"first {n_lf} light fields of {BATCH_WORKLOAD} (seed 4000)",
+           "iterations": n_iter, "steps": steps,
+           "hr_lf_mpix_per_iteration": work / n_iter / 1e6,
+           "generation_s": round(t_gen, 1)}
+    for prec in ("fp32", "fp16"):
+        kws = [dict(U=w.U, V=w.V, H=w.H, W=w.W, scale=w.scale, blur=p[2], disparity=p[3],
+                    lambda1=w.lambda1, lambda2=w.lambda2, mu=w.mu, nltv_window=w.window,
+                    nltv_patch=w.patch, nltv_h=w.h, cg_iters=w.cg_iters, cg_tol=0.0,
+                    precision=prec) for w, p in zip(wls, probs)]
+        batch = lfsr.Batch(kws, stream=stream)
+        for j in range(len(wls)):
+            batch.load(j, y_d[j], x0_d[j])
+        tuning = batch.autotune()
+
+        def batch_step():
+            for j in range(len(wls)):
+                batch.load(j, y_d[j], x0_d[j])
+            batch.iterate(n_iter)
+        t_b = timed(batch_step)
+        xb = xs_of(batch.get_x, [w.HR for w in wls])
+        launches_b = batch.launches_per_iteration()
+        batch.close()
+        solvers = [lfsr.Solver(stream=stream, **kw) for kw in kws]
+
+        def plain_step():
+            for j, sv in enumerate(solvers):
+                lfsr.load(sv.handle, y_d[j], x0_d[j])
+                lfsr.iterate(sv.handle, n_iter)
+        t_p = timed(plain_step)
+        launches_p = sum(int(lfsr.stats(sv.handle)["launches"]) for sv in solvers) // n_iter
+        xp = xs_of(lambda j, x: lfsr.get_x(solvers[j].handle, x), [w.HR for w in wls])
+        for sv in solvers:
+            sv.close()
+        dps = [synth.psnr(xb[j], gts[j]) - synth.psnr(xp[j], gts[j]) for j in range(len(wls))]
+        vb = work * steps / (t_b / 1e3) / 1e6
+        vp = work * steps / (t_p / 1e3) / 1e6
+        rec[prec] = {"batch": vb, "plain_serial": vp, "batch_vs_plain": vb / vp,
+                     "unit": UNIT, "launches_per_iteration": {
+                         "batch": launches_b, "plain_serial": launches_p},
+                     "max_abs_dpsnr_db": max(abs(d) for d in dps),
+                     "mean_psnr_db": float(np.mean([synth.psnr(xb[j], gts[j])
+                                                    for j in range(len(wls))])),
+                     "autotuned": tuning}
+    del flush
+    return rec
 
 
 # --------------------------------------------------------------------------
@@ -721,6 +814,8 @@ def main():
     work = wl.s_k * p * n_iter * a.steps * world
     value = work / (t_ms / 1e3) / 1e6
 
+    # kernel launches of one solve (the library counts them since the load)
+    launches_per_solve = int(lfsr.stats(h)["launches"])
     # output sanity: finite, and better than the bicubic start
     lfsr.get_x(h, x_d)
     xs = x_d.cpu().numpy().astype(np.float64)
@@ -763,7 +858,8 @@ def main():
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_clk * 1e6 / 1e12
     achieved = flops / (avg_ms / 1e3) / 1e12
     traffic = traffic_from_profile(wl)
-    roofline = {"bound": "alu", "kernel": "k_operator_fast<OP_NORMAL> (sum_k A_k^T A_k p)",
+    roofline = {"bound": "alu",
+                "kernel": "k_operator_fast<OP_NORMAL> (sum_k A_k^T A_k p; with the fused CG update)",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "avg_launch_ms": avg_ms, "flops_per_launch": flops,
@@ -790,6 +886,10 @@ def main():
                "sample": f"{iters} ADMM iterations (K = {wl.cg_iters}) of {wl.name} from x0, "
                          f"{dt:.1f} s"}
 
+    batch_rec = None
+    if rank == 0 and world == 1 and not a.no_batch_record and a.workload == "lf9x9_256_x2":
+        batch_rec = batch_subrecord(dev, stream)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_ms / a.steps,
@@ -815,7 +915,9 @@ def main():
                 "sai_rate": {"value": p * n_iter * a.steps * world / (t_ms / 1e3) / 1e6,
                              "unit": "HR Mpix*iter/s (reference view)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(a.steps * n_iter * (3 + 3 * wl.cg_iters)),
+                "batched": batch_rec,
+                "gpu_launches": int(a.steps * launches_per_solve),
+                "launches_per_iteration": launches_per_solve / max(n_iter, 1),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     solver.close()

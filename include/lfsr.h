@@ -66,6 +66,11 @@ extern "C" {
 #define LFSR_MEM_HOST   0
 #define LFSR_MEM_DEVICE 1
 
+/* Default limit of a device-side wait (a grid barrier of the fused CG
+ * step), in nanoseconds: after it the wait gives up and the call reports
+ * LFSR_ETIMEOUT (see lfsr_set_device_wait). */
+#define LFSR_DEFAULT_WAIT_NS 1000000000LL
+
 /* Precision of the solver state (lfsr_params.precision).
  *
  * LFSR_FP32: all state and arithmetic in float32.
@@ -276,6 +281,33 @@ int lfsr_apply_normal(lfsr_handle *h, const float *xw, const float *p, float *q,
  * kernel time.  Off by default. */
 int lfsr_set_profiling(lfsr_handle *h, int on);
 
+/* Host-side fault injection (for testing the failure paths; no device
+ * fault is involved).  The environment variable LFSR_FAULT, read at every
+ * device allocation the library makes (lfsr_create, lfsr_batch_create,
+ * server admission, staging buffers):
+ *   LFSR_FAULT=alloc     every allocation fails,
+ *   LFSR_FAULT=alloc:K   the K-th allocation fails (K >= 1, counted from
+ *                        the moment the variable took this value),
+ * as if cudaMalloc had returned cudaErrorMemoryAllocation: the call frees
+ * what it holds and returns LFSR_ENOMEM.  A dry-run server counts each
+ * admission as one allocation.  Unset (or any other value): no fault. */
+
+/* Device-side waits.  With the specialised operator kernel (separable
+ * blur, common scale and blur size) each CG step of the x-step (Algorithm
+ * 2) is one cooperative launch: the normal-matrix product, then a grid
+ * barrier, the step length alpha = pi / <p, M p>, the updates x += alpha p
+ * and r -= alpha q with their <r, r>, a second grid barrier and beta.  No
+ * barrier waits without a bound: after limit_ns nanoseconds (default
+ * LFSR_DEFAULT_WAIT_NS) a waiting CTA gives up, the CG step is abandoned
+ * and the next blocking call returns LFSR_ETIMEOUT; the device context stays
+ * usable and the next lfsr_load / lfsr_solve starts clean.  test_unreachable
+ * != 0 makes every barrier wait for one arrival more than the launch has,
+ * so that every wait runs out (a test of the timeout path; the solve then
+ * fails with LFSR_ETIMEOUT).  The setting applies from the next iteration
+ * (the captured graphs are rebuilt); the call synchronises the handle's
+ * stream. */
+int lfsr_set_device_wait(lfsr_handle *h, int64_t limit_ns, int test_unreachable);
+
 /* ---- batches of light fields ------------------------------------------
  *
  * A batch steps many light fields -- of different angular grids, LR sizes,
@@ -377,14 +409,21 @@ int64_t lfsr_estimate_state_bytes(const lfsr_params *params);
  * `iterations`-th iteration: its result is copied to host memory and its
  * device state freed.  Every result equals the request's own lfsr_solve up
  * to the order of float atomic additions.  Requests must share the solver
- * constants (as in a batch).  Single-threaded use. */
+ * constants (as in a batch).  A request can be cancelled at any time
+ * (lfsr_server_cancel); one that fails (its admission could not allocate,
+ * LFSR_ENOMEM; a kernel it needs is missing, LFSR_EUNSUPPORTED) frees its
+ * slot and budget and the requests around it continue unchanged.  The entry
+ * points of one server may be called from several host threads: each call
+ * holds the server's lock (a step holds it while the GPU runs its
+ * iterations). */
 #define LFSR_SERVER_DRY_RUN 1   /* flags: schedule without a device (checks) */
 
-#define LFSR_REQ_QUEUED  0
-#define LFSR_REQ_ACTIVE  1
-#define LFSR_REQ_DONE    2
-#define LFSR_REQ_FETCHED 3
-#define LFSR_REQ_FAILED  4
+#define LFSR_REQ_QUEUED    0
+#define LFSR_REQ_ACTIVE    1
+#define LFSR_REQ_DONE      2
+#define LFSR_REQ_FETCHED   3
+#define LFSR_REQ_FAILED    4
+#define LFSR_REQ_CANCELLED 5
 
 typedef struct lfsr_server lfsr_server;
 
@@ -405,6 +444,7 @@ typedef struct lfsr_server_stats_t {
   int64_t batch_rebuilds;      /* launch-structure rebuilds (active set changed) */
   int64_t admitted, retired;
   int64_t launches;            /* kernel launches of the batch iterations    */
+  int64_t cancelled;           /* requests cancelled (queued, active or done) */
 } lfsr_server_stats_t;
 
 /* Creates a server; work is ordered on cuda_stream.  No device call. */
@@ -436,6 +476,15 @@ int lfsr_server_status(const lfsr_server *s, int64_t id, int *state, int *iterat
 int lfsr_server_fetch(lfsr_server *s, int64_t id, float *x_out, int mem_kind);
 
 int lfsr_server_stats(const lfsr_server *s, lfsr_server_stats_t *out);
+
+/* Cancels request id: a queued one leaves the queue (the requests behind it
+ * may be admitted at the next step), an active one leaves the active set
+ * at once (its device state, slot and budget are freed; the others are
+ * rebuilt into the next step's launches and continue from their state), a
+ * done one drops its result.  The request's state becomes
+ * LFSR_REQ_CANCELLED.  Returns LFSR_EINVAL for an unknown id or a request
+ * already fetched, failed or cancelled. */
+int lfsr_server_cancel(lfsr_server *s, int64_t id);
 
 /* ---- no-allocation variant ------------------------------------------
  *

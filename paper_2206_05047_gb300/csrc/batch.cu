@@ -163,7 +163,7 @@ cudaError_t batch_iteration(lfsr_batch* b, int pa, cudaStream_t s, std::vector<P
   }
   if (e == cudaSuccess)
     e = run(KD_INIT, 0, [&] {
-      return cg_init_nltv_launch(
+      return cg_init_acc_launch(
           b->g, table(b, b->t_init[pa], n, b->vec_total, b->m_vec, KD_INIT, ctr(KD_INIT, G), 0),
           s);
     });
@@ -299,7 +299,7 @@ cudaError_t build_tables(lfsr_batch* b) {
     if (*buf) cudaFree(*buf);
     *buf = nullptr;
     *cap = 0;
-    e = cudaMalloc((void**)buf, need * elem);
+    e = fault_alloc() ? cudaErrorMemoryAllocation : cudaMalloc((void**)buf, need * elem);
     if (e == cudaSuccess) *cap = need;
   };
   grow(&b->tables, &b->cap_tables, tabs.size(), sizeof(JobArgs));
@@ -420,7 +420,8 @@ cudaError_t lfsr::batch_assign(lfsr_batch* b, const std::vector<lfsr_handle*>& j
     if (b->counters) cudaFree(b->counters);
     b->counters = nullptr;
     b->cap_counters = 0;
-    e = cudaMalloc((void**)&b->counters, n_counters * sizeof(unsigned int));
+    e = fault_alloc() ? cudaErrorMemoryAllocation
+                      : cudaMalloc((void**)&b->counters, n_counters * sizeof(unsigned int));
     if (e == cudaSuccess) {
       b->cap_counters = n_counters;
       e = cudaMemsetAsync(b->counters, 0, n_counters * sizeof(unsigned int), b->stream);

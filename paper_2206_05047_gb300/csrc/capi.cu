@@ -2,6 +2,8 @@
 // schedule (Algorithm 1 with the CG x-step of Algorithm 2) and its CUDA-graph
 // replay.  See include/lfsr.h for the contract of every entry point.
 #include <cmath>
+#include <cstdlib>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -55,7 +57,7 @@ void free_all(lfsr_handle* h) {
     cudaEventDestroy(ev.b);
   }
   void* bufs[] = {h->disp, h->y, h->x[0], h->x[1], h->wA[0], h->wA[1], h->wS[0],
-                  h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt, h->cb, h->occ,
+                  h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt, h->V, h->occ,
                   h->disp_views, h->hlr};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -70,6 +72,7 @@ void free_all(lfsr_handle* h) {
 
 template <class T>
 cudaError_t dalloc(lfsr_handle* h, T** p, size_t n) {
+  if (fault_alloc()) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
   if (e == cudaSuccess) h->state_bytes += (int64_t)(n * sizeof(T));
   return e;
@@ -77,6 +80,7 @@ cudaError_t dalloc(lfsr_handle* h, T** p, size_t n) {
 
 cudaError_t dalloc_st(lfsr_handle* h, void** p, size_t n, size_t esize) {
   const size_t bytes = n * esize;
+  if (fault_alloc()) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 16);
   if (e == cudaSuccess) h->state_bytes += (int64_t)bytes;
   return e;
@@ -172,6 +176,9 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
   const int nb = 1 - b;
   const Geom& g = h->g;
   DevScalars* sc = h->sc;
+  // v: accumulated in V (zero at entry) on the stored-weight NLTV path, else
+  // stored by the generic NLTV block into R
+  float* const vbuf = h->nlf ? h->V : h->R;
   cudaError_t e;
   // regulariser rows: weights from x^(n-1), z/w-step, v := mu/2 S^T f
   e = timed(h, s, KD_NLW, [&] {
@@ -195,7 +202,7 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
     OpArgs od{};
     od.src = h->x[b];
     set_warp_maps(h, &od);
-    od.out = g.adjoint_bw ? h->hlr : h->R;
+    od.out = g.adjoint_bw ? h->hlr : vbuf;
     od.y = h->y;
     od.wA_old = h->wA[b];
     od.wA_new = h->wA[nb];
@@ -214,7 +221,7 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
       OpArgs ob{};
       ob.src = h->hlr;
       ob.disp = h->disp;
-      ob.out = h->R;
+      ob.out = vbuf;
       ob.scale = 1.f;
       ob.view0 = 0;
       ob.nviews = g.sk;
@@ -223,12 +230,15 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
     });
     if (e != cudaSuccess) return e;
   }
-  // x-step (Algorithm 2): r = -v, x' = x, pi = <r, r>
-  e = timed(h, s, KD_INIT, [&] {
-    const TableArgs t = handle_table(h, KD_INIT, b, 0);
-    return h->nlf ? cg_init_nltv_launch(g, t, s) : cg_init_launch(g, t, s);
-  });
-  if (e != cudaSuccess) return e;
+  // x-step (Algorithm 2): r = -v, x' = x, pi = <r, r> (part of the data
+  // launch when fused)
+  if (!h->fused_init) {
+    e = timed(h, s, KD_INIT, [&] {
+      const TableArgs t = handle_table(h, KD_INIT, b, 0);
+      return h->nlf ? cg_init_acc_launch(g, t, s) : cg_init_launch(g, t, s);
+    });
+    if (e != cudaSuccess) return e;
+  }
   for (int k = 0; k < h->prm.cg_iters; ++k) {
     const int pb = k & 1;
     e = timed(h, s, KD_NLA, [&] {
@@ -266,6 +276,7 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
       return op_launch(OP_NORMAL, g, h->op, on, h->grid_op, s);
     });
     if (e != cudaSuccess) return e;
+    if (h->fused) continue;   // the normal-matrix launch finished the CG step
     e = timed(h, s, KD_UPDATE,
               [&] { return cg_update_launch(g, handle_table(h, KD_UPDATE, b, pb), s); });
     if (e != cudaSuccess) return e;
@@ -276,7 +287,9 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
 int launches_per_iteration(const lfsr_handle* h) {
   // the backward warp adds its gather launch to the data block and each CG step
   const int bw = h->g.adjoint_bw ? 1 : 0;
-  return 3 + bw + (3 + bw) * h->prm.cg_iters;
+  const int upd = h->fused ? 0 : 1;   // the fused normal-matrix launch holds the CG update
+  const int init = h->fused_init ? 0 : 1;   // the fused data launch holds the initialisation
+  return 2 + init + bw + (2 + upd + bw) * h->prm.cg_iters;
 }
 
 cudaError_t build_graph(lfsr_handle* h, int first_parity, int n, cudaGraphExec_t* out) {
@@ -493,6 +506,8 @@ int lfsr::geom_from_params(const lfsr_params* pr, Geom* out) {
     g.st = base == LFSR_FP16_STORAGE ? ST_F16 : base == LFSR_BF16_STORAGE ? ST_BF16 : ST_F32;
     g.st_y = (pr->precision & LFSR_KEEP_VIEWS_FP32) ? ST_F32 : g.st;
   }
+  g.wait_ns = LFSR_DEFAULT_WAIT_NS;
+  g.wait_unreachable = 0;
   return LFSR_OK;
 }
 
@@ -502,6 +517,25 @@ int lfsr::shift_bound(double max_abs_disparity, int U, int V) {
 }
 
 void lfsr::set_thread_error(const char* msg) { t_err = msg; }
+
+bool lfsr::fault_alloc() {
+  static std::mutex mu;
+  static std::string spec;
+  static long long count = 0;
+  const char* env = std::getenv("LFSR_FAULT");
+  const std::string cur = env ? env : "";
+  std::lock_guard<std::mutex> lock(mu);
+  if (cur != spec) {   // a new setting starts a new count
+    spec = cur;
+    count = 0;
+  }
+  if (cur.compare(0, 5, "alloc") != 0) return false;
+  if (cur.size() == 5) return true;
+  if (cur[5] != ':') return false;
+  const long long k = std::atoll(cur.c_str() + 6);
+  ++count;
+  return k >= 1 && count == k;
+}
 
 int lfsr::handle_fail(lfsr_handle* h, int code, const std::string& msg) { return fail(h, code, msg); }
 int lfsr::handle_cuda_fail(lfsr_handle* h, cudaError_t e, const char* what) {
@@ -525,7 +559,7 @@ int64_t lfsr::estimate_state_bytes(const lfsr_params* pr) {
               + 2 * es * nA      // data duals
               + 2 * es * nS      // regulariser duals
               + 4 * 4 * p;       // P ping-pong, R, Q
-  if (nlf) b += es * sh * p + 4 * sh * p;   // stored weights, divergence terms
+  if (nlf) b += es * sh * p + 4 * p;       // stored weights, accumulated v
   if (paper) b += 4 * p;                    // occlusion factor
   if (pr->disparity_views) b += 4 * sk * p;  // per-view disparity maps
   if (pr->adjoint == LFSR_ADJOINT_BACKWARD_WARP) b += 4 * nA;   // LR buffer
@@ -574,14 +608,13 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
   j.occ = h->occ;
   j.sc = h->sc;
   switch (kind) {
-    case KD_NLW:   // weights from x^(n-1), regulariser z/w-step, v := 0
+    case KD_NLW:   // weights from x^(n-1), regulariser z/w-step, v += mu/2 S^T f
       j.tiles_x = h->nl_tiles_x;
       j.src = h->x[b];
-      j.out = h->R;
+      j.out = h->V;
       j.wS_old = h->wS[b];
       j.wS_new = h->wS[nb];
       j.wt = h->wt;
-      j.cb = h->cb;
       break;
     case KD_DATA:  // data rows, v += A^T (...)
       j.tiles_x = h->op.tiles_x;
@@ -589,15 +622,23 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
       j.nviews = g.sk;
       j.scale = 1.f;
       j.src = h->x[b];
-      j.out = h->R;
+      j.out = h->nlf ? h->V : h->R;
       j.y = h->y;
       j.wA_old = h->wA[b];
       j.wA_new = h->wA[nb];
+      if (h->fused_init) {  // ... then r = -v, v := 0, x' = x, pi (fused initialisation)
+        j.fuse = 1;
+        j.fchunk = h->fchunk;
+        j.fpart = h->partials + (size_t)RED_PI * h->max_grid;
+        j.vacc = h->V;
+        j.rr = h->R;
+        j.x_next = h->x[nb];
+      }
       break;
-    case KD_INIT:  // r = -(v + regulariser divergence), x' = x
+    case KD_INIT:  // r = -v (v := 0 when accumulated), x' = x
       j.chunk = h->vec_chunk;
       j.out = h->R;
-      j.cb = h->cb;
+      j.vacc = h->V;
       j.src = h->x[b];
       j.x_next = h->x[nb];
       break;
@@ -617,6 +658,15 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
       j.scale = g.cA;
       j.src = h->P[pb];
       j.out = h->Q;
+      if (h->fused) {  // ... then x += alpha p, r -= alpha q, pi', beta (fused CG step)
+        j.fuse = 1;
+        j.fchunk = h->fchunk;
+        j.fpart = h->partials + (size_t)RED_PI * h->max_grid;
+        j.p_old = h->P[pb];
+        j.q = h->Q;
+        j.rr = h->R;
+        j.x_next = h->x[nb];
+      }
       break;
     default:       // KD_UPDATE: x += alpha p, r -= alpha q
       j.chunk = h->upd_chunk;
@@ -715,6 +765,10 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
     if (uc < 256) uc = 256;
     h->upd_chunk = (int)uc;
     h->upd_units = (int)((p + uc - 1) / uc);
+    // the fused tails of the operator launches: grid_op CTAs cover the image
+    size_t fc = (p + (size_t)h->grid_op - 1) / (size_t)h->grid_op;
+    fc = (fc + 31) / 32 * 32;
+    h->fchunk = (int)fc;
   }
   h->max_grid = h->grid_op;
   if (h->nl.n_tiles > h->max_grid) h->max_grid = h->nl.n_tiles;
@@ -737,8 +791,16 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   if (e == cudaSuccess) e = dalloc(h, &h->R, p);
   if (e == cudaSuccess) e = dalloc(h, &h->Q, p);
   h->nlf = nlf_supported(g);
+  // the specialised operator kernel finishes each CG step itself (grid
+  // barriers in a cooperative launch); the generic path keeps the separate
+  // CG update launch
+  h->fused = h->op.fast != 0;
+  // ... and the data block the x-step initialisation, when v accumulates in
+  // V (stored-weight NLTV path)
+  h->fused_init = h->fused && h->nlf;
   if (e == cudaSuccess && h->nlf) e = dalloc_st(h, &h->wt, (size_t)g.sh * p, h->esize);
-  if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->cb, (size_t)g.sh * p);
+  if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->V, p);
+  if (e == cudaSuccess && h->nlf) e = cudaMemsetAsync(h->V, 0, p * sizeof(float), h->stream);
   if (e == cudaSuccess && g.wscheme == WS_PAPER) e = dalloc(h, &h->occ, p);
   if (e == cudaSuccess && g.warp_views) e = dalloc(h, &h->disp_views, (size_t)g.sk * p);
   if (e == cudaSuccess && g.adjoint_bw) e = dalloc(h, &h->hlr, h->nA);
@@ -829,6 +891,7 @@ int lfsr::load_state(lfsr_handle* h, const float* lr_views, const float* x0, int
   CK(h, to_dev(h, h->x[b], x0, h->p, mem), "upload x0");
   CK(h, cudaMemsetAsync(h->wA[b], 0, h->nA * h->esize, h->stream), "clear data duals");
   CK(h, cudaMemsetAsync(h->wS[b], 0, h->nSpair * h->esize, h->stream), "clear NLTV duals");
+  if (h->V) CK(h, cudaMemsetAsync(h->V, 0, h->p * sizeof(float), h->stream), "clear v");
   h->parity = b;
   h->iters = 0;
   h->launches = 0;
@@ -871,6 +934,9 @@ static int read_status(lfsr_handle* h, DevScalars* hs) {
   CK(h, cudaStreamSynchronize(h->stream), "synchronize");
   if (hs->status == LFSR_EINVAL)
     return fail(h, LFSR_EINVAL, "a view or data-dual value given to the solver is not finite or outside the storage type's range");
+  if (hs->status == LFSR_ETIMEOUT)
+    return fail(h, LFSR_ETIMEOUT,
+                "a grid barrier of the fused CG step gave up waiting (device wait limit reached)");
   if (hs->status != 0)
     return fail(h, hs->status, "non-finite or negative curvature in the CG x-step");
   return LFSR_OK;
@@ -929,6 +995,22 @@ int lfsr_stats(const lfsr_handle* hc, lfsr_stats_t* out) {
 int64_t lfsr_estimate_state_bytes(const lfsr_params* params) {
   if (validate(params) != LFSR_OK) return -1;
   return estimate_state_bytes(params);
+}
+
+int lfsr_set_device_wait(lfsr_handle* h, int64_t limit_ns, int test_unreachable) {
+  if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
+  if (limit_ns < 0) return fail(h, LFSR_EINVAL, "limit_ns must be >= 0");
+  CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  h->g.wait_ns = (unsigned long long)limit_ns;
+  h->g.wait_unreachable = test_unreachable ? 1 : 0;
+  // the captured iterations hold the old limit: capture again on next use
+  if (h->graph_pair) cudaGraphExecDestroy(h->graph_pair);
+  h->graph_pair = nullptr;
+  for (auto& gs : h->graph_single) {
+    if (gs) cudaGraphExecDestroy(gs);
+    gs = nullptr;
+  }
+  return LFSR_OK;
 }
 
 int lfsr_set_profiling(lfsr_handle* h, int on) {

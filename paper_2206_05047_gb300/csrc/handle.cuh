@@ -46,7 +46,8 @@ struct lfsr_handle {
   float* R = nullptr;   // v, then the CG residual r
   float* P[2] = {nullptr, nullptr};
   float* Q = nullptr;
-  float* cb = nullptr;  // per-edge divergence terms of the z/w-step [s_d/2][p]
+  float* V = nullptr;   // accumulated v of the z/w-step (stored-weight NLTV path; zero
+                        // between iterations: the x-step initialisation clears it)
   // streams in the storage kind g.st (float, half or bfloat16), esize bytes
   // each; the views in kind g.st_y (esize_y bytes)
   size_t esize = 4, esize_y = 4;
@@ -55,6 +56,8 @@ struct lfsr_handle {
   void* wS[2] = {nullptr, nullptr};
   void* wt = nullptr;   // stored NLTV edge weights [s_d/2][p] (when supported)
   bool nlf = false;
+  bool fused = false;   // the normal-matrix launch finishes each CG step (no update launch)
+  bool fused_init = false;   // the data launch does the x-step initialisation (no init launch)
   float* io = nullptr;  // staging for host <-> device and layout conversion
   size_t io_floats = 0;
   double* partials = nullptr;
@@ -77,6 +80,7 @@ struct lfsr_handle {
   int op_units = 0;                         // (64 x 64 tile, view pair) units
   int vec_chunk = 0, vec_units = 0;         // HR pixels per vector-kernel CTA, CTAs
   int upd_chunk = 0, upd_units = 0;         // the same for the CG update (one CTA per SM)
+  int fchunk = 0;                           // HR pixels per CTA of the fused operator tails
   bool profiling = false;
   std::vector<lfsr::ProfEvent> prof;
   double prof_ms[8] = {0};
@@ -113,6 +117,9 @@ int geom_from_params(const lfsr_params* params, Geom* g);
 // Integer bound S on |theta_k * omega| over a U x V grid (the halo of the
 // warp) for a disparity map whose largest magnitude is max_abs_disparity.
 int shift_bound(double max_abs_disparity, int U, int V);
+// Host-side allocation-fault injection (LFSR_FAULT=alloc or alloc:K, see
+// lfsr.h): true when the library's next device allocation is to fail.
+bool fault_alloc();
 // Records an error on h (and the thread) and returns code.
 int handle_fail(lfsr_handle* h, int code, const std::string& msg);
 int handle_cuda_fail(lfsr_handle* h, cudaError_t e, const char* what);

@@ -211,6 +211,53 @@ __device__ __forceinline__ void cg_init_finalize(const Geom& g, const TableArgs&
   }
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a launch whose CTAs are all resident (a cooperative
+// launch of at most the co-resident CTA count).  *arrivals counts every
+// CTA's arrival at every barrier, monotonically across the launches that
+// share it (all with the same grid size; reset to 0 when a solve loads):
+// the CTA that arrives as number a waits until the count reaches the end of
+// its generation, G (a / G + 1).  The wait is bounded: after g.wait_ns of
+// %globaltimer it gives up and returns false (the caller records
+// LFSR_ETIMEOUT).  The arrival is counted either way, so the barriers after
+// a failed one keep their alignment.  Every thread of the CTA must call it;
+// the result is block-uniform.  Memory: the writes of every CTA before the
+// barrier are visible to every CTA after it (fences on both sides).
+__device__ __forceinline__ bool grid_barrier(unsigned long long* arrivals, const Geom& g) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long G = gridDim.x;
+    const unsigned long long a = atomicAdd(arrivals, 1ull);
+    const unsigned long long target = (a / G + 1ull) * G + (g.wait_unreachable ? 1ull : 0ull);
+    const unsigned long long t0 = global_ns();
+    int ok = 1;
+    while (ld_acquire_u64(arrivals) < target) {
+      if (global_ns() - t0 >= g.wait_ns) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // Table entry of work unit u.
 __device__ __forceinline__ int table_job(const TableArgs& t, int u) {
   return t.unit_job ? __ldg(t.unit_job + u) : 0;

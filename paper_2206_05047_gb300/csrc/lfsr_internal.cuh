@@ -41,6 +41,8 @@ struct Geom {
   float inv_sig_e;       // paper weights: 1 / sigma_e (0: edge factor 1)
   int warp_views;        // W_k uses per-view disparity maps (generic operator kernel)
   int adjoint_bw;        // x-step uses the backward warp W_k^* (generic operator kernel)
+  unsigned long long wait_ns;  // limit of a device-side wait (grid barrier), ns of %globaltimer
+  int wait_unreachable;  // test mode: every wait's target lies beyond the arrivals (runs out)
   float kv[LFSR_MAX_KB], kh[LFSR_MAX_KB];
   float k2[LFSR_MAX_KB * LFSR_MAX_KB];
   float tu[LFSR_MAX_VIEWS], tv[LFSR_MAX_VIEWS];
@@ -61,6 +63,7 @@ struct DevScalars {
   int status;       // sticky LFSR_* status
   unsigned int counter[8];   // last-block counters of the grid reductions
   double red[8];    // finalized totals of the grid reductions (RED_* slots)
+  unsigned long long bar;    // arrivals at the grid barriers of the fused launches
 };
 
 // Reduction slots (partials arrays and last-block counters).
@@ -146,7 +149,9 @@ struct JobArgs {
   const void* wS_old;         // NLTV block: regulariser duals, pair layout (kind g.st)
   void* wS_new;
   void* wt;                   // NLTV: stored edge weights (kind g.st)
-  float* cb;                  // NLTV block -> vector init: per-edge divergence terms
+  float* vacc;                // accumulated v of the z/w-step (stored-weight NLTV block and
+                              // data block add into it; the x-step initialisation reads and
+                              // clears it)
   const float* occ;           // NLTV (paper weights): occlusion factor o (HR)
   const float* r;             // NLTV apply: CG residual
   const float* p_old;         // NLTV apply: previous direction; vector update: p
@@ -155,6 +160,13 @@ struct JobArgs {
   float* rr;                  // vector update: residual r, updated in place
   float* x_next;              // vector: iterate of the x-step
   DevScalars* sc;             // this light field's device scalars
+  // Fused launches (one light field, fields by value): the normal-matrix
+  // operator finishes the CG step behind a grid barrier (x' += alpha p,
+  // r -= alpha q, pi' = <r, r>, beta), its CTAs each taking fchunk HR
+  // pixels; fpart holds their partial sums of <r, r>.
+  int fuse;
+  int fchunk;
+  double* fpart;
 };
 
 // Launch-wide arguments of a table-driven kernel.
@@ -200,14 +212,16 @@ cudaError_t nl_plan(const Geom& g, NlPlan* plan, int smem_limit);
 // NLTV with stored edge weights (window radius 1-3, patch radius 0-2).
 bool nlf_supported(const Geom& g);
 // Table-driven: one CTA per 32 x 32 tile (t.total_units tiles); wt holds
-// s_d/2 x p values of the storage kind g.st, cb s_d/2 x p floats.
+// s_d/2 x p values of the storage kind g.st; the block mode adds the
+// regulariser divergence into the jobs' v (out), which must start at zero.
 constexpr int NLF_TILE = 32;
 cudaError_t weights_to_canonical(const Geom& g, const void* wt, float* can, cudaStream_t s);
 cudaError_t nlw2_launch(int block, const Geom& g, const TableArgs& t, cudaStream_t s);
 // chunk: directions per batch of weight loads, 6 (default) or 3.
 constexpr int NLA_CHUNK = 6;
 cudaError_t nla2_launch(const Geom& g, const TableArgs& t, cudaStream_t s, int chunk = NLA_CHUNK);
-cudaError_t cg_init_nltv_launch(const Geom& g, const TableArgs& t, cudaStream_t s);
+// x-step initialisation from the accumulated v (jobs' vacc): r = -v, v := 0.
+cudaError_t cg_init_acc_launch(const Geom& g, const TableArgs& t, cudaStream_t s);
 // The paper's weights (g.wscheme == WS_PAPER): the stored-weight
 // z/w-step (called by nlw2_launch), and the occlusion factor
 // o = exp(-b^2 inv2_o1) exp(-pe^2 inv2_o2) of the disparity map disp and the

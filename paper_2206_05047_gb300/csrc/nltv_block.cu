@@ -4,18 +4,20 @@
 // in the half window: s_d/2 x p values, written once per ADMM iteration and
 // read by the K CG steps in nltv_fast.cu while they sit in L2).  Duals and
 // weights are kept in the storage type ST (float, half or bfloat16); the
-// per-edge divergence terms c (an intermediate read once, by the x-step
-// initialisation) and all arithmetic are float.
+// regulariser's divergence (mu/2) S^T f goes straight into the accumulated v
+// (DivAcc) and all arithmetic is float.
 #include "nltv_fast.cuh"
 
 namespace lfsr {
 
 // k_nlw2<BLOCK>: per owned pixel u and direction d: the edge weight
 //   w(u, u+d) from the staged (clamped) x, stored in wt[idx][u]; the two
-//   duals of the edge updated; c(u, d) = w (f_a - f_b) stored in cb[idx][u];
-//   v(u) := 0 (the data block accumulates into v next, the divergence of c
-//   is added by k_cg_init_nltv).  Patch sums of the strip share rows: the
-//   4 + 2 PR row sums of squared differences give all 4 patch distances.
+//   duals of the edge updated; c(u, d) = (mu/2) w (f_a - f_b) added to v(u)
+//   and subtracted from v(u+d) (v, zero before the launch, is the light
+//   field's accumulated v: the data block adds its part next and the x-step
+//   initialisation reads and clears it).  Patch sums of the strip share
+//   rows: the 4 + 2 PR row sums of squared differences give all 4 patch
+//   distances.
 // k_nlw2<ONLY>: the weights alone.
 template <int MODE, int WR, int PR, class ST>
 __global__ void __launch_bounds__(NF_THREADS)
@@ -23,7 +25,9 @@ k_nlw2(const Geom g, const TableArgs tb) {
   using D = HalfDirs<WR>;
   constexpr int T = NF_T, HX = WR + PR, NX = T + 2 * HX, NXp = NX | 1;
   constexpr int PW = 2 * PR + 1, NS = NF_PIX + 2 * PR;
+  using DA = DivAcc<WR>;
   __shared__ float sX[NX * NXp];
+  __shared__ float sV[MODE == NLW_BLOCK ? DA::SIZE : 1];
   __shared__ double s_red[NF_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // this CTA's tile: unit blockIdx.x of the table
@@ -34,7 +38,6 @@ k_nlw2(const Geom g, const TableArgs tb) {
   const ST* __restrict__ wS_old = (const ST*)jp->wS_old;
   ST* __restrict__ wS_new = (ST*)jp->wS_new;
   ST* __restrict__ wt = (ST*)jp->wt;
-  float* __restrict__ cb = jp->cb;
   const size_t p = (size_t)Hh * Wh;
   const int tile = blockIdx.x - jp->unit0;
   const int ty = tile / jp->tiles_x, tx = tile - ty * jp->tiles_x;
@@ -44,17 +47,15 @@ k_nlw2(const Geom g, const TableArgs tb) {
     const int hi = clampi(i0 - HX + rr, 0, Hh - 1), hj = clampi(j0 - HX + cc, 0, Wh - 1);
     sX[rr * NXp + cc] = __ldg(x + (size_t)hi * Wh + hj);
   }
+  if (MODE == NLW_BLOCK) DA::clear(sV, tid, NF_THREADS);
   __syncthreads();
   const int ju = lane, uj = j0 + ju;
   const int iu0 = NF_PIX * warp;            // strip rows iu0 .. iu0 + 3
   const bool col_in = uj < Wh;
-  if (MODE == NLW_BLOCK && col_in) {
+  const float half_mu = 0.5f * g.mu;
+  float vown[NF_PIX];                       // this strip's own share of v
 #pragma unroll
-    for (int m = 0; m < NF_PIX; ++m) {
-      const int ui = i0 + iu0 + m;
-      if (ui < Hh) vout[(size_t)ui * Wh + uj] = 0.f;
-    }
-  }
+  for (int m = 0; m < NF_PIX; ++m) vown[m] = 0.f;
   float psum = 0.f;
   // patch origin (u - PR) of the strip's first pixel, in sX coordinates
   const float* xs = sX + (iu0 + WR) * NXp + (ju + WR);
@@ -116,7 +117,11 @@ k_nlw2(const Geom g, const TableArgs tb) {
           const float bn = fminf(fmaxf(fmaf(-w, diff, wb), -g.thr), g.thr);
           st_s(wS_new + (size_t)(2 * idx) * p + gi, an);
           st_s(wS_new + (size_t)(2 * idx + 1) * p + gi, bn);
-          cb[(size_t)idx * p + gi] = w * ((2.f * an - wa) - (2.f * bn - wb));
+          // the edge's divergence term: + at u, - at u + d (zero for an
+          // edge that leaves the image: w = 0)
+          const float c = half_mu * w * ((2.f * an - wa) - (2.f * bn - wb));
+          vown[m] += c;
+          if (valid) atomicAdd(sV + DA::at(iu0 + m + di, ju + dj), -c);
           const float da = an - wa, db = bn - wb;
           psum = fmaf(da, da, fmaf(db, db, psum));
         }
@@ -124,6 +129,11 @@ k_nlw2(const Geom g, const TableArgs tb) {
     }
   }
   if (MODE == NLW_BLOCK) {
+#pragma unroll
+    for (int m = 0; m < NF_PIX; ++m)
+      if (vown[m] != 0.f) atomicAdd(sV + DA::at(iu0 + m, ju), vown[m]);
+    __syncthreads();
+    DA::flush(sV, vout, i0, j0, Hh, Wh, tid, NF_THREADS);
     // |w_S' - w_S|^2 per light field: one slot per tile, summed by the last CTA
     const double bs = block_sum<NF_THREADS>((double)psum, s_red);
     if (tid == 0) tb.partials[blockIdx.x] = bs;

@@ -1,9 +1,8 @@
 // Weighted non-local TV with stored edge weights, part 2: the weighted
-// divergence S^T W^2 S p of every CG step, the x-step initialisation with
-// the regulariser divergence of the z/w-step, and the canonical-layout
-// export of the weights.  The weights (s_d/2 x p values of the storage type
-// ST, written by nltv_block.cu) are read while they sit in L2; the per-edge
-// divergence terms and all arithmetic are float.
+// divergence S^T W^2 S p of every CG step and the canonical-layout export
+// of the weights.  The weights (s_d/2 x p values of the storage type ST,
+// written by nltv_block.cu) are read while they sit in L2; all arithmetic
+// is float.
 #include "nltv_fast.cuh"
 
 namespace lfsr {
@@ -130,59 +129,6 @@ k_nla2(const Geom g, const TableArgs tb) {
   }
 }
 
-// x-step initialisation (Algorithm 2) with the regulariser divergence of
-// the z/w-step folded in: v = v_data + mu/2 sum_d (c(u,d) - c(u-d,d));
-// r = -v; x' = x; pi = <r, r>.
-template <int WR>
-__global__ void __launch_bounds__(VEC_THREADS)
-k_cg_init_nltv(const Geom g, const TableArgs tb) {
-  using D = HalfDirs<WR>;
-  __shared__ double s_red[VEC_THREADS / 32];
-  // this CTA's chunk of HR pixels: unit blockIdx.x of the table
-  const JobArgs* jp = tb.jobs + table_job(tb, blockIdx.x);
-  const int Hh = jp->Hh, Wh = jp->Wh;
-  const int n = Hh * Wh;                      // p < 2^31: 32-bit pixel offsets
-  float* __restrict__ rv = jp->out;
-  const float* __restrict__ cb = jp->cb;
-  const float* __restrict__ x = jp->src;
-  float* __restrict__ x_next = jp->x_next;
-  const int c0 = (blockIdx.x - jp->unit0) * jp->chunk;
-  const int c1 = min(n, c0 + jp->chunk);
-  const float half_mu = 0.5f * g.mu;
-  double part = 0.0;
-  for (int i = c0 + threadIdx.x; i < c1; i += VEC_THREADS) {
-    const int ui = i / Wh, uj = i - ui * Wh;
-    // away from the border every backward neighbour u - d is in the image
-    const bool inner = ui + WR < Hh && uj >= WR && uj + WR < Wh;
-    float div = 0.f;
-    constexpr int DB = 8;
-#pragma unroll
-    for (int i0d = 0; i0d < D::SH; i0d += DB) {
-      float cf[DB], cbk[DB];
-#pragma unroll
-      for (int e = 0; e < DB; ++e) {
-        const int idx = i0d + e;
-        if (idx >= D::SH) break;
-        const float* cd = cb + (size_t)idx * n + i;
-        const int bi = ui - D::di(idx), bj = uj - D::dj(idx);
-        const int bo = D::di(idx) * Wh + D::dj(idx);
-        cf[e] = __ldg(cd);
-        cbk[e] = (inner || (bi < Hh && bj >= 0 && bj < Wh)) ? __ldg(cd - bo) : 0.f;
-      }
-#pragma unroll
-      for (int e = 0; e < DB; ++e)
-        if (i0d + e < D::SH) div += cf[e] - cbk[e];
-    }
-    const float r = -fmaf(half_mu, div, rv[i]);
-    rv[i] = r;
-    x_next[i] = x[i];
-    part += (double)r * (double)r;
-  }
-  const double bs = block_sum<VEC_THREADS>(part, s_red);
-  if (threadIdx.x == 0) tb.partials[blockIdx.x] = bs;
-  if (table_arrive_last(tb.counter)) cg_init_finalize<VEC_THREADS>(g, tb);
-}
-
 // canonical weights [d][u] from the stored edge weights wt[idx][u]
 template <class ST>
 __global__ void k_weights_to_canonical(const Geom g, const ST* __restrict__ wt,
@@ -238,17 +184,6 @@ cudaError_t nla2_launch(const Geom& g, const TableArgs& t, cudaStream_t s, int c
     case ST_BF16: return nla2_db<__nv_bfloat16>(g, t, s, chunk);
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t cg_init_nltv_launch(const Geom& g, const TableArgs& t, cudaStream_t s) {
-  if (t.total_units < 1) return cudaErrorInvalidValue;
-  switch (g.win_r) {
-    case 1: k_cg_init_nltv<1><<<t.total_units, VEC_THREADS, 0, s>>>(g, t); break;
-    case 2: k_cg_init_nltv<2><<<t.total_units, VEC_THREADS, 0, s>>>(g, t); break;
-    case 3: k_cg_init_nltv<3><<<t.total_units, VEC_THREADS, 0, s>>>(g, t); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
 }
 
 cudaError_t weights_to_canonical(const Geom& g, const void* wt, float* can, cudaStream_t s) {

@@ -32,4 +32,35 @@ struct HalfDirs {
   static __device__ __forceinline__ constexpr int dj(int idx) { return idx % W - WR; }
 };
 
+// Divergence accumulator of one NLTV tile (the regulariser's share of v in
+// the z/w-step, Sec. 4.1 wdd): every edge term c(u, d) of the tile's pixels
+// u adds c to v(u) and -c to v(u + d).  With d in the half window (d_i <= 0)
+// the targets lie in the tile, WR rows above it and WR columns either side.
+// A CTA gathers them in shared memory (float shared atomics) and adds the
+// whole region to the light field's v with global float atomics, so tiles
+// whose halos overlap add up; v must be zero before the NLTV block runs.
+template <int WR>
+struct DivAcc {
+  static constexpr int NR = NF_T + WR;          // rows: WR above the tile
+  static constexpr int NC = NF_T + 2 * WR;      // columns: WR either side
+  static constexpr int NCp = NC | 1;
+  static constexpr int SIZE = NR * NCp;
+  // smem index of tile-local pixel (r, c), -WR <= r < NF_T, -WR <= c < NF_T + WR
+  static __device__ __forceinline__ int at(int r, int c) { return (r + WR) * NCp + (c + WR); }
+  static __device__ __forceinline__ void clear(float* acc, int tid, int nthreads) {
+    for (int t = tid; t < SIZE; t += nthreads) acc[t] = 0.f;
+  }
+  // adds the region to v (Hh x Wh); entries outside the image are zero
+  static __device__ __forceinline__ void flush(const float* acc, float* v, int i0, int j0, int Hh,
+                                               int Wh, int tid, int nthreads) {
+    for (int t = tid; t < NR * NC; t += nthreads) {
+      const int rr = t / NC, cc = t - rr * NC;
+      const int hi = i0 - WR + rr, hj = j0 - WR + cc;
+      const float val = acc[rr * NCp + cc];
+      if (val != 0.f && hi >= 0 && hi < Hh && hj >= 0 && hj < Wh)
+        atomicAdd(v + (size_t)hi * Wh + hj, val);
+    }
+  }
+};
+
 }  // namespace lfsr

@@ -41,8 +41,9 @@ __global__ void k_occlusion(const int Hh, const int Wh, const float* __restrict_
 
 // k_nlw2p<BLOCK>: per owned pixel u and half-window direction d: the edge's
 //   directed weights from g staged over the tile + window halo, the stored
-//   edge weight, both duals of the edge updated, c(u, d) = w_a f_a - w_b f_b
-//   stored in cb[idx][u] (f = 2 w' - w, the over-relaxed duals), v(u) := 0.
+//   edge weight, both duals of the edge updated, c(u, d) = (mu/2) (w_a f_a -
+//   w_b f_b) (f = 2 w' - w, the over-relaxed duals) added to v(u) and
+//   subtracted from v(u+d) (DivAcc; v is zero before the launch).
 // k_nlw2p<ONLY>: the stored edge weights alone.
 // Thread layout as k_nlw2: a strip of NF_PIX rows of one column per thread.
 template <int MODE, int WR, class ST>
@@ -52,8 +53,10 @@ k_nlw2p(const Geom g, const TableArgs tb) {
   // x over the tile + (WR + 1): central differences at the halo's g
   constexpr int T = NF_T, HX = WR + 1, NX = T + 2 * HX, NXp = NX | 1;
   constexpr int NG = T + 2 * WR, NGp = NG | 1;
+  using DA = DivAcc<WR>;
   __shared__ float sX[NX * NXp];
   __shared__ float sG[NG * NGp];
+  __shared__ float sV[MODE == NLW_BLOCK ? DA::SIZE : 1];
   __shared__ double s_red[NF_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const JobArgs* jp = tb.jobs + table_job(tb, blockIdx.x);
@@ -64,7 +67,6 @@ k_nlw2p(const Geom g, const TableArgs tb) {
   const ST* __restrict__ wS_old = (const ST*)jp->wS_old;
   ST* __restrict__ wS_new = (ST*)jp->wS_new;
   ST* __restrict__ wt = (ST*)jp->wt;
-  float* __restrict__ cb = jp->cb;
   const size_t p = (size_t)Hh * Wh;
   const int tile = blockIdx.x - jp->unit0;
   const int ty = tile / jp->tiles_x, tx = tile - ty * jp->tiles_x;
@@ -74,6 +76,7 @@ k_nlw2p(const Geom g, const TableArgs tb) {
     const int hi = clampi(i0 - HX + rr, 0, Hh - 1), hj = clampi(j0 - HX + cc, 0, Wh - 1);
     sX[rr * NXp + cc] = __ldg(x + (size_t)hi * Wh + hj);
   }
+  if (MODE == NLW_BLOCK) DA::clear(sV, tid, NF_THREADS);
   __syncthreads();
   // g(v) over the tile + WR; 0 outside the image (only edges that leave
   // the image read it there, and those are dropped)
@@ -96,13 +99,10 @@ k_nlw2p(const Geom g, const TableArgs tb) {
   const int ju = lane, uj = j0 + ju;
   const int iu0 = NF_PIX * warp;
   const bool col_in = uj < Wh;
-  if (MODE == NLW_BLOCK && col_in) {
+  const float half_mu = 0.5f * g.mu;
+  float vown[NF_PIX];                       // this strip's own share of v
 #pragma unroll
-    for (int m = 0; m < NF_PIX; ++m) {
-      const int ui = i0 + iu0 + m;
-      if (ui < Hh) vout[(size_t)ui * Wh + uj] = 0.f;
-    }
-  }
+  for (int m = 0; m < NF_PIX; ++m) vown[m] = 0.f;
   float psum = 0.f;
   const float* gs = sG + (iu0 + WR) * NGp + (ju + WR);   // g(u) of the strip's first pixel
   const float* xs = sX + (iu0 + HX) * NXp + (ju + HX);   // x(u) of the strip's first pixel
@@ -153,7 +153,11 @@ k_nlw2p(const Geom g, const TableArgs tb) {
           const float bn = fminf(fmaxf(fmaf(-w_b, diff, wb), -g.thr), g.thr);
           st_s(wS_new + (size_t)(2 * idx) * p + gi, an);
           st_s(wS_new + (size_t)(2 * idx + 1) * p + gi, bn);
-          cb[(size_t)idx * p + gi] = fmaf(w_a, 2.f * an - wa, -w_b * (2.f * bn - wb));
+          // the edge's divergence term: + at u, - at u + d (zero for an
+          // edge that leaves the image: w_a = w_b = 0)
+          const float c = half_mu * fmaf(w_a, 2.f * an - wa, -w_b * (2.f * bn - wb));
+          vown[m] += c;
+          if (valid) atomicAdd(sV + DA::at(iu0 + m + di, ju + dj), -c);
           const float da = an - wa, db = bn - wb;
           psum = fmaf(da, da, fmaf(db, db, psum));
         }
@@ -161,6 +165,11 @@ k_nlw2p(const Geom g, const TableArgs tb) {
     }
   }
   if (MODE == NLW_BLOCK) {
+#pragma unroll
+    for (int m = 0; m < NF_PIX; ++m)
+      if (vown[m] != 0.f) atomicAdd(sV + DA::at(iu0 + m, ju), vown[m]);
+    __syncthreads();
+    DA::flush(sV, vout, i0, j0, Hh, Wh, tid, NF_THREADS);
     // |w_S' - w_S|^2 per light field: one slot per tile, summed by the last CTA
     const double bs = block_sum<NF_THREADS>((double)psum, s_red);
     if (tid == 0) tb.partials[blockIdx.x] = bs;

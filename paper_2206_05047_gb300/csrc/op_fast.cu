@@ -29,9 +29,38 @@ static cudaError_t fast_launch_zk(int mode, const Geom& g, const OpPlan& P, cons
                                   const JobArgs& one, int grid, cudaStream_t s) {
   switch (mode) {
     case OP_NORMAL:
+      if (one.fuse) {
+        // the fused CG step waits at grid barriers: a cooperative launch
+        // guarantees that every CTA is resident (the grid never exceeds the
+        // co-resident count, see op_grid)
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(FT_THREADS);
+        cfg.dynamicSmemBytes = P.smem_bytes;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_operator_fast<OP_NORMAL, Z, KB, true>, g, P, t, one);
+      }
       k_operator_fast<OP_NORMAL, Z, KB, true><<<grid, FT_THREADS, P.smem_bytes, s>>>(g, P, t, one);
       break;
     case OP_DATA:
+      if (one.fuse) {
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(FT_THREADS);
+        cfg.dynamicSmemBytes = P.smem_bytes;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_operator_fast<OP_DATA, Z, KB, true>, g, P, t, one);
+      }
       k_operator_fast<OP_DATA, Z, KB, true><<<grid, FT_THREADS, P.smem_bytes, s>>>(g, P, t, one);
       break;
     case OP_FWD:

@@ -587,6 +587,171 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
   }
 
   if (jb >= 0) end_job();
+  if (SINGLE && MODE == OP_DATA && one.fuse) {
+    // The x-step initialisation (Algorithm 2) in the same launch: once
+    // every CTA has flushed its v atomics, each CTA takes its chunk of the
+    // accumulated v (the regulariser's part came from the NLTV block):
+    // r = -v, v := 0 for the next iteration, x' = x, and its partial of
+    // pi = <r, r>; after a second barrier CTA 0 finishes pi and the fresh
+    // CG state.
+    DevScalars* sc = one.sc;
+    const bool ok1 = grid_barrier(&sc->bar, g);
+    if (ok1 && blockIdx.x == 0 && tid < 32) {
+      const double total = warp_sum_slots(t.partials, gridDim.x);
+      if (tid == 0) {
+        sc->red[RED_DW_A] = total;
+        sc->dwA = total;
+      }
+    }
+    double rr = 0.0;
+    const int n = p_Hh * p_Wh;
+    const int c0 = blockIdx.x * one.fchunk;
+    const int c1 = min(n, c0 + one.fchunk);   // may be <= c0: the last CTAs can have no pixels
+    if (ok1 && c0 < c1) {
+      float* __restrict__ va = one.vacc;
+      float* __restrict__ rv = one.rr;
+      const float* __restrict__ xs = one.src;
+      float* __restrict__ xn = one.x_next;
+      const int v0 = c0 >> 2, v1 = c1 >> 2;
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int v = v0 + tid; v < v1; v += FT_THREADS) {
+        const float4 a4 = __ldcg(reinterpret_cast<const float4*>(va) + v);
+        reinterpret_cast<float4*>(va)[v] = z4;
+        const float4 r4 = make_float4(-a4.x, -a4.y, -a4.z, -a4.w);
+        reinterpret_cast<float4*>(rv)[v] = r4;
+        reinterpret_cast<float4*>(xn)[v] = __ldg(reinterpret_cast<const float4*>(xs) + v);
+        rr += (double)r4.x * (double)r4.x;
+        rr += (double)r4.y * (double)r4.y;
+        rr += (double)r4.z * (double)r4.z;
+        rr += (double)r4.w * (double)r4.w;
+      }
+      for (int i = 4 * v1 + tid; i < c1; i += FT_THREADS) {
+        const float r = -__ldcg(va + i);
+        va[i] = 0.f;
+        rv[i] = r;
+        xn[i] = xs[i];
+        rr += (double)r * (double)r;
+      }
+    }
+    {
+      const double bs = block_sum<FT_THREADS>(rr, s_red);
+      if (tid == 0) one.fpart[blockIdx.x] = bs;
+    }
+    const bool ok2 = grid_barrier(&sc->bar, g);
+    if (!ok1 || !ok2) {
+      if (tid == 0) set_status(sc, -5);   // LFSR_ETIMEOUT
+      return;
+    }
+    if (blockIdx.x == 0 && tid < 32) {
+      const double total = warp_sum_slots(one.fpart, gridDim.x);
+      if (tid == 0) {
+        sc->pi = total;
+        sc->cg_first = 1;
+        sc->cg_steps = 0;
+        sc->beta = 0.0;
+        sc->dw2 = sc->dwA + sc->dwS;
+        if (!isfinite(total)) set_status(sc, -4);  // LFSR_ENUMERIC
+        sc->cg_done = (total > g.tau && isfinite(total)) ? 0 : 1;
+      }
+    }
+    return;
+  }
+  if (SINGLE && MODE == OP_NORMAL && one.fuse) {
+    // The rest of the CG step (Algorithm 2) in the same launch: once every
+    // CTA has flushed its q atomics and stored its <p, A^T A p> partial, each
+    // CTA forms the step length from the partials (the same sum in the same
+    // order in every CTA), updates its chunk of x' and r, and its partial of
+    // pi' = <r, r>; after a second barrier CTA 0 finishes pi', beta and the
+    // step count.  A finished x-step (skip) returns in every CTA alike.
+    if (skip) return;
+    DevScalars* sc = one.sc;
+    __shared__ double s_alpha;
+    __shared__ int s_go;
+    const bool ok1 = grid_barrier(&sc->bar, g);
+    if (tid < 32) {
+      const double total = warp_sum_slots(t.partials, gridDim.x);
+      if (tid == 0) {
+        const double pAp =
+            (double)g.cA * total + (double)g.mu * ((volatile double*)sc->red)[RED_NLTV];
+        const bool good = pAp > 0.0 && isfinite(pAp);
+        s_alpha = good ? ((volatile double*)&sc->pi)[0] / pAp : 0.0;
+        s_go = ok1 && good;
+        if (blockIdx.x == 0 && ok1) {
+          sc->red[RED_OP] = total;
+          sc->pAp = pAp;
+          sc->alpha = s_alpha;
+          if (!good) {
+            // a curvature of exactly 0 ends the x-step; a negative or
+            // non-finite one is a numeric failure (as cg_set_alpha)
+            sc->cg_done = 1;
+            if (!(pAp == 0.0)) set_status(sc, -4);  // LFSR_ENUMERIC
+          }
+        }
+      }
+    }
+    __syncthreads();
+    double rr = 0.0;
+    const int n = p_Hh * p_Wh;
+    const int c0 = blockIdx.x * one.fchunk;
+    const int c1 = min(n, c0 + one.fchunk);   // may be <= c0: the last CTAs can have no pixels
+    if (s_go && c0 < c1) {
+      const float alpha = (float)s_alpha;
+      const float* __restrict__ pv = one.p_old;
+      const float* __restrict__ qv = one.q;
+      float* __restrict__ rv = one.rr;
+      float* __restrict__ xv = one.x_next;
+      // chunks are whole multiples of 32 floats on 256-byte aligned buffers
+      const int v0 = c0 >> 2, v1 = c1 >> 2;
+      for (int v = v0 + tid; v < v1; v += FT_THREADS) {
+        const float4 pp = __ldg(reinterpret_cast<const float4*>(pv) + v);
+        const float4 qq = __ldcg(reinterpret_cast<const float4*>(qv) + v);
+        float4 r4 = reinterpret_cast<const float4*>(rv)[v];
+        float4 x4 = reinterpret_cast<const float4*>(xv)[v];
+        x4.x = fmaf(alpha, pp.x, x4.x);
+        x4.y = fmaf(alpha, pp.y, x4.y);
+        x4.z = fmaf(alpha, pp.z, x4.z);
+        x4.w = fmaf(alpha, pp.w, x4.w);
+        r4.x = fmaf(-alpha, qq.x, r4.x);
+        r4.y = fmaf(-alpha, qq.y, r4.y);
+        r4.z = fmaf(-alpha, qq.z, r4.z);
+        r4.w = fmaf(-alpha, qq.w, r4.w);
+        reinterpret_cast<float4*>(xv)[v] = x4;
+        reinterpret_cast<float4*>(rv)[v] = r4;
+        rr += (double)r4.x * (double)r4.x;
+        rr += (double)r4.y * (double)r4.y;
+        rr += (double)r4.z * (double)r4.z;
+        rr += (double)r4.w * (double)r4.w;
+      }
+      for (int i = 4 * v1 + tid; i < c1; i += FT_THREADS) {
+        xv[i] = fmaf(alpha, pv[i], xv[i]);
+        const float rn = fmaf(-alpha, __ldcg(qv + i), rv[i]);
+        rv[i] = rn;
+        rr += (double)rn * (double)rn;
+      }
+    }
+    {
+      const double bs = block_sum<FT_THREADS>(rr, s_red);
+      if (tid == 0) one.fpart[blockIdx.x] = bs;
+    }
+    const bool ok2 = grid_barrier(&sc->bar, g);
+    if (!ok1 || !ok2) {
+      if (tid == 0) set_status(sc, -5);   // LFSR_ETIMEOUT
+      return;
+    }
+    if (blockIdx.x == 0 && s_go && tid < 32) {
+      const double total = warp_sum_slots(one.fpart, gridDim.x);
+      if (tid == 0) {
+        const double pi_old = sc->pi;
+        sc->beta = total / pi_old;
+        sc->pi = total;
+        sc->cg_first = 0;
+        sc->cg_steps += 1;
+        if (!isfinite(total)) set_status(sc, -4);  // LFSR_ENUMERIC
+        if (!(total > g.tau) || !isfinite(total)) sc->cg_done = 1;
+      }
+    }
+    return;
+  }
   if (REDUCE && table_arrive_last(t.counter)) {
     // every light field's total over the CTAs' slots, one warp per light field
     const int warp = tid >> 5, lane = tid & 31;

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -53,7 +54,9 @@ struct lfsr_server {
   int64_t next_id = 0;
   int64_t bytes_in_use = 0, bytes_peak = 0;
   int64_t iterations = 0, rebuilds = 0, admitted = 0, retired = 0, dry_parity = 0, launches = 0;
+  int64_t cancelled = 0;
   std::string err = "no error";
+  mutable std::mutex mu;                      // every entry point holds it
 };
 
 namespace {
@@ -103,6 +106,12 @@ int admit(lfsr_server* s) {
     }
     if (s->bytes_in_use + r.bytes > s->cfg.hbm_budget_bytes) break;
     s->queue.pop_front();
+    if (dry(s) && fault_alloc()) {   // an injected allocation failure at admission
+      r.state = LFSR_REQ_FAILED;
+      r.error = LFSR_ENOMEM;
+      release_inputs(r);
+      continue;
+    }
     if (!dry(s)) {
       lfsr_params p = r.prm;
       p.blur = r.blur.data();
@@ -175,6 +184,7 @@ const char* lfsr_server_last_error(const lfsr_server* s) {
 int lfsr_server_submit(lfsr_server* s, const lfsr_params* params, const float* lr_views,
                        const float* x0, int64_t* id) {
   if (!s) return sfail(nullptr, LFSR_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
   if (!params || !lr_views || !x0 || !id)
     return sfail(s, LFSR_EINVAL, "params, lr_views, x0 and id are required");
   const int64_t est = lfsr_estimate_state_bytes(params);
@@ -218,6 +228,7 @@ int lfsr_server_submit(lfsr_server* s, const lfsr_params* params, const float* l
 
 int lfsr_server_step(lfsr_server* s) {
   if (!s) return sfail(nullptr, LFSR_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
   admit(s);
   if (s->active.empty()) return 0;
   if (!dry(s) && s->changed) {
@@ -271,6 +282,7 @@ int lfsr_server_step(lfsr_server* s) {
 
 int lfsr_server_status(const lfsr_server* s, int64_t id, int* state, int* iterations) {
   if (!s) return sfail(nullptr, LFSR_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
   auto it = s->reqs.find(id);
   if (it == s->reqs.end()) return LFSR_EINVAL;
   if (state) *state = it->second.state;
@@ -280,6 +292,7 @@ int lfsr_server_status(const lfsr_server* s, int64_t id, int* state, int* iterat
 
 int lfsr_server_fetch(lfsr_server* s, int64_t id, float* x_out, int mem) {
   if (!s) return sfail(nullptr, LFSR_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
   auto it = s->reqs.find(id);
   if (it == s->reqs.end()) return sfail(s, LFSR_EINVAL, "unknown request");
   Request& r = it->second;
@@ -303,6 +316,7 @@ int lfsr_server_fetch(lfsr_server* s, int64_t id, float* x_out, int mem) {
 
 int lfsr_server_stats(const lfsr_server* s, lfsr_server_stats_t* out) {
   if (!s) return sfail(nullptr, LFSR_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
   if (!out || out->struct_size != sizeof(lfsr_server_stats_t))
     return sfail(const_cast<lfsr_server*>(s), LFSR_EINVAL,
                  "out->struct_size != sizeof(lfsr_server_stats_t)");
@@ -320,6 +334,37 @@ int lfsr_server_stats(const lfsr_server* s, lfsr_server_stats_t* out) {
   out->admitted = s->admitted;
   out->retired = s->retired;
   out->launches = s->launches;
+  out->cancelled = s->cancelled;
+  return LFSR_OK;
+}
+
+int lfsr_server_cancel(lfsr_server* s, int64_t id) {
+  if (!s) return sfail(nullptr, LFSR_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return sfail(s, LFSR_EINVAL, "unknown request");
+  Request& r = it->second;
+  switch (r.state) {
+    case LFSR_REQ_QUEUED:
+      s->queue.erase(std::find(s->queue.begin(), s->queue.end(), id));
+      release_inputs(r);
+      break;
+    case LFSR_REQ_ACTIVE:
+      // between steps no launch of the batch is in flight (a step ends with
+      // a stream synchronisation): free the state, rebuild at the next step
+      s->active.erase(std::find(s->active.begin(), s->active.end(), id));
+      release(s, r);
+      s->changed = true;
+      break;
+    case LFSR_REQ_DONE:
+      r.result.clear();
+      r.result.shrink_to_fit();
+      break;
+    default:
+      return sfail(s, LFSR_EINVAL, "the request is already fetched, failed or cancelled");
+  }
+  r.state = LFSR_REQ_CANCELLED;
+  s->cancelled += 1;
   return LFSR_OK;
 }
 

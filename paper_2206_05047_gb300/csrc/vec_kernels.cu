@@ -37,6 +37,33 @@ k_cg_init(const Geom g, const TableArgs tb) {
   if (table_arrive_last(tb.counter)) cg_init_finalize<VEC_THREADS>(g, tb);
 }
 
+// x-step initialisation from the accumulated v (the stored-weight NLTV
+// block and the data block add into it): r = -v, v := 0 for the next
+// iteration, x' = x, pi = <r, r>.
+__global__ void __launch_bounds__(VEC_THREADS)
+k_cg_init_acc(const Geom g, const TableArgs tb) {
+  __shared__ double s_red[VEC_THREADS / 32];
+  const JobArgs* jp = tb.jobs + table_job(tb, blockIdx.x);
+  const int n = jp->Hh * jp->Wh;              // p < 2^31: 32-bit offsets
+  float* __restrict__ va = jp->vacc;
+  float* __restrict__ rv = jp->out;
+  const float* __restrict__ x = jp->src;
+  float* __restrict__ x_next = jp->x_next;
+  const int c0 = (blockIdx.x - jp->unit0) * jp->chunk;
+  const int c1 = min(n, c0 + jp->chunk);
+  double part = 0.0;
+  for (int i = c0 + threadIdx.x; i < c1; i += VEC_THREADS) {
+    const float r = -va[i];
+    va[i] = 0.f;
+    rv[i] = r;
+    x_next[i] = x[i];
+    part += (double)r * (double)r;
+  }
+  const double bs = block_sum<VEC_THREADS>(part, s_red);
+  if (threadIdx.x == 0) tb.partials[blockIdx.x] = bs;
+  if (table_arrive_last(tb.counter)) cg_init_finalize<VEC_THREADS>(g, tb);
+}
+
 // CG update: x += alpha p, r -= alpha q, pi' = <r, r>, beta = pi' / pi.
 __global__ void __launch_bounds__(VEC_THREADS)
 k_cg_update(const Geom g, const TableArgs tb) {
@@ -108,6 +135,12 @@ k_cg_update(const Geom g, const TableArgs tb) {
 cudaError_t cg_init_launch(const Geom& g, const TableArgs& t, cudaStream_t s) {
   if (t.total_units < 1) return cudaErrorInvalidValue;
   k_cg_init<<<t.total_units, VEC_THREADS, 0, s>>>(g, t);
+  return cudaGetLastError();
+}
+
+cudaError_t cg_init_acc_launch(const Geom& g, const TableArgs& t, cudaStream_t s) {
+  if (t.total_units < 1) return cudaErrorInvalidValue;
+  k_cg_init_acc<<<t.total_units, VEC_THREADS, 0, s>>>(g, t);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ LFSR_ADJOINT_EXACT = 0
 LFSR_ADJOINT_BACKWARD_WARP = 1
 ADJOINTS = {"exact": LFSR_ADJOINT_EXACT, "backward": LFSR_ADJOINT_BACKWARD_WARP}
 LFSR_REQ_QUEUED, LFSR_REQ_ACTIVE, LFSR_REQ_DONE, LFSR_REQ_FETCHED, LFSR_REQ_FAILED = 0, 1, 2, 3, 4
+LFSR_REQ_CANCELLED = 5
 # precision names accepted by Solver(precision=...) and the benchmark
 PRECISIONS = {"fp32": LFSR_FP32, "fp16": LFSR_FP16_STORAGE, "bf16": LFSR_BF16_STORAGE,
               "fp16-views32": LFSR_FP16_STORAGE | LFSR_KEEP_VIEWS_FP32,
@@ -47,14 +48,16 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblfsr.so
 EXPORTS = ("lfsr_create", "lfsr_solve", "lfsr_destroy", "lfsr_last_error", "lfsr_stats",
            "lfsr_load", "lfsr_iterate", "lfsr_get_x", "lfsr_set_state", "lfsr_get_state",
            "lfsr_apply_A", "lfsr_apply_AT", "lfsr_weights", "lfsr_apply_normal",
-           "lfsr_set_profiling", "lfsr_apply_normal_noalloc", "lfsr_batch_create",
+           "lfsr_set_profiling", "lfsr_set_device_wait", "lfsr_apply_normal_noalloc",
+           "lfsr_batch_create",
            "lfsr_batch_destroy", "lfsr_batch_last_error", "lfsr_batch_size", "lfsr_batch_load",
            "lfsr_batch_iterate", "lfsr_batch_get_x", "lfsr_batch_stats",
            "lfsr_batch_launches_per_iteration", "lfsr_batch_set_profiling",
            "lfsr_batch_kernel_times", "lfsr_batch_autotune", "lfsr_batch_tuning",
            "lfsr_batch_set_tuning", "lfsr_estimate_state_bytes", "lfsr_server_create",
            "lfsr_server_destroy", "lfsr_server_last_error", "lfsr_server_submit",
-           "lfsr_server_step", "lfsr_server_status", "lfsr_server_fetch", "lfsr_server_stats")
+           "lfsr_server_step", "lfsr_server_status", "lfsr_server_fetch", "lfsr_server_stats",
+           "lfsr_server_cancel")
 
 
 class lfsr_params(C.Structure):
@@ -89,7 +92,7 @@ class lfsr_server_stats_t(C.Structure):
                 ("done", C.c_int32), ("failed", C.c_int32), ("bytes_in_use", C.c_int64),
                 ("bytes_peak", C.c_int64), ("iterations", C.c_int64),
                 ("batch_rebuilds", C.c_int64), ("admitted", C.c_int64), ("retired", C.c_int64),
-                ("launches", C.c_int64)]
+                ("launches", C.c_int64), ("cancelled", C.c_int64)]
 
 
 class LfsrError(RuntimeError):
@@ -127,6 +130,7 @@ def load_library(path: str = _LIB_PATH):
         "lfsr_weights": (C.c_int, [H, fp, fp, C.c_int]),
         "lfsr_apply_normal": (C.c_int, [H, fp, fp, fp, C.POINTER(C.c_double), C.c_int]),
         "lfsr_set_profiling": (C.c_int, [H, C.c_int]),
+        "lfsr_set_device_wait": (C.c_int, [H, C.c_int64, C.c_int]),
         "lfsr_apply_normal_noalloc": (C.c_int, [C.POINTER(lfsr_params), fp, fp, fp, fp,
                                                 C.POINTER(C.c_double), C.c_void_p]),
         "lfsr_batch_create": (C.c_int, [C.POINTER(lfsr_params), C.c_int, C.c_void_p,
@@ -153,6 +157,7 @@ def load_library(path: str = _LIB_PATH):
                                          C.POINTER(C.c_int)]),
         "lfsr_server_fetch": (C.c_int, [H, C.c_int64, fp, C.c_int]),
         "lfsr_server_stats": (C.c_int, [H, C.POINTER(lfsr_server_stats_t)]),
+        "lfsr_server_cancel": (C.c_int, [H, C.c_int64]),
         "lfsr_batch_set_tuning": (C.c_int, [H, C.POINTER(C.c_int), C.c_int, C.c_int]),
         "lfsr_batch_tuning": (C.c_int, [H, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
         "lfsr_batch_kernel_times": (C.c_int, [H, C.POINTER(C.c_double),
@@ -332,6 +337,17 @@ def apply_normal(handle, xw, p, q) -> float:
 
 def set_profiling(handle, on: bool) -> None:
     _check(load_library().lfsr_set_profiling(handle, int(bool(on))), handle)
+
+
+LFSR_DEFAULT_WAIT_NS = 1_000_000_000
+
+
+def set_device_wait(handle, limit_ns: int = LFSR_DEFAULT_WAIT_NS,
+                    test_unreachable: bool = False) -> None:
+    """lfsr_set_device_wait: bound of the fused CG step's grid-barrier waits
+    (ns); test_unreachable makes every wait run out (LFSR_ETIMEOUT)."""
+    _check(load_library().lfsr_set_device_wait(handle, int(limit_ns), int(bool(test_unreachable))),
+           handle)
 
 
 def stats(handle) -> dict:
@@ -586,6 +602,11 @@ class Server:
         st.struct_size = C.sizeof(lfsr_server_stats_t)
         self._check(load_library().lfsr_server_stats(self.handle, C.byref(st)))
         return {k: getattr(st, k) for k, _ in lfsr_server_stats_t._fields_ if k != "struct_size"}
+
+    def cancel(self, rid) -> None:
+        """lfsr_server_cancel: a queued, active or done request leaves the
+        server (state LFSR_REQ_CANCELLED; slot and budget freed)."""
+        self._check(load_library().lfsr_server_cancel(self.handle, int(rid)))
 
     def close(self):
         if self.handle is not None:

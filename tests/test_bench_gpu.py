@@ -31,6 +31,9 @@ def test_bench_line_on_a_small_workload():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0 and cb["sample"]
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
-    # 3 timed solves of N = 50 iterations, 18 launches each
-    assert d["gpu_launches"] == 3 * 50 * 18
+    # 3 timed solves of N = 50 iterations, 2 + 2K launches each (the x-step
+    # initialisation is part of the data-block launch, the CG update part of
+    # the normal-matrix launch)
+    assert d["gpu_launches"] == 3 * 50 * (2 + 2 * 5)
+    assert d["launches_per_iteration"] == 2 + 2 * 5
     assert "sm_mhz" in d["clocks"] and "reasons" in d["clocks"]

@@ -109,3 +109,107 @@ def test_served_requests_take_one_map_and_the_exact_adjoint():
     del pe
     assert rid == 0
     srv.close()
+
+
+# --------------------------------------------------------------------------
+# failure paths on the host: cancelled requests, injected allocation faults
+# --------------------------------------------------------------------------
+def test_cancel_queued_active_and_done_requests():
+    srv = lfsr.Server(1 << 40, max_active=2, iterations=6, iterations_per_step=2, dry_run=True)
+    ids = [_submit(srv) for _ in range(5)]
+    assert srv.step() == 2                       # 0 and 1 active
+    srv.cancel(3)                                # queued
+    srv.cancel(0)                                # active: its slot frees at once
+    assert srv.status(0)[0] == lfsr.LFSR_REQ_CANCELLED
+    assert srv.status(3)[0] == lfsr.LFSR_REQ_CANCELLED
+    st = srv.stats()
+    assert st["active"] == 1 and st["queued"] == 2 and st["cancelled"] == 2
+    assert srv.step() == 2                       # 2 takes the freed slot; 4 waits
+    assert srv.status(2)[:2] == (lfsr.LFSR_REQ_ACTIVE, 2)
+    for _ in range(20):
+        if srv.stats()["done"] == 3:
+            break
+        srv.step()
+    st = srv.stats()
+    assert st["done"] == 3 and st["failed"] == 0 and st["cancelled"] == 2
+    assert st["active"] == 0 and st["bytes_in_use"] == 0
+    srv.cancel(4)                                # done, not fetched: drops its result
+    assert srv.status(4)[0] == lfsr.LFSR_REQ_CANCELLED
+    with pytest.raises(lfsr.LfsrError):
+        srv.fetch(4, np.zeros((32, 32), np.float32))
+    for bad in (0, 4, 99):                       # already cancelled, unknown
+        with pytest.raises(lfsr.LfsrError) as e:
+            srv.cancel(bad)
+        assert e.value.code == lfsr.LFSR_EINVAL
+    x = np.zeros((32, 32), np.float32)
+    srv.fetch(1, x)
+    with pytest.raises(lfsr.LfsrError):          # fetched: nothing left to cancel
+        srv.cancel(1)
+    assert srv.stats()["cancelled"] == 3
+    srv.close()
+
+
+def test_injected_allocation_fault_fails_one_admission(monkeypatch):
+    """LFSR_FAULT=alloc:2 fails the second admission as an allocation error:
+    that request fails with LFSR_ENOMEM and holds no slot or budget, the
+    others run to the end."""
+    y, x0, args = _req()
+    est = lfsr.estimate_state_bytes(**args)
+    srv = lfsr.Server(4 * est, max_active=3, iterations=4, iterations_per_step=2, dry_run=True)
+    ids = [srv.submit(y, x0, **args) for _ in range(4)]
+    monkeypatch.setenv("LFSR_FAULT", "alloc:2")
+    assert srv.step() == 3                       # 0, 2, 3 admitted; 1 failed
+    monkeypatch.delenv("LFSR_FAULT")
+    state, _, rc = srv.status(ids[1])
+    assert state == lfsr.LFSR_REQ_FAILED and rc == lfsr.LFSR_ENOMEM
+    assert srv.stats()["bytes_in_use"] == 3 * est
+    while srv.step() > 0:
+        pass
+    st = srv.stats()
+    assert st["done"] == 3 and st["failed"] == 1 and st["bytes_in_use"] == 0
+    srv.close()
+
+
+def test_every_allocation_failing_fails_every_admission(monkeypatch):
+    srv = lfsr.Server(1 << 40, max_active=4, iterations=4, iterations_per_step=2, dry_run=True)
+    ids = [_submit(srv) for _ in range(3)]
+    monkeypatch.setenv("LFSR_FAULT", "alloc")
+    assert srv.step() == 0
+    assert all(srv.status(i)[2] == lfsr.LFSR_ENOMEM for i in ids)
+    monkeypatch.setenv("LFSR_FAULT", "none")     # any other value: no fault
+    i = _submit(srv)
+    assert srv.step() == 1 and srv.status(i)[0] == lfsr.LFSR_REQ_ACTIVE
+    srv.close()
+
+
+def test_cancel_from_another_thread_while_stepping():
+    """The server's entry points may be called from several host threads: a
+    cancel issued while another thread steps takes effect between steps."""
+    import threading
+    srv = lfsr.Server(1 << 40, max_active=4, iterations=40, iterations_per_step=1, dry_run=True)
+    ids = [_submit(srv) for _ in range(6)]
+    stop = threading.Event()
+
+    def loop():
+        while not stop.is_set():
+            srv.step()
+            st = srv.stats()
+            if st["active"] == 0 and st["queued"] == 0:
+                break
+
+    t = threading.Thread(target=loop)
+    t.start()
+    for i in (1, 4, 5):
+        try:
+            srv.cancel(i)
+        except lfsr.LfsrError:
+            pass                                 # finished before the cancel
+    t.join(timeout=60)
+    stop.set()
+    assert not t.is_alive()
+    st = srv.stats()
+    assert st["done"] + st["cancelled"] == 6 and st["failed"] == 0
+    assert st["active"] == 0 and st["bytes_in_use"] == 0
+    for i in ids:
+        assert srv.status(i)[0] in (lfsr.LFSR_REQ_DONE, lfsr.LFSR_REQ_CANCELLED)
+    srv.close()
