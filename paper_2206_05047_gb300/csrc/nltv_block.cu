@@ -16,8 +16,8 @@ namespace lfsr {
 //   and subtracted from v(u+d) (v, zero before the launch, is the light
 //   field's accumulated v: the data block adds its part next and the x-step
 //   initialisation reads and clears it).  Patch sums of the strip share
-//   rows: the 4 + 2 PR row sums of squared differences give all 4 patch
-//   distances.
+//   rows: the NF_PIX + 2 PR row sums of squared differences give all NF_PIX
+//   patch distances.
 // k_nlw2<ONLY>: the weights alone.
 template <int MODE, int WR, int PR, class ST>
 __global__ void __launch_bounds__(NF_THREADS)
@@ -50,7 +50,7 @@ k_nlw2(const Geom g, const TableArgs tb) {
   if (MODE == NLW_BLOCK) DA::clear(sV, tid, NF_THREADS);
   __syncthreads();
   const int ju = lane, uj = j0 + ju;
-  const int iu0 = NF_PIX * warp;            // strip rows iu0 .. iu0 + 3
+  const int iu0 = NF_PIX * warp;            // strip rows iu0 .. iu0 + NF_PIX - 1
   const bool col_in = uj < Wh;
   const float half_mu = 0.5f * g.mu;
   float vown[NF_PIX];                       // this strip's own share of v

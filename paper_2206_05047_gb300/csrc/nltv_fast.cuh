@@ -7,7 +7,7 @@
 
 namespace lfsr {
 
-constexpr int NF_THREADS = 256;
+constexpr int NF_THREADS = 512;
 constexpr int NF_T = 32;
 constexpr int NF_PIX = NF_T * NF_T / NF_THREADS;
 // The weighted-divergence kernel (k_nla2) is bound by the latency of its
@@ -19,8 +19,8 @@ constexpr int NA_PIX = NF_T * NF_T / NA_THREADS;
 enum { NLW_BLOCK = 0, NLW_ONLY = 1 };
 
 // Pixel-owner kernels, no shared-memory exchange between directions.
-// Each thread owns a strip of NF_PIX = 4 consecutive rows of one column of
-// a 32 x 32 tile (rows 4 warp + m, column lane).  The half window's
+// Each thread owns a strip of NF_PIX consecutive rows of one column of a
+// 32 x 32 tile (rows NF_PIX warp + m, column lane).  The half window's
 // directions are compile-time constants (raster order, the same table the
 // host builds), so the direction loops unroll and every global load of a
 // thread is independent of the others.

@@ -55,8 +55,8 @@ struct FastShape {
   static constexpr int MG = (R + Z - 1) / Z + 1;             // zero margin of the LR grid
   static constexpr int NG = NL + 2 * MG;                     // LR grid with margins
   static constexpr int NGp = NG | 1;                         // its (odd) pitch
-  // stage 2 (horizontal forward): MB2 LR columns per task
-  static constexpr int MB2 = pick_block(VB * NE, NL);
+  // stage 2 (horizontal forward): MB2 LR columns of both views per task
+  static constexpr int MB2 = pick_block(NE, NL);
   static constexpr int NB2 = (NL + MB2 - 1) / MB2;
   static constexpr int W2 = Z * (MB2 - 1) + KB;              // window length
   static constexpr int NEp = ((Z * (NB2 * MB2 - 1) + KB) > NE ? (Z * (NB2 * MB2 - 1) + KB) : NE) | 1;
@@ -72,7 +72,7 @@ struct FastShape {
   // exactly T / Z values of m
   static constexpr bool ALIGNED = (T % Z) == 0;
   static constexpr int NM = ALIGNED ? T / Z : (T - 1) / Z + 2;  // m values per tile
-  static constexpr int MB5 = pick_block(VB * NG, NM);
+  static constexpr int MB5 = pick_block(NG, NM);   // both views per task
   static constexpr int NB5 = (NM + MB5 - 1) / MB5;
   static constexpr int DMIN = -(R / Z) - 1;                  // safe delta bounds (all phases)
   static constexpr int DMAX = (Z - 1 + R) / Z;
@@ -108,6 +108,33 @@ __device__ __forceinline__ void split_shift(float t, int& ip, float& fr) {
   const float f = __fadd_rd(t, 8388608.0f);
   ip = __float_as_int(f) - 0x4B000000;
   fr = t - (f - 8388608.0f);
+}
+
+// Two FP32 lanes per instruction (the packed FFMA2 / FADD2 / FMUL2 of this
+// architecture): the two views of a pass go through the same arithmetic in
+// the two lanes.  Every lane rounds as the scalar operation it replaces;
+// x - y is fma(y, -1, x), one rounding of the exact difference.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 add2_rd(float2 a, float2 b) {
+  unsigned long long ra, rb, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
+// split_shift of both lanes
+__device__ __forceinline__ void split_shift2(float2 t, int& i0, int& i1, float2& fr) {
+  const float2 f = add2_rd(t, make_float2(8388608.0f, 8388608.0f));
+  i0 = __float_as_int(f.x) - 0x4B000000;
+  i1 = __float_as_int(f.y) - 0x4B000000;
+  fr = sub2(t, __fadd2_rn(f, make_float2(-8388608.0f, -8388608.0f)));
 }
 
 // SINGLE: one light field whose fields come by value (kernel parameters,
@@ -327,57 +354,56 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
       //    staged source is 0, so the sample is 0 without a branch.  The
       //    two views of the pass share the disparity read and, when they
       //    lie in the same row of the angular grid, the vertical split.
+      //    Both views in the two lanes of packed FP32 operations (for a
+      //    single-view pass the second lane repeats the first view and is
+      //    not stored).
+      const bool two = nv > 1;
       {
-        const float tu0 = tu_of(kbase), tv0 = tv_of(kbase);
-        const int k1 = kbase + (nv > 1 ? 1 : 0);
-        const float tu1 = tu_of(k1), tv1 = tv_of(k1);
-        const bool two = nv > 1;
-        const bool same_row = tv1 == tv0;
+        const int k1 = kbase + (two ? 1 : 0);
+        const float2 tu2 = pk(tu_of(kbase), tu_of(k1)), tv2 = pk(tv_of(kbase), tv_of(k1));
+        const float2 S2 = pk(Sf, Sf);
 #pragma unroll
         for (int it = 0; it < SH::IT1; ++it) {
           const int t = tid + it * FT_THREADS;
           if (it < SH::IT1 - 1 || t < SH::NS1) {
             const int si = (NEp == NE) ? t : (t / NE) * NEp + (t % NE);
-            const float om = s1_om[it];
+            const float2 om2 = pk(s1_om[it], s1_om[it]);
             const float* qb = sP + s1_base[it];
-            int iy, ix;
-            float fy, fx;
-            split_shift(fmaf(tv0, om, Sf), iy, fy);
-            split_shift(fmaf(tu0, om, Sf), ix, fx);
-            {
-              const float* q = qb + iy * NPc + ix;
-              const float top = fmaf(fx, q[1] - q[0], q[0]);
-              const float bot = fmaf(fx, q[NPc + 1] - q[NPc], q[NPc]);
-              sW[si] = fmaf(fy, bot - top, top);
-            }
-            if (two) {
-              if (!same_row) split_shift(fmaf(tv1, om, Sf), iy, fy);
-              split_shift(fmaf(tu1, om, Sf), ix, fx);
-              const float* q = qb + iy * NPc + ix;
-              const float top = fmaf(fx, q[1] - q[0], q[0]);
-              const float bot = fmaf(fx, q[NPc + 1] - q[NPc], q[NPc]);
-              sW[SH::WS + si] = fmaf(fy, bot - top, top);
-            }
+            int iy0, iy1, ix0, ix1;
+            float2 fy, fx;
+            split_shift2(fma2(tv2, om2, S2), iy0, iy1, fy);
+            split_shift2(fma2(tu2, om2, S2), ix0, ix1, fx);
+            const float* qa = qb + iy0 * NPc + ix0;
+            const float* qc = qb + iy1 * NPc + ix1;
+            const float2 a = pk(qa[0], qc[0]), b = pk(qa[1], qc[1]);
+            const float2 c = pk(qa[NPc], qc[NPc]), d = pk(qa[NPc + 1], qc[NPc + 1]);
+            const float2 top = fma2(fx, sub2(b, a), a);
+            const float2 bot = fma2(fx, sub2(d, c), c);
+            const float2 o = fma2(fy, sub2(bot, top), top);
+            sW[si] = o.x;
+            if (two) sW[SH::WS + si] = o.y;
           }
         }
       }
       __syncthreads();
-      // 2. horizontal blur at decimated columns; lanes along rows
-      for (int t = tid; t < VB * NE * SH::NB2; t += FT_THREADS) {
-        const int v = t / (NE * SH::NB2), r2 = t - v * (NE * SH::NB2);
-        if (v >= nv) continue;
-        const int er = r2 % NE, cb = r2 / NE;
-        const float* w = sW + v * SH::WS + er * NEp + Z * SH::MB2 * cb;
-        float win[SH::W2];
+      // 2. horizontal blur at decimated columns, both views per task; lanes
+      //    along rows
+      for (int t = tid; t < NE * SH::NB2; t += FT_THREADS) {
+        const int er = t % NE, cb = t / NE;
+        const float* w = sW + er * NEp + Z * SH::MB2 * cb;
+        float2 win[SH::W2];
 #pragma unroll
-        for (int c = 0; c < SH::W2; ++c) win[c] = w[c];
+        for (int c = 0; c < SH::W2; ++c) win[c] = pk(w[c], w[SH::WS + c]);
 #pragma unroll
         for (int o = 0; o < SH::MB2; ++o) {
-          float acc = 0.f;
+          float2 acc = pk(0.f, 0.f);
 #pragma unroll
-          for (int b = 0; b < KB; ++b) acc = fmaf(g.kh[b], win[Z * o + b], acc);
+          for (int b = 0; b < KB; ++b) acc = fma2(pk(g.kh[b], g.kh[b]), win[Z * o + b], acc);
           const int lc = cb * SH::MB2 + o;
-          if (lc < NL) sH[v * SH::HS + er * NHp + lc] = acc;
+          if (lc < NL) {
+            sH[er * NHp + lc] = acc.x;
+            if (two) sH[SH::HS + er * NHp + lc] = acc.y;
+          }
         }
       }
       __syncthreads();
@@ -449,33 +475,37 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
     // 4. adjoint blur, rows (polyphase): V(hi, c) for hi in the tile and
     //    every column c of the LR grid (margins included, they are zero)
     const int m_lo = floor_div(i0, Z);
-    for (int t = tid; t < VB * SH::NG * SH::NB5; t += FT_THREADS) {
-      const int v = t / (SH::NG * SH::NB5), r4 = t - v * (SH::NG * SH::NB5);
-      if (v >= nv) continue;
-      const int c = r4 % SH::NG, mb = r4 / SH::NG;
+    const bool two = nv > 1;
+    for (int t = tid; t < SH::NG * SH::NB5; t += FT_THREADS) {
+      const int c = t % SH::NG, mb = t / SH::NG;
       const int m0 = m_lo + mb * SH::MB5;
-      const float* gv = sG + v * SH::GS;
-      // window rows l = m0 + DMIN .. m0 + MB5 - 1 + DMAX (grid row l - lr_lo + MG)
+      // window rows l = m0 + DMIN .. m0 + MB5 - 1 + DMAX (grid row l - lr_lo + MG),
+      // both views (the second view's grid is stale for a single-view pass)
       const int r0 = m0 + SH::DMIN - lr_lo + MG;
-      float win[SH::W5];
+      float2 win[SH::W5];
 #pragma unroll
       for (int w = 0; w < SH::W5; ++w) {
         const int rr = r0 + w;
-        win[w] = (rr >= 0 && rr < SH::NG) ? gv[rr * NGp + c] : 0.f;
+        win[w] = (rr >= 0 && rr < SH::NG) ? pk(sG[rr * NGp + c], sG[SH::GS + rr * NGp + c])
+                                          : pk(0.f, 0.f);
       }
 #pragma unroll
       for (int o = 0; o < SH::MB5; ++o) {
 #pragma unroll
         for (int ph = 0; ph < Z; ++ph) {
           const int hi = Z * (m0 + o) + ph;
-          float acc = 0.f;
+          float2 acc = pk(0.f, 0.f);
 #pragma unroll
           for (int d = SH::DMIN; d <= SH::DMAX; ++d) {
             const int ai = ph + R - Z * d;
-            if (ai >= 0 && ai <= 2 * R) acc = fmaf(g.kv[ai], win[o + d - SH::DMIN], acc);
+            if (ai >= 0 && ai <= 2 * R)
+              acc = fma2(pk(g.kv[ai], g.kv[ai]), win[o + d - SH::DMIN], acc);
           }
           const int ri = hi - i0;
-          if (ri >= 0 && ri < T) sV[v * SH::VS + ri * NVp + c] = acc;
+          if (ri >= 0 && ri < T) {
+            sV[ri * NVp + c] = acc.x;
+            if (two) sV[SH::VS + ri * NVp + c] = acc.y;
+          }
         }
       }
     }
@@ -485,25 +515,20 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
     const int n_lo = floor_div(j0, Z);
     const int TRr = min(T, JF(Hh) - i0);
     const bool full_cols = j0 + T <= JF(Wh);
-    const float tu0 = tu_of(kbase), tv0 = tv_of(kbase);
-    const int k1 = kbase + (nv > 1 ? 1 : 0);
-    const float tu1 = tu_of(k1), tv1 = tv_of(k1);
-    const bool two = nv > 1;
-    const bool same_row = tv1 == tv0;
+    const int k1 = kbase + (two ? 1 : 0);
+    const float2 tu2 = pk(tu_of(kbase), tu_of(k1)), tv2 = pk(tv_of(kbase), tv_of(k1));
+    const float2 S2 = pk(Sf, Sf);
     for (int t = tid; t < T * SH::NB6; t += FT_THREADS) {
       const int i = t % T, nb = t / T;
       if (i >= TRr) continue;
       const int n0 = n_lo + nb * SH::MB6;
       const int c0 = n0 + SH::DMIN - lc_lo + MG;     // in [0, NG - W6] for every tile
-      float win0[SH::W6], win1[SH::W6];
+      float2 win[SH::W6];
       {
         const float* v0 = sV + i * NVp + c0;
         const float* v1 = v0 + SH::VS;
 #pragma unroll
-        for (int w = 0; w < SH::W6; ++w) {
-          win0[w] = v0[w];
-          win1[w] = two ? v1[w] : 0.f;
-        }
+        for (int w = 0; w < SH::W6; ++w) win[w] = pk(v0[w], two ? v1[w] : 0.f);
       }
       const int hi = i0 + i;
       const float* orow = sO + (hi - e_r0) * NEp - e_c0;
@@ -513,11 +538,10 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
       bool pend0 = false, pend1 = false;
       int pr0 = 0, pc0 = 0, pr1 = 0, pc1 = 0;
       float pt0 = 0.f, pb0 = 0.f, pt1 = 0.f, pb1 = 0.f;
-      auto scatter = [&](float tval, int r, int c, float fy, float fx, bool& pend, int& pr_,
-                         int& pc_, float& pt, float& pb) {
-        const float ty = fy * tval, by = tval - ty;
-        float tl = by - fx * by, bl = ty - fx * ty;
-        const float tr = fx * by, br = fx * ty;
+      // tl, bl, tr, br: the bilinear weights times the value, for the taps
+      // (r, c), (r + 1, c), (r, c + 1), (r + 1, c + 1)
+      auto scatter = [&](float tl, float bl, float tr, float br, int r, int c, bool& pend,
+                         int& pr_, int& pc_, float& pt, float& pb) {
         const bool merged = pend && pr_ == r && pc_ == c;
         if (merged) {
           tl += pt;
@@ -536,27 +560,27 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
       };
       auto pixel = [&](int o, int ph) {
         const int hj = Z * (n0 + o) + ph;
-        float t0 = 0.f, t1 = 0.f;
+        float2 tv = pk(0.f, 0.f);          // the adjoint-blurred value of both views
 #pragma unroll
         for (int d = SH::DMIN; d <= SH::DMAX; ++d) {
           const int ai = ph + R - Z * d;
-          if (ai >= 0 && ai <= 2 * R) {
-            t0 = fmaf(g.kh[ai], win0[o + d - SH::DMIN], t0);
-            t1 = fmaf(g.kh[ai], win1[o + d - SH::DMIN], t1);
-          }
+          if (ai >= 0 && ai <= 2 * R) tv = fma2(pk(g.kh[ai], g.kh[ai]), win[o + d - SH::DMIN], tv);
         }
         const float om = orow[hj];
+        const float2 om2 = pk(om, om);
         const int cc = hj - j0;
-        int iy, ix;
-        float fy, fx;
-        split_shift(fmaf(tv0, om, Sf), iy, fy);
-        split_shift(fmaf(tu0, om, Sf), ix, fx);
-        scatter(t0, i + iy, cc + ix, fy, fx, pend0, pr0, pc0, pt0, pb0);
-        if (two) {
-          if (!same_row) split_shift(fmaf(tv1, om, Sf), iy, fy);
-          split_shift(fmaf(tu1, om, Sf), ix, fx);
-          scatter(t1, i + iy, cc + ix, fy, fx, pend1, pr1, pc1, pt1, pb1);
-        }
+        int iy0, iy1, ix0, ix1;
+        float2 fy, fx;
+        split_shift2(fma2(tv2, om2, S2), iy0, iy1, fy);
+        split_shift2(fma2(tu2, om2, S2), ix0, ix1, fx);
+        // weights: (1 - fx) is exact (fx is a multiple of the shift's ulp)
+        const float2 omfx = sub2(pk(1.f, 1.f), fx);
+        const float2 ty = mul2(fy, tv);
+        const float2 by = sub2(tv, ty);
+        const float2 tl = mul2(by, omfx), bl = mul2(ty, omfx);
+        const float2 tr = mul2(fx, by), br = mul2(fx, ty);
+        scatter(tl.x, bl.x, tr.x, br.x, i + iy0, cc + ix0, pend0, pr0, pc0, pt0, pb0);
+        if (two) scatter(tl.y, bl.y, tr.y, br.y, i + iy1, cc + ix1, pend1, pr1, pc1, pt1, pb1);
       };
       if (SH::ALIGNED && full_cols) {
 #pragma unroll
