@@ -528,6 +528,7 @@ int lfsr_batch_load(lfsr_batch* b, int job, const float* lr_views, const float* 
 }
 
 int lfsr_batch_iterate(lfsr_batch* b, int iterations) {
+  NvtxRange range("lfsr_batch_iterate");
   if (!b) return bfail(nullptr, LFSR_EINVAL, "batch is NULL");
   if (iterations < 0) return bfail(b, LFSR_EINVAL, "iterations must be >= 0");
   int left = iterations;

@@ -145,6 +145,7 @@ cudaError_t bw_normal(lfsr_handle* h, const OpArgs& a, cudaStream_t s) {
 template <class F>
 cudaError_t timed(lfsr_handle* h, cudaStream_t s, int cls, F&& launch) {
   if (!h->profiling) return launch();
+  NvtxRange range(kind_name(cls));
   ProfEvent ev{cls, nullptr, nullptr};
   cudaError_t e = cudaEventCreate(&ev.a);
   if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
@@ -866,6 +867,7 @@ void lfsr_destroy(lfsr_handle* h) {
 const char* lfsr_last_error(const lfsr_handle* h) { return h ? h->err.c_str() : t_err.c_str(); }
 
 int lfsr_load(lfsr_handle* h, const float* lr_views, const float* x0, int mem) {
+  NvtxRange range("lfsr_load (io: views and x0 in)");
   return load_state(h, lr_views, x0, mem, 0);
 }
 
@@ -901,6 +903,7 @@ int lfsr::load_state(lfsr_handle* h, const float* lr_views, const float* x0, int
 extern "C" {
 
 int lfsr_iterate(lfsr_handle* h, int iterations) {
+  NvtxRange range("lfsr_iterate (wz-step and x-step)");
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
   if (iterations < 0) return fail(h, LFSR_EINVAL, "iterations must be >= 0");
   if (h->profiling) {
@@ -943,6 +946,7 @@ static int read_status(lfsr_handle* h, DevScalars* hs) {
 }
 
 int lfsr_get_x(lfsr_handle* h, float* x_out, int mem) {
+  NvtxRange range("lfsr_get_x (io: x out)");
   if (!h) return fail(nullptr, LFSR_EINVAL, "handle is NULL");
   if (!x_out) return fail(h, LFSR_EINVAL, "x_out is NULL");
   if (check_mem(h, mem)) return LFSR_EINVAL;
@@ -953,6 +957,7 @@ int lfsr_get_x(lfsr_handle* h, float* x_out, int mem) {
 
 int lfsr_solve(lfsr_handle* h, const float* lr_views, int iterations, const float* x0,
                float* x_out, int mem) {
+  NvtxRange range("lfsr_solve");
   int rc = lfsr_load(h, lr_views, x0, mem);
   if (rc) return rc;
   rc = lfsr_iterate(h, iterations);

@@ -6,10 +6,31 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lfsr.h"
 #include "lfsr_internal.cuh"
 
 namespace lfsr {
+
+// NVTX range for the host-side phases (the paper splits a solve's time into
+// io, wz-step and x-step, Sec. 6): visible in a profiler's timeline, a no-op
+// without one attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+// Names of the launch classes (KD_*) in the profiling mode's NVTX ranges.
+inline const char* kind_name(int kind) {
+  static const char* names[] = {"nltv_block (z/w-step, regulariser rows)",
+                                "data_block (z/w-step, data rows; x-step init when fused)",
+                                "cg_init (x-step)", "nltv_apply (x-step, S^T W^2 S p)",
+                                "normal_apply (x-step, A^T A p; CG update when fused)",
+                                "cg_update (x-step)"};
+  return kind >= 0 && kind < 6 ? names[kind] : "lfsr";
+}
 
 struct ProfEvent {
   int cls;

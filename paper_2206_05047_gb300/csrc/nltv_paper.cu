@@ -47,7 +47,7 @@ __global__ void k_occlusion(const int Hh, const int Wh, const float* __restrict_
 // k_nlw2p<ONLY>: the stored edge weights alone.
 // Thread layout as k_nlw2: a strip of NF_PIX rows of one column per thread.
 template <int MODE, int WR, class ST>
-__global__ void __launch_bounds__(NF_THREADS)
+__global__ void __launch_bounds__(NF_THREADS, 2)   // two CTAs per SM: <= 64 registers
 k_nlw2p(const Geom g, const TableArgs tb) {
   using D = HalfDirs<WR>;
   // x over the tile + (WR + 1): central differences at the halo's g

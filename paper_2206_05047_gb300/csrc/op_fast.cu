@@ -92,7 +92,8 @@ cudaError_t fast_prepare(const Geom& g, int optin) {
 cudaError_t fast_plan(const Geom& g, OpPlan* P, int smem_limit) {
 #define X(z, k)                                                     \
   if (g.zeta == z && g.kb == k) {                                   \
-    if (fast_layout<z, k>(g, P) > (size_t)smem_limit)               \
+    if (fast_layout<z, k>(g, P, true) > (size_t)smem_limit &&       \
+        fast_layout<z, k>(g, P, false) > (size_t)smem_limit)        \
       return cudaErrorInvalidValue;                                 \
     P->ctas_per_sm = fast_occupancy<z, k>(P->smem_bytes);           \
     P->fast = 1;                                                    \

@@ -801,8 +801,12 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
 
 // Shared-memory layout and tiling of the specialised kernel for tile side
 // TILE (host side; S from g).
+// bank_pitch: the staged source's row pitch is congruent to NE modulo 32,
+// so that the warp-sample reads of consecutive sample indices t (rows of NE
+// samples wrap inside a warp) fall on bank t mod 32 where the shifts agree;
+// else the smallest odd pitch (less shared memory).
 template <int Z, int KB, int TILE = FAST_TILE>
-inline size_t fast_layout(const Geom& g, OpPlan* P) {
+inline size_t fast_layout(const Geom& g, OpPlan* P, bool bank_pitch = true) {
   using SH = FastShape<Z, KB, TILE>;
   const int S = g.S;
   auto al = [](size_t n) { return (n + 3) & ~(size_t)3; };
@@ -810,7 +814,8 @@ inline size_t fast_layout(const Geom& g, OpPlan* P) {
   P->NLr = P->NLc = SH::NL;
   P->NEr = P->NEc = SH::NE;
   P->NPr = SH::NE + 2 * S + 1;
-  P->NPc = (SH::NE + 2 * S + 2) | 1;         // +1: the last tap column; odd pitch
+  const int np = SH::NE + 2 * S + 2;         // +1: the last tap column
+  P->NPc = bank_pitch ? SH::NE + 32 * ((np - SH::NE + 31) / 32) : (np | 1);
   P->NAr = SH::T + 2 * S + 2;
   P->NAc = (SH::T + 2 * S + 2) | 1;
   size_t off = 0;

@@ -36,7 +36,9 @@ inline cudaError_t table_launch_zkt(int mode, const Geom& g, const OpPlan& P, co
 
 template <int Z, int KB, int TILE>
 inline cudaError_t table_plan_zkt(const Geom& g, OpPlan* P, int smem_limit) {
-  if (fast_layout<Z, KB, TILE>(g, P) > (size_t)smem_limit) return cudaErrorInvalidValue;
+  if (fast_layout<Z, KB, TILE>(g, P, true) > (size_t)smem_limit &&
+      fast_layout<Z, KB, TILE>(g, P, false) > (size_t)smem_limit)
+    return cudaErrorInvalidValue;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
           &n, k_operator_fast<OP_NORMAL, Z, KB, false, TILE>, FT_THREADS, P->smem_bytes) !=

@@ -227,6 +227,7 @@ int lfsr_server_submit(lfsr_server* s, const lfsr_params* params, const float* l
 }
 
 int lfsr_server_step(lfsr_server* s) {
+  NvtxRange range("lfsr_server_step (admit, step the active set, retire)");
   if (!s) return sfail(nullptr, LFSR_EINVAL, "server is NULL");
   std::lock_guard<std::mutex> lock(s->mu);
   admit(s);
