@@ -58,7 +58,7 @@ void free_all(lfsr_handle* h) {
   }
   void* bufs[] = {h->disp, h->y, h->x[0], h->x[1], h->wA[0], h->wA[1], h->wS[0],
                   h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt, h->V, h->occ,
-                  h->disp_views, h->hlr};
+                  h->disp_views, h->hlr, h->wt_map};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->partials) cudaFree(h->partials);
@@ -243,7 +243,9 @@ cudaError_t enqueue_iteration(lfsr_handle* h, int b, cudaStream_t s) {
   for (int k = 0; k < h->prm.cg_iters; ++k) {
     const int pb = k & 1;
     e = timed(h, s, KD_NLA, [&] {
-      if (h->nlf) return nla2_launch(g, handle_table(h, KD_NLA, b, pb), s);
+      if (h->nlf)
+        return h->nla_tma ? nla2t_launch(g, handle_table(h, KD_NLA, b, pb), s)
+                          : nla2_launch(g, handle_table(h, KD_NLA, b, pb), s);
       NlArgs na{};
       na.x = h->x[b];
       na.occ = h->occ;
@@ -560,7 +562,7 @@ int64_t lfsr::estimate_state_bytes(const lfsr_params* pr) {
               + 2 * es * nA      // data duals
               + 2 * es * nS      // regulariser duals
               + 4 * 4 * p;       // P ping-pong, R, Q
-  if (nlf) b += es * sh * p + 4 * p;       // stored weights, accumulated v
+  if (nlf) b += es * sh * p + 4 * p + 128; // stored weights, accumulated v, their tensor map
   if (paper) b += 4 * p;                    // occlusion factor
   if (pr->disparity_views) b += 4 * sk * p;  // per-view disparity maps
   if (pr->adjoint == LFSR_ADJOINT_BACKWARD_WARP) b += 4 * nA;   // LR buffer
@@ -651,6 +653,7 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
       j.p_new = h->P[pb];
       j.out = h->Q;
       j.wt = h->wt;
+      j.wt_map = h->nla_tma ? h->wt_map : nullptr;
       break;
     case KD_NORMAL:  // q += cA sum_k A_k^T A_k p
       j.tiles_x = h->op.tiles_x;
@@ -723,6 +726,7 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   }
   e = op_prepare(g, optin);
   if (e == cudaSuccess) e = nl_prepare(optin);
+  if (e == cudaSuccess && nla2t_supported(g)) e = nla2t_prepare(optin);
   if (e == cudaSuccess && g.adjoint_bw) e = bw_prepare(optin);
   if (e != cudaSuccess) {
     rc = cuda_fail(nullptr, e, "kernel attributes");
@@ -800,6 +804,18 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   // V (stored-weight NLTV path)
   h->fused_init = h->fused && h->nlf;
   if (e == cudaSuccess && h->nlf) e = dalloc_st(h, &h->wt, (size_t)g.sh * p, h->esize);
+  // the NLTV apply stages the weight planes with TMA when their rows are
+  // 16-byte multiples: its tensor map lives in device memory for the jobs
+  if (e == cudaSuccess && h->nlf && nla2t_supported(g)) {
+    unsigned char map[NLA_TMA_MAP_BYTES];
+    if (nla2t_make_map(g, h->wt, map) == cudaSuccess) {
+      e = dalloc(h, &h->wt_map, (size_t)NLA_TMA_MAP_BYTES);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->wt_map, map, NLA_TMA_MAP_BYTES, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // map is a stack buffer
+      h->nla_tma = e == cudaSuccess;
+    }
+  }
   if (e == cudaSuccess && h->nlf) e = dalloc(h, &h->V, p);
   if (e == cudaSuccess && h->nlf) e = cudaMemsetAsync(h->V, 0, p * sizeof(float), h->stream);
   if (e == cudaSuccess && g.wscheme == WS_PAPER) e = dalloc(h, &h->occ, p);

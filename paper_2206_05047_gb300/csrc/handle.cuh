@@ -77,6 +77,8 @@ struct lfsr_handle {
   void* wS[2] = {nullptr, nullptr};
   void* wt = nullptr;   // stored NLTV edge weights [s_d/2][p] (when supported)
   bool nlf = false;
+  unsigned char* wt_map = nullptr;   // tensor map of the weight planes (TMA NLTV apply)
+  bool nla_tma = false;              // the NLTV apply stages the weights with TMA
   bool fused = false;   // the normal-matrix launch finishes each CG step (no update launch)
   bool fused_init = false;   // the data launch does the x-step initialisation (no init launch)
   float* io = nullptr;  // staging for host <-> device and layout conversion

@@ -167,6 +167,9 @@ struct JobArgs {
   int fuse;
   int fchunk;
   double* fpart;
+  // NLTV apply with TMA-staged weights: the device address of the weight
+  // planes' tensor map (a CUtensorMap, 64-byte aligned), or NULL.
+  const void* wt_map;
 };
 
 // Launch-wide arguments of a table-driven kernel.
@@ -220,6 +223,15 @@ cudaError_t nlw2_launch(int block, const Geom& g, const TableArgs& t, cudaStream
 // chunk: directions per batch of weight loads, 6 (default) or 3.
 constexpr int NLA_CHUNK = 6;
 cudaError_t nla2_launch(const Geom& g, const TableArgs& t, cudaStream_t s, int chunk = NLA_CHUNK);
+// The same with the weights staged by TMA (nltv_tma.cu): needs every job's
+// wt_map, a row of the weight planes a multiple of 16 bytes and the driver's
+// tensor-map encoder.  The map covers the s_d/2 planes of wt (kind g.st);
+// map_out is host memory of sizeof(CUtensorMap) = 128 bytes.
+constexpr int NLA_TMA_MAP_BYTES = 128;
+bool nla2t_supported(const Geom& g);
+cudaError_t nla2t_prepare(int smem_optin);
+cudaError_t nla2t_make_map(const Geom& g, const void* wt, void* map_out);
+cudaError_t nla2t_launch(const Geom& g, const TableArgs& t, cudaStream_t s);
 // x-step initialisation from the accumulated v (jobs' vacc): r = -v, v := 0.
 cudaError_t cg_init_acc_launch(const Geom& g, const TableArgs& t, cudaStream_t s);
 // The paper's weights (g.wscheme == WS_PAPER): the stored-weight

@@ -30,6 +30,10 @@ SMALL = [
                             disparities=(0.0, 0.5)), None),
     ("x2_big_shift", dict(U=7, V=3, H=12, W=40, scale=2, kb=3, blur_sigma=0.8, window=3,
                           disparities=(-3.6, 2.9)), None),
+    # rows of 40 floats (16-byte multiples): the NLTV apply stages its weight
+    # planes with TMA; ragged 32 x 32 tiles in both directions, 7x7 window
+    ("x2_tma_ragged", dict(U=3, V=3, H=22, W=20, scale=2, kb=5, blur_sigma=1.0, window=7,
+                           disparities=(-0.9, 0.7)), None),
     # 9x9 window: the generic NLTV kernel (weights recomputed per direction)
     ("x2_window9", dict(U=3, V=3, H=12, W=13, scale=2, kb=3, blur_sigma=0.8, window=9,
                         disparities=(-0.7, 0.9)), None),

@@ -101,6 +101,10 @@ ONE_ITER = [
                        disparities=(-0.6, 1.2)), "motion"),
     ("x2_window9", dict(U=3, V=3, H=12, W=13, scale=2, kb=3, blur_sigma=0.8, window=9,
                         disparities=(-0.7, 0.9)), None),
+    # rows of 40 16-bit weights (80 bytes): the NLTV apply stages them with
+    # TMA; ragged tiles, 7x7 window
+    ("x2_tma_ragged", dict(U=3, V=3, H=22, W=20, scale=2, kb=5, blur_sigma=1.0, window=7,
+                           disparities=(-0.9, 0.7)), None),
 ]
 # rel-L2 bounds of one iteration: outputs rounded once, plus the rounded
 # weights / divergence terms inside the x-step
