@@ -205,6 +205,7 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
   static_assert(VB == 2, "the sample and scatter stages handle view pairs");
   int cur_tile = -1;
   int i0 = 0, j0 = 0, lr_lo = 0, lr_n = 0, lc_lo = 0, lc_n = 0, e_r0 = 0, e_c0 = 0;
+  int or0 = 0, or1 = 0, oc0 = 0, oc1 = 0;   // LR rows / columns owned by the tile (grid-local)
   int NAr_t = 0, NAc_t = 0;
   // this thread's warp-sample positions (fixed for all views of a tile):
   // staged-source index of the (0, 0) tap before the shift, and disparity
@@ -280,6 +281,12 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
       lc_n = min(JF(W) - 1, floor_div(j0 + TRc - 1 + R, Z)) - lc_lo + 1;
       e_r0 = Z * lr_lo - R;
       e_c0 = Z * lc_lo - R;
+      // LR pixel (gr, gc) belongs to the tile when its HR position (Z gr, Z gc)
+      // lies in it: gr in [ceil(i0 / Z), ceil((i0 + T) / Z))
+      or0 = ceil_div(i0, Z) - lr_lo;
+      or1 = ceil_div(i0 + T, Z) - lr_lo;
+      oc0 = ceil_div(j0, Z) - lc_lo;
+      oc1 = ceil_div(j0 + T, Z) - lc_lo;
       NAr_t = TRr + 2 * S + 1;
       NAc_t = TRc + 2 * S + 1;
       // stage the source (zero outside the image) and the disparity with
@@ -417,6 +424,7 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
         if (v >= nv) break;
         const int lc = r3 % NL, rb = r3 / NL;
         const int k = kbase + v;
+        const bool col_in = lc < lc_n, col_own = lc >= oc0 && lc < oc1;
         const float* hcol = sH + v * SH::HS + (Z * SH::MB3 * rb) * NHp + lc;
         float win[SH::W3];
 #pragma unroll
@@ -429,10 +437,9 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
 #pragma unroll
           for (int b = 0; b < KB; ++b) acc = fmaf(g.kv[b], win[Z * o + b], acc);
           float h = 0.f;
-          if (lr < lr_n && lc < lc_n) {
+          if (lr < lr_n && col_in) {
             const int gr = lr_lo + lr, gc = lc_lo + lc;
-            const bool owned = (Z * gr >= i0) && (Z * gr < i0 + T) && (Z * gc >= j0) &&
-                               (Z * gc < j0 + T);
+            const bool owned = col_own && lr >= or0 && lr < or1;
             h = acc;
             if (MODE == OP_NORMAL) {
               if (owned) psum = fmaf(acc, acc, psum);
@@ -543,15 +550,15 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
       auto scatter = [&](float tl, float bl, float tr, float br, int r, int c, bool& pend,
                          int& pr_, int& pc_, float& pt, float& pb) {
         const bool merged = pend && pr_ == r && pc_ == c;
-        if (merged) {
-          tl += pt;
-          bl += pb;
-        } else if (pend) {
+        if (pend && !merged) {
           atomicAdd(sA + pr_ * NAc + pc_, pt);
           atomicAdd(sA + (pr_ + 1) * NAc + pc_, pb);
         }
-        atomicAdd(sA + r * NAc + c, tl);
-        atomicAdd(sA + (r + 1) * NAc + c, bl);
+        tl += merged ? pt : 0.f;
+        bl += merged ? pb : 0.f;
+        float* a = sA + r * NAc + c;
+        atomicAdd(a, tl);
+        atomicAdd(a + NAc, bl);
         pend = true;
         pr_ = r;
         pc_ = c + 1;
