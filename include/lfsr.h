@@ -200,6 +200,15 @@ typedef struct lfsr_stats_t {
    * 3 nltv-apply, 4 normal-apply, 5 cg-update                              */
   double kernel_ms[8];
   int64_t kernel_launches[8];
+  /* load balance of the specialised operator launches, measured once by
+   * lfsr_create (one launch that times every (tile, view pair) unit): the
+   * slowest CTA's cost over the mean for the even split of the units and
+   * for the cost-balanced contiguous ranges the launches use (equal when
+   * the balanced ranges would not be faster and the even split stays);
+   * 0 when not measured (generic operator kernel, or fewer than two units
+   * per CTA)                                                               */
+  double op_split_even;
+  double op_split_balanced;
 } lfsr_stats_t;
 
 /* Creates a solver for one light-field geometry.  Copies blur and

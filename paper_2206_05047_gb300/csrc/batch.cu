@@ -472,7 +472,7 @@ int lfsr_batch_create(const lfsr_params* params, int n, void* cuda_stream, lfsr_
   b->cg_iters = params[0].cg_iters;
   for (int j = 0; j < n; ++j) {
     lfsr_handle* h = nullptr;
-    const int rc = lfsr_create(&params[j], cuda_stream, &h);
+    const int rc = create_handle(&params[j], cuda_stream, &h, false);
     if (rc != LFSR_OK) {
       const std::string msg = std::string("light field ") + std::to_string(j) + ": " +
                               lfsr_last_error(nullptr);

@@ -1,6 +1,7 @@
 // C ABI of liblfsr: handle, validation, device state, the ADMM iteration
 // schedule (Algorithm 1 with the CG x-step of Algorithm 2) and its CUDA-graph
 // replay.  See include/lfsr.h for the contract of every entry point.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <mutex>
@@ -58,7 +59,7 @@ void free_all(lfsr_handle* h) {
   }
   void* bufs[] = {h->disp, h->y, h->x[0], h->x[1], h->wA[0], h->wA[1], h->wS[0],
                   h->wS[1], h->R, h->P[0], h->P[1], h->Q, h->io, h->wt, h->V, h->occ,
-                  h->disp_views, h->hlr, h->wt_map};
+                  h->disp_views, h->hlr, h->wt_map, h->cta_unit0};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->partials) cudaFree(h->partials);
@@ -430,6 +431,146 @@ JobArgs standalone_job(const lfsr_handle* h) {
 
 }  // namespace
 
+namespace {
+
+// Cost-balanced split of the operator units over the CTAs of one light
+// field.  A unit is one (64 x 64 tile, view pair); a CTA takes a contiguous
+// range (consecutive pairs of a tile share its staged source and its
+// scatter accumulator).  Units differ in cost with their tile's disparity
+// content (the spread of the sub-pixel shifts decides how many scatter
+// taps merge and how often shared-memory accesses collide), and a CTA pays
+// for staging and flushing each tile it starts.  The even split leaves the
+// slowest CTA well above the mean, and every fused CG step waits at its
+// grid barrier for the slowest one.
+//
+// Measured once per handle: a normal-matrix launch on the even split
+// records the SM clock at the start of every unit and at the end of each
+// CTA's range.  Unit costs follow from the differences; the cost of a tile
+// switch is the median excess of a range's tile-starting unit over the
+// next unit.  The ranges are then the contiguous split with the smallest
+// maximum predicted cost (bisection on that maximum, greedy packing), kept
+// only when it predicts a lower maximum than the even split.
+struct SplitCost {
+  std::vector<double> base;   // per unit, without tile staging
+  double sw = 0.0;            // staging and flushing one tile
+  int upt = 1;                // units per tile
+};
+
+// CTAs that greedy packing with at most `cap` per CTA needs (starts filled
+// in when non-NULL).
+int pack_units(const SplitCost& c, double cap, std::vector<int>* starts) {
+  const int units = (int)c.base.size();
+  int ctas = 0;
+  double cur = 0.0;
+  bool open = false;
+  for (int u = 0; u < units; ++u) {
+    const double add = c.base[u] + (u % c.upt == 0 ? c.sw : 0.0);
+    if (!open || cur + add > cap) {
+      if (starts) starts->push_back(u);
+      ++ctas;
+      open = true;
+      cur = c.base[u] + c.sw;   // a range's first unit stages its tile
+    } else {
+      cur += add;
+    }
+  }
+  return ctas;
+}
+
+cudaError_t balance_operator_units(lfsr_handle* h) {
+  const int units = h->op_units, grid = h->grid_op;
+  const size_t bytes = (size_t)(units + grid) * sizeof(long long);
+  // nothing to balance with fewer than two units per CTA; the clocks go to
+  // R, which is unused until the first load (8-byte aligned: cudaMalloc)
+  if (!h->fused || units < 2 * grid || bytes > h->p * sizeof(float)) return cudaSuccess;
+  long long* clk = reinterpret_cast<long long*>(h->R);
+  JobArgs j = make_job(h, KD_NORMAL, 0, 0, 0);
+  j.fuse = 0;             // the operator part alone (P[0] is zero, Q scratch)
+  j.cta_unit0 = nullptr;  // the even split
+  j.sc = h->sc + 1;       // its <p, M p> = 0 ends an x-step: not the solver's scalars
+  TableArgs t = handle_table(h, KD_NORMAL, 0, 0);
+  t.check_done = 0;       // (the warm-up launch has ended the x-step of sc[1])
+  cudaError_t e = fast_launch(OP_NORMAL, h->g, h->op, t, grid, h->stream, &j);   // warm-up
+  j.unit_clock = clk;
+  if (e == cudaSuccess) e = fast_launch(OP_NORMAL, h->g, h->op, t, grid, h->stream, &j);
+  std::vector<long long> c((size_t)units + grid);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c.data(), clk, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->sc, 0, 2 * sizeof(DevScalars), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return e;
+
+  SplitCost sc;
+  sc.upt = std::max(1, units / std::max(1, h->op.n_tiles));
+  std::vector<double> cost(units);
+  std::vector<char> staged(units, 0);
+  std::vector<double> even(grid, 0.0);
+  std::vector<double> excess;
+  for (int b = 0; b < grid; ++b) {
+    const int ub = (int)((long long)b * units / grid), ue = (int)((long long)(b + 1) * units / grid);
+    for (int u = ub; u < ue; ++u) {
+      const long long next = u + 1 < ue ? c[u + 1] : c[(size_t)units + b];
+      cost[u] = next > c[u] ? (double)(next - c[u]) : 1.0;
+      staged[u] = (u == ub || u % sc.upt == 0) ? 1 : 0;
+      even[b] += cost[u];
+    }
+    for (int u = ub; u + 1 < ue; ++u)
+      if (staged[u] && !staged[u + 1] && (u + 1) / sc.upt == u / sc.upt)
+        excess.push_back(cost[u] - cost[u + 1]);
+  }
+  if (!excess.empty()) {
+    std::nth_element(excess.begin(), excess.begin() + excess.size() / 2, excess.end());
+    sc.sw = std::max(0.0, excess[excess.size() / 2]);
+  }
+  sc.base.resize(units);
+  double total = 0.0, lo = 0.0;
+  for (int u = 0; u < units; ++u) {
+    sc.base[u] = std::max(1.0, cost[u] - (staged[u] ? sc.sw : 0.0));
+    total += sc.base[u] + (u % sc.upt == 0 ? sc.sw : 0.0);
+    lo = std::max(lo, sc.base[u] + sc.sw);
+  }
+  double hi = total + grid * sc.sw;
+  for (int it = 0; it < 60 && hi - lo > 1e-6 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (pack_units(sc, mid, nullptr) <= grid) hi = mid;
+    else lo = mid;
+  }
+  std::vector<int> starts;
+  pack_units(sc, hi, &starts);
+  if ((int)starts.size() > grid) return cudaSuccess;   // (cannot happen: hi is feasible)
+  // predicted cost of each balanced range
+  double bal_max = 0.0, bal_sum = 0.0;
+  for (size_t r = 0; r < starts.size(); ++r) {
+    const int ue = r + 1 < starts.size() ? starts[r + 1] : units;
+    double v = sc.sw;
+    for (int u = starts[r]; u < ue; ++u)
+      v += sc.base[u] + (u > starts[r] && u % sc.upt == 0 ? sc.sw : 0.0);
+    bal_max = std::max(bal_max, v);
+    bal_sum += v;
+  }
+  double even_max = 0.0, even_sum = 0.0;
+  for (double v : even) {
+    even_max = std::max(even_max, v);
+    even_sum += v;
+  }
+  h->op_split[0] = even_max / (even_sum / grid);
+  h->op_split[1] = bal_max / (bal_sum / grid);
+  if (!(bal_max < 0.99 * even_max)) {
+    h->op_split[1] = h->op_split[0];
+    return cudaSuccess;
+  }
+  std::vector<int> r0(grid + 1, units);
+  for (size_t r = 0; r < starts.size(); ++r) r0[r] = starts[r];
+  r0[0] = 0;
+  e = dalloc(h, &h->cta_unit0, (size_t)grid + 1);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->cta_unit0, r0.data(), r0.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // r0 is a local buffer
+  return e;
+}
+
+}  // namespace
+
 int lfsr::geom_from_params(const lfsr_params* pr, Geom* out) {
   int rc = validate(pr);
   if (rc != LFSR_OK) return rc;
@@ -570,6 +711,7 @@ int64_t lfsr::estimate_state_bytes(const lfsr_params* pr) {
   b += (int64_t)RED_NUM * 8 * (nl_tiles > 4096 ? nl_tiles : 4096);   // reduction slots (bound)
   b += 2 * (int64_t)sizeof(DevScalars) + (4 * KD_NUM + 4) * (int64_t)sizeof(JobArgs) +
        (KD_NUM + 4) * 4 + 8 * sk;
+  b += 4 * (4096 + 1);                      // balanced operator ranges (bound)
   return b;
 }
 
@@ -621,6 +763,7 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
       break;
     case KD_DATA:  // data rows, v += A^T (...)
       j.tiles_x = h->op.tiles_x;
+      j.cta_unit0 = h->cta_unit0;
       j.view0 = 0;
       j.nviews = g.sk;
       j.scale = 1.f;
@@ -657,6 +800,7 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
       break;
     case KD_NORMAL:  // q += cA sum_k A_k^T A_k p
       j.tiles_x = h->op.tiles_x;
+      j.cta_unit0 = h->cta_unit0;
       j.view0 = 0;
       j.nviews = g.sk;
       j.scale = g.cA;
@@ -686,6 +830,13 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
 extern "C" {
 
 int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
+  return create_handle(pr, cuda_stream, out, true);
+}
+
+}  // extern "C"
+
+int lfsr::create_handle(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out,
+                        bool balance) {
   if (!out) return fail(nullptr, LFSR_EINVAL, "out is NULL");
   *out = nullptr;
   Geom geom{};
@@ -863,6 +1014,16 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(h->P[0], 0, p * sizeof(float), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->P[1], 0, p * sizeof(float), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && balance) e = balance_operator_units(h);
+  if (e == cudaSuccess && h->cta_unit0) {   // the operator jobs take the balanced ranges
+    for (int b = 0; b < 2; ++b)
+      for (int pb = 0; pb < 2; ++pb)
+        for (int kd = 0; kd < KD_NUM; ++kd)
+          h->jobs_host[(2 * b + pb) * KD_NUM + kd] = make_job(h, kd, b, pb, 0);
+    e = cudaMemcpyAsync(h->jobs_dev, h->jobs_host.data(), h->jobs_host.size() * sizeof(JobArgs),
+                        cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
   if (e != cudaSuccess) {
     rc = cuda_fail(nullptr, e, "lfsr_create");
     free_all(h);
@@ -872,6 +1033,8 @@ int lfsr_create(const lfsr_params* pr, void* cuda_stream, lfsr_handle** out) {
   *out = h;
   return LFSR_OK;
 }
+
+extern "C" {
 
 void lfsr_destroy(lfsr_handle* h) {
   if (!h) return;
@@ -1006,6 +1169,8 @@ int lfsr_stats(const lfsr_handle* hc, lfsr_stats_t* out) {
   out->cg_pi = hs.pi;
   out->state_bytes = h->state_bytes;
   out->launches = h->launches;
+  out->op_split_even = h->op_split[0];
+  out->op_split_balanced = h->op_split[1];
   for (int c = 0; c < NUM_CLASSES; ++c) {
     out->kernel_ms[c] = h->prof_ms[c];
     out->kernel_launches[c] = h->prof_n[c];

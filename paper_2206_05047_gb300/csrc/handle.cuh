@@ -104,6 +104,8 @@ struct lfsr_handle {
   int vec_chunk = 0, vec_units = 0;         // HR pixels per vector-kernel CTA, CTAs
   int upd_chunk = 0, upd_units = 0;         // the same for the CG update (one CTA per SM)
   int fchunk = 0;                           // HR pixels per CTA of the fused operator tails
+  int* cta_unit0 = nullptr;                 // cost-balanced operator ranges (grid_op + 1), or NULL
+  double op_split[2] = {0.0, 0.0};          // max / mean CTA cost: even split, balanced ranges
   bool profiling = false;
   std::vector<lfsr::ProfEvent> prof;
   double prof_ms[8] = {0};
@@ -117,6 +119,10 @@ namespace lfsr {
 // writes state 1 - b) and CG direction parity pb, for a table whose first
 // unit of this light field is unit0.
 JobArgs make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0);
+// lfsr_create; balance: measure the operator units' costs and split them
+// over the CTAs by cost (single-light-field launches; light fields that run
+// only inside batch tables skip it).
+int create_handle(const lfsr_params* params, void* cuda_stream, lfsr_handle** out, bool balance);
 // Work units of a launch kind for this light field.
 int kind_units(const lfsr_handle* h, int kind);
 // Reduction slot (RED_*) of a launch kind.

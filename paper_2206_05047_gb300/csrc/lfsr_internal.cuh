@@ -170,6 +170,14 @@ struct JobArgs {
   // NLTV apply with TMA-staged weights: the device address of the weight
   // planes' tensor map (a CUtensorMap, 64-byte aligned), or NULL.
   const void* wt_map;
+  // Operator launches of one light field: the first unit of each CTA's
+  // contiguous range (grid + 1 entries, cut where the measured cost of the
+  // units crosses multiples of total / grid), or NULL for the even split;
+  // when unit_clock is not NULL, the kernel records there the SM clock at
+  // the start of each unit and (after the units) at the end of each CTA's
+  // range.
+  const int* cta_unit0;
+  long long* unit_clock;
 };
 
 // Launch-wide arguments of a table-driven kernel.

@@ -119,7 +119,7 @@ int admit(lfsr_server* s) {
       p.views = r.view_list.empty() ? nullptr : r.view_list.data();
       p.proj_err = r.proj_err.empty() ? nullptr : r.proj_err.data();
       lfsr_handle* h = nullptr;
-      int rc = lfsr_create(&p, s->stream, &h);
+      int rc = create_handle(&p, s->stream, &h, false);
       if (rc == LFSR_OK && (!h->op.fast || !h->nlf)) rc = LFSR_EUNSUPPORTED;
       const int parity = s->batch ? batch_parity(s->batch) : 0;
       if (rc == LFSR_OK)

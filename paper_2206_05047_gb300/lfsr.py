@@ -78,7 +78,8 @@ class lfsr_stats_t(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("iterations", C.c_int32), ("cg_steps", C.c_int32),
                 ("status", C.c_int32), ("dual_change_sq", C.c_double), ("cg_pi", C.c_double),
                 ("state_bytes", C.c_int64), ("launches", C.c_int64),
-                ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_int64 * 8)]
+                ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_int64 * 8),
+                ("op_split_even", C.c_double), ("op_split_balanced", C.c_double)]
 
 
 class lfsr_server_config(C.Structure):
@@ -357,7 +358,8 @@ def stats(handle) -> dict:
     return dict(iterations=st.iterations, cg_steps=st.cg_steps, status=st.status,
                 dual_change_sq=st.dual_change_sq, cg_pi=st.cg_pi, state_bytes=st.state_bytes,
                 launches=st.launches, kernel_ms=list(st.kernel_ms),
-                kernel_launches=list(st.kernel_launches))
+                kernel_launches=list(st.kernel_launches), op_split_even=st.op_split_even,
+                op_split_balanced=st.op_split_balanced)
 
 
 def apply_normal_noalloc(U, V, H, W, scale, blur, disparity, d_disparity, xw, p, q,

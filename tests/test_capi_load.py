@@ -35,7 +35,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(lfsr.lfsr_params) == 168
     assert lfsr.lfsr_params.weights.offset == 124 and lfsr.lfsr_params.proj_err.offset == 144
     assert lfsr.lfsr_params.disparity_views.offset == 152 and lfsr.lfsr_params.adjoint.offset == 160
-    assert C.sizeof(lfsr.lfsr_stats_t) == 4 * 4 + 8 * 2 + 8 * 2 + 8 * 8 + 8 * 8
+    assert C.sizeof(lfsr.lfsr_stats_t) == 4 * 4 + 8 * 2 + 8 * 2 + 8 * 8 + 8 * 8 + 8 * 2
 
 
 def test_invalid_arguments_fail_without_gpu():
