@@ -33,6 +33,8 @@ struct Group {
   std::vector<int> unit0;   // first operator unit of each member
   std::vector<int> units_m; // operator units of each member at this tile side
   std::vector<int> tiles_x; // tile columns of each member at this tile side
+  int* cta_unit0 = nullptr; // cost-balanced CTA ranges of the operator launches (grid + 1), or NULL
+  double split[2] = {0.0, 0.0};   // slowest CTA over the mean: even split, balanced
 };
 
 }  // namespace
@@ -94,8 +96,18 @@ void drop_events(lfsr_batch* b) {
   b->prof.clear();
 }
 
+// Drops the balanced operator ranges (they belong to one table layout).
+void free_ranges(lfsr_batch* b) {
+  for (Group& gr : b->groups) {
+    if (gr.cta_unit0) cudaFree(gr.cta_unit0);
+    gr.cta_unit0 = nullptr;
+    gr.split[0] = gr.split[1] = 0.0;
+  }
+}
+
 void batch_free(lfsr_batch* b) {
   drop_events(b);
+  free_ranges(b);
   if (b->graph_pair) cudaGraphExecDestroy(b->graph_pair);
   for (auto& gs : b->graph_single)
     if (gs) cudaGraphExecDestroy(gs);
@@ -155,10 +167,10 @@ cudaError_t batch_iteration(lfsr_batch* b, int pa, cudaStream_t s, std::vector<P
   for (int gi = 0; gi < G && e == cudaSuccess; ++gi) {
     const Group& gr = b->groups[gi];
     e = run(KD_DATA, gi, [&] {
-      return fast_launch(OP_DATA, gr.g, gr.P,
-                         table(b, b->t_data[pa][gi], (int)gr.members.size(), gr.units,
-                               b->m_op[gi], KD_DATA, ctr(KD_DATA, gi), 0),
-                         gr.grid, s, nullptr);
+      TableArgs t = table(b, b->t_data[pa][gi], (int)gr.members.size(), gr.units, b->m_op[gi],
+                          KD_DATA, ctr(KD_DATA, gi), 0);
+      t.cta_unit0 = gr.cta_unit0;
+      return fast_launch(OP_DATA, gr.g, gr.P, t, gr.grid, s, nullptr);
     });
   }
   if (e == cudaSuccess)
@@ -177,10 +189,10 @@ cudaError_t batch_iteration(lfsr_batch* b, int pa, cudaStream_t s, std::vector<P
     for (int gi = 0; gi < G && e == cudaSuccess; ++gi) {
       const Group& gr = b->groups[gi];
       e = run(KD_NORMAL, gi, [&] {
-        return fast_launch(OP_NORMAL, gr.g, gr.P,
-                           table(b, b->t_norm[pa][pb][gi], (int)gr.members.size(), gr.units,
-                                 b->m_op[gi], KD_NORMAL, ctr(KD_NORMAL, gi), 1),
-                           gr.grid, s, nullptr);
+        TableArgs t = table(b, b->t_norm[pa][pb][gi], (int)gr.members.size(), gr.units,
+                            b->m_op[gi], KD_NORMAL, ctr(KD_NORMAL, gi), 1);
+        t.cta_unit0 = gr.cta_unit0;
+        return fast_launch(OP_NORMAL, gr.g, gr.P, t, gr.grid, s, nullptr);
       });
     }
     if (e == cudaSuccess)
@@ -217,6 +229,12 @@ cudaError_t set_tile(lfsr_batch* b, Group& gr, int tile) {
   OpPlan P{};
   cudaError_t e = fast_plan_table(gr.g, &P, b->smem_limit, tile);
   if (e != cudaSuccess) return e;
+  if (gr.cta_unit0) {   // ranges of the old unit count: the even split until rebalanced
+    cudaStreamSynchronize(b->stream);
+    cudaFree(gr.cta_unit0);
+    gr.cta_unit0 = nullptr;
+    gr.split[0] = gr.split[1] = 0.0;
+  }
   gr.P = P;
   gr.tile = tile;
   gr.units = 0;
@@ -236,9 +254,54 @@ cudaError_t set_tile(lfsr_batch* b, Group& gr, int tile) {
   return cudaSuccess;
 }
 
+// Cost-balanced CTA ranges of each operator group (see lfsr::split_by_cost):
+// two timing launches of the group's normal-matrix table (the second one
+// measured; timing launches leave the light fields' scalars alone, and q is
+// scratch between CG steps).  Groups with fewer than two units per CTA, or
+// whose balanced split would not be faster, keep the even split.
+cudaError_t balance_groups(lfsr_batch* b) {
+  const int G = (int)b->groups.size();
+  cudaError_t e = cudaSuccess;
+  for (int gi = 0; gi < G && e == cudaSuccess; ++gi) {
+    Group& gr = b->groups[gi];
+    if (gr.units < 2 * gr.grid) continue;
+    const size_t n = (size_t)gr.units + gr.grid;
+    long long* clk = nullptr;
+    e = fault_alloc() ? cudaErrorMemoryAllocation : cudaMalloc((void**)&clk, n * sizeof(long long));
+    if (e != cudaSuccess) break;
+    TableArgs t = table(b, b->t_norm[0][0][gi], (int)gr.members.size(), gr.units, b->m_op[gi],
+                        KD_NORMAL, KD_NORMAL * (G + 1) + gi, 0);
+    t.unit_clock = clk;
+    e = fast_launch(OP_NORMAL, gr.g, gr.P, t, gr.grid, b->stream, nullptr);   // warm-up
+    if (e == cudaSuccess) e = fast_launch(OP_NORMAL, gr.g, gr.P, t, gr.grid, b->stream, nullptr);
+    std::vector<long long> c(n);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c.data(), clk, n * sizeof(long long), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(clk);
+    if (e != cudaSuccess) break;
+    // a tile starts every (views + 1) / 2 units of each member
+    std::vector<char> tile_start(gr.units, 0);
+    for (size_t m = 0; m < gr.members.size(); ++m) {
+      const int pairs = (b->jobs[gr.members[m]]->g.sk + FAST_VIEWS - 1) / FAST_VIEWS;
+      for (int u = 0; u < gr.units_m[m]; u += pairs) tile_start[gr.unit0[m] + u] = 1;
+    }
+    std::vector<int> r0;
+    if (!split_by_cost(c, gr.units, gr.grid, tile_start, &r0, gr.split)) continue;
+    e = fault_alloc() ? cudaErrorMemoryAllocation
+                      : cudaMalloc((void**)&gr.cta_unit0, r0.size() * sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(gr.cta_unit0, r0.data(), r0.size() * sizeof(int), cudaMemcpyHostToDevice,
+                          b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // r0 is a local buffer
+  }
+  return e;
+}
+
 // Builds the job tables and unit maps of every launch for the current tile
 // sides, uploads them (growing the device buffers when needed) and drops
-// the captured graphs, which hold the old launch shapes.
+// the captured graphs, which hold the old launch shapes.  A batch that owns
+// its light fields then balances its operator groups' CTA ranges.
 cudaError_t build_tables(lfsr_batch* b) {
   const int n = (int)b->jobs.size();
   std::vector<JobArgs> tabs;
@@ -294,6 +357,7 @@ cudaError_t build_tables(lfsr_batch* b) {
     if (gr.members.size() * (size_t)gr.grid > stride) stride = gr.members.size() * (size_t)gr.grid;
   b->part_stride = stride;
   cudaError_t e = cudaStreamSynchronize(b->stream);   // no launch may still read the old tables
+  free_ranges(b);                                    // (they belong to the old layout)
   auto grow = [&](auto** buf, size_t* cap, size_t need, size_t elem) {
     if (e != cudaSuccess || need <= *cap) return;
     if (*buf) cudaFree(*buf);
@@ -318,6 +382,7 @@ cudaError_t build_tables(lfsr_batch* b) {
     if (gs) cudaGraphExecDestroy(gs);
     gs = nullptr;
   }
+  if (e == cudaSuccess && b->owns_jobs) e = balance_groups(b);
   return e;
 }
 
@@ -359,6 +424,8 @@ cudaError_t lfsr::batch_assign(lfsr_batch* b, const std::vector<lfsr_handle*>& j
     if (!found) b->tuned_tiles.emplace_back(gr.g, gr.tile);
   }
   if (&jobs != &b->jobs) b->jobs = jobs;
+  cudaStreamSynchronize(b->stream);
+  free_ranges(b);
   b->groups.clear();
   b->nl_unit0.clear();
   b->vec_unit0.clear();
@@ -578,6 +645,13 @@ int lfsr_batch_stats(const lfsr_batch* bc, int job, lfsr_stats_t* out) {
   const int rc = lfsr_stats(b->jobs[job], out);
   if (rc != LFSR_OK) return bfail(b, rc, lfsr_last_error(b->jobs[job]));
   out->launches = 0;
+  out->op_split_even = out->op_split_balanced = 0.0;   // the batch's ranges: its group's
+  for (const Group& gr : b->groups)
+    for (int m : gr.members)
+      if (m == job) {
+        out->op_split_even = gr.split[0];
+        out->op_split_balanced = gr.split[1];
+      }
   return LFSR_OK;
 }
 
@@ -678,6 +752,11 @@ int lfsr_batch_set_tuning(lfsr_batch* b, const int* op_tile, int n_groups, int n
   for (int gi = 0; gi < n_groups; ++gi)
     if (op_tile[gi] != 64 && op_tile[gi] != 32)
       return bfail(b, LFSR_EINVAL, "operator tile sides are 64 or 32");
+  for (int gi = 0; gi < n_groups; ++gi) {   // every side fits before any group changes
+    OpPlan P{};
+    if (fast_plan_table(b->groups[gi].g, &P, b->smem_limit, op_tile[gi]) != cudaSuccess)
+      return bfail(b, LFSR_EUNSUPPORTED, "tile side does not fit the shared memory");
+  }
   for (int gi = 0; gi < n_groups; ++gi)
     if (set_tile(b, b->groups[gi], op_tile[gi]) != cudaSuccess)
       return bfail(b, LFSR_EUNSUPPORTED, "tile side does not fit the shared memory");

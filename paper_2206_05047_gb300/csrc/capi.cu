@@ -168,6 +168,7 @@ TableArgs handle_table(lfsr_handle* h, int kind, int b, int pb) {
   t.check_done = (kind == KD_NLA || kind == KD_NORMAL) ? 1 : 0;
   t.partials = part_slot(h, kind_slot(kind));
   t.counter = h->counters + kind;
+  if (kind == KD_NORMAL || kind == KD_DATA) t.cta_unit0 = h->cta_unit0;
   return t;
 }
 
@@ -431,29 +432,27 @@ JobArgs standalone_job(const lfsr_handle* h) {
 
 }  // namespace
 
+// Cost-balanced split of operator units over the CTAs of a launch.  A unit
+// is one (tile, view pair); a CTA takes a contiguous range (consecutive
+// pairs of a tile share its staged source and its scatter accumulator).
+// Units differ in cost with their tile's disparity content (the spread of
+// the sub-pixel shifts decides how many scatter taps merge and how often
+// shared-memory accesses collide), and a CTA pays for staging and flushing
+// each tile it starts.  The even split leaves the slowest CTA well above
+// the mean, and the launch (and, fused, every CG step's grid barrier) waits
+// for the slowest one.
+//
+// The costs come from one timing launch on the even split: unit costs from
+// the differences of the start clocks, the cost of a tile switch from the
+// median excess of a range's tile-starting unit over the next unit.  The
+// ranges are the contiguous split with the smallest maximum predicted cost
+// (bisection on that maximum, greedy packing).
 namespace {
 
-// Cost-balanced split of the operator units over the CTAs of one light
-// field.  A unit is one (64 x 64 tile, view pair); a CTA takes a contiguous
-// range (consecutive pairs of a tile share its staged source and its
-// scatter accumulator).  Units differ in cost with their tile's disparity
-// content (the spread of the sub-pixel shifts decides how many scatter
-// taps merge and how often shared-memory accesses collide), and a CTA pays
-// for staging and flushing each tile it starts.  The even split leaves the
-// slowest CTA well above the mean, and every fused CG step waits at its
-// grid barrier for the slowest one.
-//
-// Measured once per handle: a normal-matrix launch on the even split
-// records the SM clock at the start of every unit and at the end of each
-// CTA's range.  Unit costs follow from the differences; the cost of a tile
-// switch is the median excess of a range's tile-starting unit over the
-// next unit.  The ranges are then the contiguous split with the smallest
-// maximum predicted cost (bisection on that maximum, greedy packing), kept
-// only when it predicts a lower maximum than the even split.
 struct SplitCost {
-  std::vector<double> base;   // per unit, without tile staging
-  double sw = 0.0;            // staging and flushing one tile
-  int upt = 1;                // units per tile
+  std::vector<double> base;       // per unit, without tile staging
+  const std::vector<char>* tile_start = nullptr;
+  double sw = 0.0;                // staging and flushing one tile
 };
 
 // CTAs that greedy packing with at most `cap` per CTA needs (starts filled
@@ -464,7 +463,7 @@ int pack_units(const SplitCost& c, double cap, std::vector<int>* starts) {
   double cur = 0.0;
   bool open = false;
   for (int u = 0; u < units; ++u) {
-    const double add = c.base[u] + (u % c.upt == 0 ? c.sw : 0.0);
+    const double add = c.base[u] + ((*c.tile_start)[u] ? c.sw : 0.0);
     if (!open || cur + add > cap) {
       if (starts) starts->push_back(u);
       ++ctas;
@@ -477,46 +476,31 @@ int pack_units(const SplitCost& c, double cap, std::vector<int>* starts) {
   return ctas;
 }
 
-cudaError_t balance_operator_units(lfsr_handle* h) {
-  const int units = h->op_units, grid = h->grid_op;
-  const size_t bytes = (size_t)(units + grid) * sizeof(long long);
-  // nothing to balance with fewer than two units per CTA; the clocks go to
-  // R, which is unused until the first load (8-byte aligned: cudaMalloc)
-  if (!h->fused || units < 2 * grid || bytes > h->p * sizeof(float)) return cudaSuccess;
-  long long* clk = reinterpret_cast<long long*>(h->R);
-  JobArgs j = make_job(h, KD_NORMAL, 0, 0, 0);
-  j.fuse = 0;             // the operator part alone (P[0] is zero, Q scratch)
-  j.cta_unit0 = nullptr;  // the even split
-  j.sc = h->sc + 1;       // its <p, M p> = 0 ends an x-step: not the solver's scalars
-  TableArgs t = handle_table(h, KD_NORMAL, 0, 0);
-  t.check_done = 0;       // (the warm-up launch has ended the x-step of sc[1])
-  cudaError_t e = fast_launch(OP_NORMAL, h->g, h->op, t, grid, h->stream, &j);   // warm-up
-  j.unit_clock = clk;
-  if (e == cudaSuccess) e = fast_launch(OP_NORMAL, h->g, h->op, t, grid, h->stream, &j);
-  std::vector<long long> c((size_t)units + grid);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c.data(), clk, bytes, cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->sc, 0, 2 * sizeof(DevScalars), h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) return e;
+}  // namespace
 
-  SplitCost sc;
-  sc.upt = std::max(1, units / std::max(1, h->op.n_tiles));
+bool lfsr::split_by_cost(const std::vector<long long>& clk, int units, int grid,
+                         const std::vector<char>& tile_start, std::vector<int>* r0,
+                         double ratio[2]) {
+  ratio[0] = ratio[1] = 0.0;
+  if (units < 1 || grid < 1 || (int)tile_start.size() != units ||
+      clk.size() != (size_t)units + grid)
+    return false;
   std::vector<double> cost(units);
   std::vector<char> staged(units, 0);
-  std::vector<double> even(grid, 0.0);
-  std::vector<double> excess;
+  std::vector<double> even(grid, 0.0), excess;
   for (int b = 0; b < grid; ++b) {
     const int ub = (int)((long long)b * units / grid), ue = (int)((long long)(b + 1) * units / grid);
     for (int u = ub; u < ue; ++u) {
-      const long long next = u + 1 < ue ? c[u + 1] : c[(size_t)units + b];
-      cost[u] = next > c[u] ? (double)(next - c[u]) : 1.0;
-      staged[u] = (u == ub || u % sc.upt == 0) ? 1 : 0;
+      const long long next = u + 1 < ue ? clk[u + 1] : clk[(size_t)units + b];
+      cost[u] = next > clk[u] ? (double)(next - clk[u]) : 1.0;
+      staged[u] = (u == ub || tile_start[u]) ? 1 : 0;
       even[b] += cost[u];
     }
     for (int u = ub; u + 1 < ue; ++u)
-      if (staged[u] && !staged[u + 1] && (u + 1) / sc.upt == u / sc.upt)
-        excess.push_back(cost[u] - cost[u + 1]);
+      if (staged[u] && !staged[u + 1]) excess.push_back(cost[u] - cost[u + 1]);
   }
+  SplitCost sc;
+  sc.tile_start = &tile_start;
   if (!excess.empty()) {
     std::nth_element(excess.begin(), excess.begin() + excess.size() / 2, excess.end());
     sc.sw = std::max(0.0, excess[excess.size() / 2]);
@@ -525,7 +509,7 @@ cudaError_t balance_operator_units(lfsr_handle* h) {
   double total = 0.0, lo = 0.0;
   for (int u = 0; u < units; ++u) {
     sc.base[u] = std::max(1.0, cost[u] - (staged[u] ? sc.sw : 0.0));
-    total += sc.base[u] + (u % sc.upt == 0 ? sc.sw : 0.0);
+    total += sc.base[u] + (tile_start[u] ? sc.sw : 0.0);
     lo = std::max(lo, sc.base[u] + sc.sw);
   }
   double hi = total + grid * sc.sw;
@@ -535,15 +519,13 @@ cudaError_t balance_operator_units(lfsr_handle* h) {
     else lo = mid;
   }
   std::vector<int> starts;
-  pack_units(sc, hi, &starts);
-  if ((int)starts.size() > grid) return cudaSuccess;   // (cannot happen: hi is feasible)
-  // predicted cost of each balanced range
+  if (pack_units(sc, hi, &starts) > grid) return false;
   double bal_max = 0.0, bal_sum = 0.0;
   for (size_t r = 0; r < starts.size(); ++r) {
     const int ue = r + 1 < starts.size() ? starts[r + 1] : units;
     double v = sc.sw;
     for (int u = starts[r]; u < ue; ++u)
-      v += sc.base[u] + (u > starts[r] && u % sc.upt == 0 ? sc.sw : 0.0);
+      v += sc.base[u] + (u > starts[r] && tile_start[u] ? sc.sw : 0.0);
     bal_max = std::max(bal_max, v);
     bal_sum += v;
   }
@@ -552,15 +534,47 @@ cudaError_t balance_operator_units(lfsr_handle* h) {
     even_max = std::max(even_max, v);
     even_sum += v;
   }
-  h->op_split[0] = even_max / (even_sum / grid);
-  h->op_split[1] = bal_max / (bal_sum / grid);
-  if (!(bal_max < 0.99 * even_max)) {
-    h->op_split[1] = h->op_split[0];
-    return cudaSuccess;
+  ratio[0] = even_max / (even_sum / grid);
+  ratio[1] = bal_max / (bal_sum / grid);
+  if (!(bal_max < 0.99 * even_max)) {   // not worth a change: the even split stays
+    ratio[1] = ratio[0];
+    return false;
   }
-  std::vector<int> r0(grid + 1, units);
-  for (size_t r = 0; r < starts.size(); ++r) r0[r] = starts[r];
-  r0[0] = 0;
+  r0->assign((size_t)grid + 1, units);
+  for (size_t r = 0; r < starts.size(); ++r) (*r0)[r] = starts[r];
+  (*r0)[0] = 0;
+  return true;
+}
+
+namespace {
+
+// The single-light-field operator launches of h: a timing launch of the
+// normal-matrix kernel after a warm-up one (P[0] is zero, Q is scratch, the
+// clocks go to R, all unused until the first load), then the balanced
+// ranges when they beat the even split.
+cudaError_t balance_operator_units(lfsr_handle* h) {
+  const int units = h->op_units, grid = h->grid_op;
+  const size_t bytes = (size_t)(units + grid) * sizeof(long long);
+  // nothing to balance with fewer than two units per CTA (R: 8-byte aligned)
+  if (!h->fused || units < 2 * grid || bytes > h->p * sizeof(float)) return cudaSuccess;
+  long long* clk = reinterpret_cast<long long*>(h->R);
+  JobArgs j = make_job(h, KD_NORMAL, 0, 0, 0);
+  j.fuse = 0;             // the operator part alone
+  TableArgs t = handle_table(h, KD_NORMAL, 0, 0);
+  t.cta_unit0 = nullptr;  // the even split
+  t.check_done = 0;
+  t.unit_clock = clk;     // timing launches leave the scalars alone
+  cudaError_t e = fast_launch(OP_NORMAL, h->g, h->op, t, grid, h->stream, &j);   // warm-up
+  if (e == cudaSuccess) e = fast_launch(OP_NORMAL, h->g, h->op, t, grid, h->stream, &j);
+  std::vector<long long> c((size_t)units + grid);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c.data(), clk, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return e;
+  const int upt = std::max(1, units / std::max(1, h->op.n_tiles));
+  std::vector<char> tile_start(units);
+  for (int u = 0; u < units; ++u) tile_start[u] = u % upt == 0;
+  std::vector<int> r0;
+  if (!split_by_cost(c, units, grid, tile_start, &r0, h->op_split)) return cudaSuccess;
   e = dalloc(h, &h->cta_unit0, (size_t)grid + 1);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->cta_unit0, r0.data(), r0.size() * sizeof(int), cudaMemcpyHostToDevice,
@@ -763,7 +777,6 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
       break;
     case KD_DATA:  // data rows, v += A^T (...)
       j.tiles_x = h->op.tiles_x;
-      j.cta_unit0 = h->cta_unit0;
       j.view0 = 0;
       j.nviews = g.sk;
       j.scale = 1.f;
@@ -800,7 +813,6 @@ JobArgs lfsr::make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0)
       break;
     case KD_NORMAL:  // q += cA sum_k A_k^T A_k p
       j.tiles_x = h->op.tiles_x;
-      j.cta_unit0 = h->cta_unit0;
       j.view0 = 0;
       j.nviews = g.sk;
       j.scale = g.cA;
@@ -1015,15 +1027,6 @@ int lfsr::create_handle(const lfsr_params* pr, void* cuda_stream, lfsr_handle** 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->P[1], 0, p * sizeof(float), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess && balance) e = balance_operator_units(h);
-  if (e == cudaSuccess && h->cta_unit0) {   // the operator jobs take the balanced ranges
-    for (int b = 0; b < 2; ++b)
-      for (int pb = 0; pb < 2; ++pb)
-        for (int kd = 0; kd < KD_NUM; ++kd)
-          h->jobs_host[(2 * b + pb) * KD_NUM + kd] = make_job(h, kd, b, pb, 0);
-    e = cudaMemcpyAsync(h->jobs_dev, h->jobs_host.data(), h->jobs_host.size() * sizeof(JobArgs),
-                        cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  }
   if (e != cudaSuccess) {
     rc = cuda_fail(nullptr, e, "lfsr_create");
     free_all(h);

@@ -123,6 +123,15 @@ JobArgs make_job(const lfsr_handle* h, int kind, int b, int pb, int unit0);
 // over the CTAs by cost (single-light-field launches; light fields that run
 // only inside batch tables skip it).
 int create_handle(const lfsr_params* params, void* cuda_stream, lfsr_handle** out, bool balance);
+// Contiguous split of `units` operator units over `grid` CTAs with the
+// smallest maximum measured cost.  clk: the clocks of one timing launch on
+// the even split (units start clocks, then grid range-end clocks);
+// tile_start[u]: unit u is the first of its tile.  ratio: the slowest CTA's
+// cost over the mean, for the even split and for the chosen split.  True,
+// with r0 = the grid + 1 range starts, when the split beats the even one by
+// more than 1 %.
+bool split_by_cost(const std::vector<long long>& clk, int units, int grid,
+                   const std::vector<char>& tile_start, std::vector<int>* r0, double ratio[2]);
 // Work units of a launch kind for this light field.
 int kind_units(const lfsr_handle* h, int kind);
 // Reduction slot (RED_*) of a launch kind.

@@ -170,14 +170,6 @@ struct JobArgs {
   // NLTV apply with TMA-staged weights: the device address of the weight
   // planes' tensor map (a CUtensorMap, 64-byte aligned), or NULL.
   const void* wt_map;
-  // Operator launches of one light field: the first unit of each CTA's
-  // contiguous range (grid + 1 entries, cut where the measured cost of the
-  // units crosses multiples of total / grid), or NULL for the even split;
-  // when unit_clock is not NULL, the kernel records there the SM clock at
-  // the start of each unit and (after the units) at the end of each CTA's
-  // range.
-  const int* cta_unit0;
-  long long* unit_clock;
 };
 
 // Launch-wide arguments of a table-driven kernel.
@@ -189,6 +181,14 @@ struct TableArgs {
   int check_done;             // CG steps: skip light fields whose x-step has finished
   double* partials;           // reduction slots
   unsigned int* counter;      // arrival counter of the grid reduction (re-armed by the kernel)
+  // Operator launches: the first unit of each CTA's contiguous range
+  // (grid + 1 entries, split by measured cost), or NULL for the even split.
+  // A timing launch passes unit_clock: the kernel records there the SM
+  // clock at the start of each unit and, after its units, at the end of
+  // each CTA's range, and leaves the device scalars alone (no final
+  // reduction).
+  const int* cta_unit0;
+  long long* unit_clock;
 };
 
 struct NlPlan {

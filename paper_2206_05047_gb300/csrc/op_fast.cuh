@@ -161,14 +161,14 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
   const float Sf = (float)S;
   const int NPc = P.NPc, NAc = P.NAc;
   const int units = t.total_units;
-  // this CTA's contiguous range of units: cost-balanced ranges of one light
-  // field when given, else the even split
-  const bool ranged = SINGLE && one.cta_unit0 != nullptr;
-  const int u_begin = ranged ? __ldg(one.cta_unit0 + blockIdx.x)
+  // this CTA's contiguous range of units: cost-balanced ranges when given,
+  // else the even split
+  const bool ranged = t.cta_unit0 != nullptr;
+  const int u_begin = ranged ? __ldg(t.cta_unit0 + blockIdx.x)
                              : (int)((long long)blockIdx.x * units / gridDim.x);
-  const int u_end = ranged ? __ldg(one.cta_unit0 + blockIdx.x + 1)
+  const int u_end = ranged ? __ldg(t.cta_unit0 + blockIdx.x + 1)
                            : (int)((long long)(blockIdx.x + 1) * units / gridDim.x);
-  long long* const clk = SINGLE ? one.unit_clock : nullptr;
+  long long* const clk = t.unit_clock;
   constexpr bool REDUCE = MODE == OP_NORMAL || MODE == OP_DATA;
   // this CTA's partial slot of every light field of the table starts at 0
   if (REDUCE)
@@ -257,7 +257,7 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
   }
 
   for (int u = u_begin; u < u_end; ++u) {
-    if (SINGLE && clk && tid == 0) clk[u] = clock64();
+    if (clk && tid == 0) clk[u] = clock64();
     if (!SINGLE && u >= j_end) {
       if (jb >= 0) end_job();
       jb = table_job(t, u);
@@ -625,7 +625,10 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
   }
 
   if (jb >= 0) end_job();   // (SINGLE: always; ends with a barrier after the last flush)
-  if (SINGLE && clk && tid == 0) clk[units + blockIdx.x] = clock64();
+  if (clk) {                // a timing launch
+    if (tid == 0) clk[units + blockIdx.x] = clock64();
+    return;
+  }
   if (SINGLE && MODE == OP_DATA && one.fuse) {
     // The x-step initialisation (Algorithm 2) in the same launch: once
     // every CTA has flushed its v atomics, each CTA takes its chunk of the

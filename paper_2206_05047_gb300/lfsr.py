@@ -488,7 +488,8 @@ class Batch:
         _bcheck(load_library().lfsr_batch_stats(self.handle, int(job), C.byref(st)), self.handle)
         return dict(iterations=st.iterations, cg_steps=st.cg_steps, status=st.status,
                     dual_change_sq=st.dual_change_sq, cg_pi=st.cg_pi,
-                    state_bytes=st.state_bytes)
+                    state_bytes=st.state_bytes, op_split_even=st.op_split_even,
+                    op_split_balanced=st.op_split_balanced)
 
     def launches_per_iteration(self) -> int:
         return load_library().lfsr_batch_launches_per_iteration(self.handle)

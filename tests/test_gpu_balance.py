@@ -1,14 +1,15 @@
 """Cost-balanced ranges of the operator launches.
 
-lfsr_create times every (64 x 64 tile, view pair) unit of one normal-matrix
+lfsr_create (and a batch that owns its light fields, for each operator
+group) times every (64 x 64 tile, view pair) unit of one normal-matrix
 launch and splits the units over the CTAs in contiguous ranges of equal
 measured cost.  The split changes only which CTA runs a unit (and so the
 order of the float atomic additions):
 
 * a light field with enough units reports both load-balance figures, the
-  balanced one no worse than the even split's;
-* its solve matches the FP64 oracle and the same light field run inside a
-  batch table (which keeps the even split);
+  balanced one no worse than the even split's, alone and in a batch;
+* its solve matches the FP64 oracle, the batch, and the server (whose
+  batch keeps the even split);
 * a light field with fewer than two units per CTA keeps the even split and
   reports no measurement.
 """
@@ -40,17 +41,30 @@ def test_balanced_ranges_match_the_oracle_and_the_even_split():
     assert lfsr.stats(c.h)["status"] == 0
     ref, _, _ = c.oracle.admm(c.y.astype(np.float64), c.x0.astype(np.float64), n)
     assert rel_err(got, ref) <= 1e-4
-    # the same light field in a batch table: the even split of the units
-    b = lfsr.Batch([dict(U=wl.U, V=wl.V, H=wl.H, W=wl.W, scale=wl.scale, blur=c.blur,
-                         disparity=c.disp, lambda1=wl.lambda1, lambda2=wl.lambda2, mu=wl.mu,
-                         nltv_window=wl.window, nltv_patch=wl.patch, nltv_h=wl.h,
-                         cg_iters=wl.cg_iters, cg_tol=0.0)])
+    kw = dict(U=wl.U, V=wl.V, H=wl.H, W=wl.W, scale=wl.scale, blur=c.blur, disparity=c.disp,
+              lambda1=wl.lambda1, lambda2=wl.lambda2, mu=wl.mu, nltv_window=wl.window,
+              nltv_patch=wl.patch, nltv_h=wl.h, cg_iters=wl.cg_iters, cg_tol=0.0)
+    # the same light field in a batch table, its group balanced
+    b = lfsr.Batch([kw])
+    bs = b.stats(0)
+    assert 1.0 <= bs["op_split_balanced"] <= bs["op_split_even"]
     b.load(0, c.t(c.y), c.t(c.x0))
     b.iterate(n)
     xb = c.empty(*c.oracle.hr)
     b.get_x(0, xb)
-    assert rel_err(got, c.np(xb)) <= 1e-5
+    assert rel_err(c.np(xb), got) <= 1e-5
     b.close()
+    # ... and served: the server's batch keeps the even split
+    srv = lfsr.Server(8 << 30, max_active=2, iterations=n, iterations_per_step=1)
+    rid = srv.submit(c.y, c.x0, **kw)
+    for _ in range(4 * n):
+        if srv.status(rid)[0] == lfsr.LFSR_REQ_DONE:
+            break
+        srv.step()
+    xs = np.zeros(c.oracle.hr, np.float32)
+    srv.fetch(rid, xs)
+    assert rel_err(xs, got) <= 1e-5
+    srv.close()
     c.solver.close()
 
 
