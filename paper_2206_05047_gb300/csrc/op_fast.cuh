@@ -59,7 +59,12 @@ struct FastShape {
   static constexpr int MB2 = pick_block(NE, NL);
   static constexpr int NB2 = (NL + MB2 - 1) / MB2;
   static constexpr int W2 = Z * (MB2 - 1) + KB;              // window length
-  static constexpr int NEp = ((Z * (NB2 * MB2 - 1) + KB) > NE ? (Z * (NB2 * MB2 - 1) + KB) : NE) | 1;
+  // pitch of the sample buffer: NE itself when odd (the sample index is then
+  // the task index); stage 2's last windows read up to NE2 - NE columns past
+  // a row, which feed only outputs beyond the LR grid (never stored); the
+  // last view's last row reads into the next buffer
+  static constexpr int NE2 = (Z * (NB2 * MB2 - 1) + KB) > NE ? (Z * (NB2 * MB2 - 1) + KB) : NE;
+  static constexpr int NEp = NE | 1;
   // stage 3 (vertical forward): MB3 LR rows per task
   static constexpr int MB3 = pick_block(VB * NL, NL);
   static constexpr int NB3 = (NL + MB3 - 1) / MB3;
@@ -103,13 +108,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-__device__ __forceinline__ void split_shift(float t, int& ip, float& fr) {
-  // t in [0, 2^23): ip = floor(t), fr = t - floor(t), exactly, on the FP32 pipe
-  const float f = __fadd_rd(t, 8388608.0f);
-  ip = __float_as_int(f) - 0x4B000000;
-  fr = t - (f - 8388608.0f);
-}
-
 // Two FP32 lanes per instruction (the packed FFMA2 / FADD2 / FMUL2 of this
 // architecture): the two views of a pass go through the same arithmetic in
 // the two lanes.  Every lane rounds as the scalar operation it replaces;
@@ -129,11 +127,17 @@ __device__ __forceinline__ float2 add2_rd(float2 a, float2 b) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
   return d;
 }
-// split_shift of both lanes
-__device__ __forceinline__ void split_shift2(float2 t, int& i0, int& i1, float2& fr) {
+// Floor and fraction of a sub-pixel shift t in [0, 2^23), in both lanes,
+// exactly, on the FP32 pipe: f = t + 2^23 rounded down holds floor(t) in its
+// low mantissa bits, and t - (f - 2^23) is the fraction.  The integer parts
+// are left biased: b = floor(t) + SHIFT_BIAS as an unsigned word.  Index arithmetic folds the bias into a
+// base term once (unsigned arithmetic wraps modulo 2^32, and every true
+// index is small and non-negative), instead of removing it per sample.
+constexpr unsigned SHIFT_BIAS = 0x4B000000u;
+__device__ __forceinline__ void split_bits2(float2 t, unsigned& b0, unsigned& b1, float2& fr) {
   const float2 f = add2_rd(t, make_float2(8388608.0f, 8388608.0f));
-  i0 = __float_as_int(f.x) - 0x4B000000;
-  i1 = __float_as_int(f.y) - 0x4B000000;
+  b0 = __float_as_uint(f.x);
+  b1 = __float_as_uint(f.y);
   fr = sub2(t, __fadd2_rn(f, make_float2(-8388608.0f, -8388608.0f)));
 }
 
@@ -214,8 +218,9 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
   int or0 = 0, or1 = 0, oc0 = 0, oc1 = 0;   // LR rows / columns owned by the tile (grid-local)
   int NAr_t = 0, NAc_t = 0;
   // this thread's warp-sample positions (fixed for all views of a tile):
-  // staged-source index of the (0, 0) tap before the shift, and disparity
-  int s1_base[SH::IT1];
+  // staged-source index of the (0, 0) tap before the shift (less the bias
+  // of the shift's split, SHIFT_BIAS (NPc + 1)), and disparity
+  unsigned s1_base[SH::IT1];
   float s1_om[SH::IT1];
 
   for (int t = tid; t < VB * SH::GS; t += FT_THREADS) sG[t] = 0.f;
@@ -333,7 +338,7 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
           const int t = tid + it * FT_THREADS;
           const int er = t / NE, ec = t - er * NE;
           const bool ok = t < SH::NS1;
-          s1_base[it] = ok ? er * NPc + ec : 0;
+          s1_base[it] = ok ? (unsigned)(er * NPc + ec) - SHIFT_BIAS * (unsigned)(NPc + 1) : 0u;
           s1_om[it] = ok ? sO[er * NEp + ec] : 0.f;
         }
       }
@@ -382,13 +387,12 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
           if (it < SH::IT1 - 1 || t < SH::NS1) {
             const int si = (NEp == NE) ? t : (t / NE) * NEp + (t % NE);
             const float2 om2 = pk(s1_om[it], s1_om[it]);
-            const float* qb = sP + s1_base[it];
-            int iy0, iy1, ix0, ix1;
+            unsigned by0, by1, bx0, bx1;
             float2 fy, fx;
-            split_shift2(fma2(tv2, om2, S2), iy0, iy1, fy);
-            split_shift2(fma2(tu2, om2, S2), ix0, ix1, fx);
-            const float* qa = qb + iy0 * NPc + ix0;
-            const float* qc = qb + iy1 * NPc + ix1;
+            split_bits2(fma2(tv2, om2, S2), by0, by1, fy);
+            split_bits2(fma2(tu2, om2, S2), bx0, bx1, fx);
+            const float* qa = sP + (int)(s1_base[it] + by0 * (unsigned)NPc + bx0);
+            const float* qc = sP + (int)(s1_base[it] + by1 * (unsigned)NPc + bx1);
             const float2 a = pk(qa[0], qc[0]), b = pk(qa[1], qc[1]);
             const float2 c = pk(qa[NPc], qc[NPc]), d = pk(qa[NPc + 1], qc[NPc + 1]);
             const float2 top = fma2(fx, sub2(b, a), a);
@@ -546,29 +550,30 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
       }
       const int hi = i0 + i;
       const float* orow = sO + (hi - e_r0) * NEp - e_c0;
+      // accumulator index of the (0, 0) tap of pixel (hi, Z n0) before its
+      // shift, less the bias of the shift's split
+      const unsigned a_row = (unsigned)(i * NAc + Z * n0 - j0) - SHIFT_BIAS * (unsigned)(NAc + 1);
       // taps of consecutive pixels of this row segment: when a pixel's
       // integer shift equals its left neighbour's, its left taps coincide
       // with the neighbour's right taps and are added before one atomic
       bool pend0 = false, pend1 = false;
-      int pr0 = 0, pc0 = 0, pr1 = 0, pc1 = 0;
+      unsigned pa0 = 0u, pa1 = 0u;
       float pt0 = 0.f, pb0 = 0.f, pt1 = 0.f, pb1 = 0.f;
       // tl, bl, tr, br: the bilinear weights times the value, for the taps
-      // (r, c), (r + 1, c), (r, c + 1), (r + 1, c + 1)
-      auto scatter = [&](float tl, float bl, float tr, float br, int r, int c, bool& pend,
-                         int& pr_, int& pc_, float& pt, float& pb) {
-        const bool merged = pend && pr_ == r && pc_ == c;
+      // a, a + NAc, a + 1, a + NAc + 1 (a: accumulator index of the top-left)
+      auto scatter = [&](float tl, float bl, float tr, float br, unsigned a, bool& pend,
+                         unsigned& pa, float& pt, float& pb) {
+        const bool merged = pend && pa == a;
         if (pend && !merged) {
-          atomicAdd(sA + pr_ * NAc + pc_, pt);
-          atomicAdd(sA + (pr_ + 1) * NAc + pc_, pb);
+          atomicAdd(sA + pa, pt);
+          atomicAdd(sA + pa + NAc, pb);
         }
         tl += merged ? pt : 0.f;
         bl += merged ? pb : 0.f;
-        float* a = sA + r * NAc + c;
-        atomicAdd(a, tl);
-        atomicAdd(a + NAc, bl);
+        atomicAdd(sA + a, tl);
+        atomicAdd(sA + a + NAc, bl);
         pend = true;
-        pr_ = r;
-        pc_ = c + 1;
+        pa = a + 1;
         pt = tr;
         pb = br;
       };
@@ -582,19 +587,19 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
         }
         const float om = orow[hj];
         const float2 om2 = pk(om, om);
-        const int cc = hj - j0;
-        int iy0, iy1, ix0, ix1;
+        const unsigned ap = a_row + (unsigned)(Z * o + ph);
+        unsigned by0, by1, bx0, bx1;
         float2 fy, fx;
-        split_shift2(fma2(tv2, om2, S2), iy0, iy1, fy);
-        split_shift2(fma2(tu2, om2, S2), ix0, ix1, fx);
+        split_bits2(fma2(tv2, om2, S2), by0, by1, fy);
+        split_bits2(fma2(tu2, om2, S2), bx0, bx1, fx);
         // weights: (1 - fx) is exact (fx is a multiple of the shift's ulp)
         const float2 omfx = sub2(pk(1.f, 1.f), fx);
         const float2 ty = mul2(fy, tv);
         const float2 by = sub2(tv, ty);
         const float2 tl = mul2(by, omfx), bl = mul2(ty, omfx);
         const float2 tr = mul2(fx, by), br = mul2(fx, ty);
-        scatter(tl.x, bl.x, tr.x, br.x, i + iy0, cc + ix0, pend0, pr0, pc0, pt0, pb0);
-        if (two) scatter(tl.y, bl.y, tr.y, br.y, i + iy1, cc + ix1, pend1, pr1, pc1, pt1, pb1);
+        scatter(tl.x, bl.x, tr.x, br.x, ap + by0 * (unsigned)NAc + bx0, pend0, pa0, pt0, pb0);
+        if (two) scatter(tl.y, bl.y, tr.y, br.y, ap + by1 * (unsigned)NAc + bx1, pend1, pa1, pt1, pb1);
       };
       if (SH::ALIGNED && full_cols) {
 #pragma unroll
@@ -611,12 +616,12 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
           }
       }
       if (pend0) {
-        atomicAdd(sA + pr0 * NAc + pc0, pt0);
-        atomicAdd(sA + (pr0 + 1) * NAc + pc0, pb0);
+        atomicAdd(sA + pa0, pt0);
+        atomicAdd(sA + pa0 + NAc, pb0);
       }
       if (pend1) {
-        atomicAdd(sA + pr1 * NAc + pc1, pt1);
-        atomicAdd(sA + (pr1 + 1) * NAc + pc1, pb1);
+        atomicAdd(sA + pa1, pt1);
+        atomicAdd(sA + pa1 + NAc, pb1);
       }
     }
     // no barrier here: the next unit's stages 1-2 write sW and sH, which this
