@@ -561,6 +561,15 @@ def batch_subrecord(dev, stream, n_lf: int = 16, n_iter: int = 10, steps: int = 
         t_b = timed(batch_step)
         xb = xs_of(batch.get_x, [w.HR for w in wls])
         launches_b = batch.launches_per_iteration()
+        # both launch forms (per-phase launches, one persistent launch per
+        # iteration) at the tuned tiles, where the persistent one is available
+        forms = {}
+        if batch.persistent_available():
+            tuned_form = batch.form()
+            for form in ("phases", "persistent"):
+                batch.set_form(form)
+                forms[form] = timed(batch_step) / (steps * n_iter)
+            batch.set_form(tuned_form)
         batch.close()
         solvers = [lfsr.Solver(stream=stream, **kw) for kw in kws]
 
@@ -579,6 +588,7 @@ def batch_subrecord(dev, stream, n_lf: int = 16, n_iter: int = 10, steps: int = 
         rec[prec] = {"batch": vb, "plain_serial": vp, "batch_vs_plain": vb / vp,
                      "unit": UNIT, "launches_per_iteration": {
                          "batch": launches_b, "plain_serial": launches_p},
+                     "forms_ms_per_iteration": forms or None,
                      "max_abs_dpsnr_db": max(abs(d) for d in dps),
                      "mean_psnr_db": float(np.mean([synth.psnr(xb[j], gts[j])
                                                     for j in range(len(wls))])),

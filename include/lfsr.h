@@ -355,7 +355,8 @@ const char *lfsr_batch_last_error(const lfsr_batch *b);
 /* Number of light fields (0 for NULL). */
 int lfsr_batch_size(const lfsr_batch *b);
 
-/* As lfsr_load for light field `job`: views and x0 in, duals := 0. */
+/* As lfsr_load for light field `job`: views and x0 in, duals := 0.  Also
+ * re-arms the batch's reduction counters (needed after LFSR_ETIMEOUT). */
 int lfsr_batch_load(lfsr_batch *b, int job, const float *lr_views, const float *x0,
                     int mem_kind);
 
@@ -372,12 +373,14 @@ int lfsr_batch_launches_per_iteration(const lfsr_batch *b);
 
 /* Autotuner: times, on the loaded light fields, the candidate tile shapes
  * of the operator kernel (64 x 64 and 32 x 32 HR pixels per work unit) for
- * each group of light fields sharing scale and blur, and the stencil
- * blocking of the NLTV divergence kernel (6 or 3 window directions per batch
- * of weight loads), and keeps the fastest of each.  It runs about
- * 3 x (candidate tiles) x (groups) + 4 ADMM iterations on the loaded state,
- * which therefore has to be loaded again (lfsr_batch_load) before a solve
- * whose result matters.  Synchronous. */
+ * each group of light fields sharing scale and blur, the stencil blocking
+ * of the NLTV divergence kernel (6 or 3 window directions per batch of
+ * weight loads) and, where the persistent form is available, the launch
+ * form (per-phase launches or one persistent launch per iteration), and
+ * keeps the fastest of each.  It runs about 3 x (candidate tiles) x
+ * (groups) + 10 ADMM iterations on the loaded state, which therefore has to
+ * be loaded again (lfsr_batch_load) before a solve whose result matters.
+ * Synchronous. */
 int lfsr_batch_autotune(lfsr_batch *b);
 
 /* The current choices: op_tile[g] for g < min(groups, max_groups) and
@@ -389,6 +392,44 @@ int lfsr_batch_tuning(const lfsr_batch *b, int *op_tile, int max_groups, int *nl
  * op_tile holds one tile side (64 or 32) per operator group, in the order
  * lfsr_batch_tuning reports them; nla_chunk is 6 or 3. */
 int lfsr_batch_set_tuning(lfsr_batch *b, const int *op_tile, int n_groups, int nla_chunk);
+
+/* Launch forms of a batch iteration (Algorithm 1 with K CG steps of
+ * Algorithm 2 for every light field).
+ *   LFSR_BATCH_PHASES: one launch per phase (per operator group for the
+ *     operator phases), 2 + G + K (2 + G) launches for G groups.
+ *   LFSR_BATCH_PERSISTENT: one cooperative launch per iteration runs every
+ *     phase over the same work units on one CTA per SM, a grid barrier
+ *     between dependent phases.  Every barrier wait is bounded (the limit of
+ *     lfsr_batch_set_device_wait, default LFSR_DEFAULT_WAIT_NS): a CTA whose
+ *     wait runs out records LFSR_ETIMEOUT in every light field's status
+ *     (reported by lfsr_batch_get_x) and abandons the iteration's work; the
+ *     light fields must then be loaded again.  Compiled for the NLTV window
+ *     5 (patch 3) with (scale, kb) = (2, 5), and the window 7 (patch 3) with
+ *     (2, 7), (3, 9) or both groups, patch-distance weights, float or half
+ *     storage, 64 x 64 operator tiles.
+ * Results of the two forms agree up to the order of float atomic additions.
+ * Both forms run two iterations per CUDA graph; profiling mode always times
+ * the per-phase launches. */
+#define LFSR_BATCH_PHASES 0
+#define LFSR_BATCH_PERSISTENT 1
+
+/* 1 when a compiled persistent iteration fits the batch as it is now
+ * (operator groups, tile sides, NLTV window, weights, storage), else 0. */
+int lfsr_batch_persistent_available(const lfsr_batch *b);
+
+/* The current launch form (-1 for NULL). */
+int lfsr_batch_form(const lfsr_batch *b);
+
+/* Selects the launch form (LFSR_EUNSUPPORTED for the persistent form when
+ * lfsr_batch_persistent_available is 0).  A change of tuning that makes the
+ * persistent form unavailable falls back to LFSR_BATCH_PHASES.  Synchronises
+ * the batch's stream. */
+int lfsr_batch_set_form(lfsr_batch *b, int form);
+
+/* As lfsr_set_device_wait, for the grid barriers of the persistent form:
+ * limit_ns of %globaltimer per wait; test_unreachable != 0 makes every wait
+ * run out (the test path of LFSR_ETIMEOUT). */
+int lfsr_batch_set_device_wait(lfsr_batch *b, int64_t limit_ns, int test_unreachable);
 
 /* Profiling mode (as lfsr_set_profiling): lfsr_batch_iterate launches one by
  * one with CUDA events around each launch; lfsr_batch_kernel_times

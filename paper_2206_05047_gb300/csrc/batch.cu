@@ -6,10 +6,12 @@
 // chunks of HR pixels -- with one launch per group of light fields sharing
 // the scale and the blur for the operator phases (the operator kernel is
 // compiled per (scale, blur size)).  Two iterations are captured as one CUDA
-// graph.  Each light field keeps its own state (an lfsr_handle), so loading,
-// reading and diagnostics reuse the single-light-field entry points.  An
-// autotuner picks, on the batch's own data, the operator tile side of each
-// group and the NLTV-apply direction chunk (lfsr_batch_autotune).
+// graph.  The persistent form runs the same phases as one cooperative launch
+// per iteration (batch_persist.cuh) where a compiled instance fits.  Each
+// light field keeps its own state (an lfsr_handle), so loading, reading and
+// diagnostics reuse the single-light-field entry points.  An autotuner picks,
+// on the batch's own data, the operator tile side of each group, the
+// NLTV-apply direction chunk and the launch form (lfsr_batch_autotune).
 #include <cstring>
 #include <new>
 #include <string>
@@ -72,6 +74,19 @@ struct lfsr_batch {
   int64_t iters = 0;
   cudaGraphExec_t graph_pair = nullptr;
   cudaGraphExec_t graph_single[2] = {nullptr, nullptr};
+  // the persistent form (one cooperative launch per iteration): whether a
+  // compiled instance fits the current groups, the group of each slot, its
+  // launch shape, the arguments of both iteration parities (device) and the
+  // grid-barrier arrival counter
+  int form = LFSR_BATCH_PHASES;
+  bool persist_ok = false;
+  int persist_order[PERSIST_MAX_GROUPS] = {0, 0};
+  size_t persist_smem = 0;
+  int persist_grid = 0;
+  PersistArgs* persist_args = nullptr;
+  unsigned long long* bar = nullptr;
+  unsigned long long wait_ns = LFSR_DEFAULT_WAIT_NS;   // device wait limit of its barriers
+  int wait_unreachable = 0;
   bool profiling = false;
   std::vector<ProfEvent> prof;
   double prof_ms[8] = {0};
@@ -105,12 +120,21 @@ void free_ranges(lfsr_batch* b) {
   }
 }
 
+void drop_graphs(lfsr_batch* b) {
+  if (b->graph_pair) cudaGraphExecDestroy(b->graph_pair);
+  b->graph_pair = nullptr;
+  for (auto& gs : b->graph_single) {
+    if (gs) cudaGraphExecDestroy(gs);
+    gs = nullptr;
+  }
+}
+
 void batch_free(lfsr_batch* b) {
   drop_events(b);
   free_ranges(b);
-  if (b->graph_pair) cudaGraphExecDestroy(b->graph_pair);
-  for (auto& gs : b->graph_single)
-    if (gs) cudaGraphExecDestroy(gs);
+  drop_graphs(b);
+  if (b->persist_args) cudaFree(b->persist_args);
+  if (b->bar) cudaFree(b->bar);
   if (b->tables) cudaFree(b->tables);
   if (b->maps) cudaFree(b->maps);
   if (b->partials) cudaFree(b->partials);
@@ -206,13 +230,29 @@ cudaError_t batch_iteration(lfsr_batch* b, int pa, cudaStream_t s, std::vector<P
   return e;
 }
 
+// One ADMM iteration of every light field at parity pa as one persistent
+// launch (batch_persist.cuh).
+cudaError_t persist_iteration(lfsr_batch* b, int pa, cudaStream_t s) {
+  const int G = (int)b->groups.size();
+  Geom gg[PERSIST_MAX_GROUPS];
+  for (int gi = 0; gi < G && gi < PERSIST_MAX_GROUPS; ++gi) gg[gi] = b->groups[gi].g;
+  return persist_launch(b->g, gg, b->persist_order, G, b->persist_args + pa, b->bar,
+                        b->persist_smem, b->persist_grid, s);
+}
+
+// One iteration in the batch's current form.
+cudaError_t form_iteration(lfsr_batch* b, int pa, cudaStream_t s) {
+  if (b->form == LFSR_BATCH_PERSISTENT) return persist_iteration(b, pa, s);
+  return batch_iteration(b, pa, s, nullptr);
+}
+
 cudaError_t batch_graph(lfsr_batch* b, int first_parity, int n, cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   cudaError_t el = cudaSuccess;
   for (int i = 0; i < n && el == cudaSuccess; ++i)
-    el = batch_iteration(b, (first_parity + i) & 1, b->cap_stream, nullptr);
+    el = form_iteration(b, (first_parity + i) & 1, b->cap_stream);
   e = cudaStreamEndCapture(b->cap_stream, &graph);
   if (el != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -298,6 +338,88 @@ cudaError_t balance_groups(lfsr_batch* b) {
   return e;
 }
 
+// The persistent form for the current groups and tables: whether a compiled
+// instance fits them (else the batch keeps the per-phase launches), its
+// shared memory and grid, and the arguments of both iteration parities
+// (the same tables, counters and CTA ranges as the per-phase launches).
+cudaError_t persist_setup(lfsr_batch* b) {
+  b->persist_ok = false;
+  const int G = (int)b->groups.size();
+  const int n = (int)b->jobs.size();
+  if (G < 1 || G > PERSIST_MAX_GROUPS) {
+    b->form = LFSR_BATCH_PHASES;
+    return cudaSuccess;
+  }
+  Geom gg[PERSIST_MAX_GROUPS];
+  int tile[PERSIST_MAX_GROUPS];
+  for (int gi = 0; gi < G; ++gi) {
+    gg[gi] = b->groups[gi].g;
+    tile[gi] = b->groups[gi].tile;
+  }
+  int* order = b->persist_order;
+  OpPlan P[PERSIST_MAX_GROUPS];
+  int sx_off = 0;
+  bool ok = persist_supported(b->g, gg, tile, G, order);
+  if (ok) {
+    for (int sl = 0; sl < G; ++sl) P[sl] = b->groups[order[sl]].P;
+    b->persist_smem = persist_smem(b->g, P, G, &sx_off);
+    ok = b->persist_smem <= (size_t)b->smem_limit &&
+         persist_prepare(b->g, gg, order, G, b->smem_limit + 1024) == cudaSuccess &&
+         persist_occupancy(b->g, gg, order, G, b->persist_smem) >= 1;
+  }
+  if (!ok) {
+    cudaGetLastError();   // an attribute call that failed leaves no sticky error
+    b->form = LFSR_BATCH_PHASES;
+    return cudaSuccess;
+  }
+  b->persist_grid = b->sm_count;
+  auto ctr = [&](int kind, int gi) { return kind * (G + 1) + gi; };
+  PersistArgs pa_args[2];
+  for (int pa = 0; pa < 2; ++pa) {
+    PersistArgs& a = pa_args[pa];
+    a = PersistArgs{};
+    a.nlw = table(b, b->t_nlw[pa], n, b->nl_total, b->m_nl, KD_NLW, ctr(KD_NLW, G), 0);
+    a.init = table(b, b->t_init[pa], n, b->vec_total, b->m_vec, KD_INIT, ctr(KD_INIT, G), 0);
+    for (int pb = 0; pb < 2; ++pb) {
+      a.nla[pb] = table(b, b->t_nla[pa][pb], n, b->nl_total, b->m_nl, KD_NLA, ctr(KD_NLA, G), 1);
+      a.upd[pb] =
+          table(b, b->t_upd[pa][pb], n, b->vec_total, b->m_vec, KD_UPDATE, ctr(KD_UPDATE, G), 0);
+    }
+    for (int sl = 0; sl < G; ++sl) {
+      const int gi = order[sl];
+      const Group& gr = b->groups[gi];
+      const int m = (int)gr.members.size();
+      // the balanced ranges split the units over gr.grid CTAs
+      const int* ranges = gr.grid == b->persist_grid ? gr.cta_unit0 : nullptr;
+      a.data[sl] = table(b, b->t_data[pa][gi], m, gr.units, b->m_op[gi], KD_DATA, ctr(KD_DATA, gi), 0);
+      a.data[sl].cta_unit0 = ranges;
+      for (int pb = 0; pb < 2; ++pb) {
+        a.norm[pb][sl] = table(b, b->t_norm[pa][pb][gi], m, gr.units, b->m_op[gi], KD_NORMAL,
+                               ctr(KD_NORMAL, gi), 1);
+        a.norm[pb][sl].cta_unit0 = ranges;
+      }
+      a.P[sl] = gr.P;
+    }
+    a.cg_iters = b->cg_iters;
+    a.sx_off = sx_off;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!b->persist_args)
+    e = fault_alloc() ? cudaErrorMemoryAllocation
+                      : cudaMalloc((void**)&b->persist_args, 2 * sizeof(PersistArgs));
+  if (e == cudaSuccess && !b->bar) {
+    e = fault_alloc() ? cudaErrorMemoryAllocation
+                      : cudaMalloc((void**)&b->bar, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned long long), b->stream);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->persist_args, pa_args, sizeof(pa_args), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // pa_args is a local buffer
+  if (e == cudaSuccess) b->persist_ok = true;
+  else b->form = LFSR_BATCH_PHASES;
+  return e;
+}
+
 // Builds the job tables and unit maps of every launch for the current tile
 // sides, uploads them (growing the device buffers when needed) and drops
 // the captured graphs, which hold the old launch shapes.  A batch that owns
@@ -353,8 +475,11 @@ cudaError_t build_tables(lfsr_batch* b) {
   // reduction slots: operator launches n_members x grid, the others one per unit
   size_t stride = (size_t)b->nl_total;
   if ((size_t)b->vec_total > stride) stride = b->vec_total;
-  for (const Group& gr : b->groups)
-    if (gr.members.size() * (size_t)gr.grid > stride) stride = gr.members.size() * (size_t)gr.grid;
+  // (the persistent form runs the operator phases on sm_count CTAs)
+  for (const Group& gr : b->groups) {
+    const size_t grid = gr.grid > b->sm_count ? (size_t)gr.grid : (size_t)b->sm_count;
+    if (gr.members.size() * grid > stride) stride = gr.members.size() * grid;
+  }
   b->part_stride = stride;
   cudaError_t e = cudaStreamSynchronize(b->stream);   // no launch may still read the old tables
   free_ranges(b);                                    // (they belong to the old layout)
@@ -376,13 +501,9 @@ cudaError_t build_tables(lfsr_batch* b) {
     e = cudaMemcpyAsync(b->maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice,
                         b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  if (b->graph_pair) cudaGraphExecDestroy(b->graph_pair);
-  b->graph_pair = nullptr;
-  for (auto& gs : b->graph_single) {
-    if (gs) cudaGraphExecDestroy(gs);
-    gs = nullptr;
-  }
+  drop_graphs(b);
   if (e == cudaSuccess && b->owns_jobs) e = balance_groups(b);
+  if (e == cudaSuccess) e = persist_setup(b);
   return e;
 }
 
@@ -403,6 +524,27 @@ cudaError_t time_iteration(lfsr_batch* b, int cls, int grp, double* ms) {
     cudaEventDestroy(x.b);
   }
   *ms = t;
+  return e;
+}
+
+// Device time of two iterations in the current form, after one warm-up
+// iteration (all at the current parity, which advances).
+cudaError_t time_form(lfsr_batch* b, double* ms) {
+  cudaEvent_t a = nullptr, c = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&c);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    if (i == 1) e = cudaEventRecord(a, b->stream);
+    if (e == cudaSuccess) e = form_iteration(b, b->parity, b->stream);
+    b->parity ^= 1;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(c, b->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(c);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, c);
+  *ms = t;
+  if (a) cudaEventDestroy(a);
+  if (c) cudaEventDestroy(c);
   return e;
 }
 
@@ -434,6 +576,8 @@ cudaError_t lfsr::batch_assign(lfsr_batch* b, const std::vector<lfsr_handle*>& j
   const int n = (int)b->jobs.size();
   if (n == 0) return cudaSuccess;
   b->g = b->jobs[0]->g;
+  b->g.wait_ns = b->wait_ns;
+  b->g.wait_unreachable = b->wait_unreachable;
   b->sm_count = b->jobs[0]->sm_count;
   b->cg_iters = b->jobs[0]->prm.cg_iters;
   int optin = 0;
@@ -591,6 +735,19 @@ int lfsr_batch_load(lfsr_batch* b, int job, const float* lr_views, const float* 
   if (job < 0 || job >= (int)b->jobs.size()) return bfail(b, LFSR_EINVAL, "job out of range");
   const int rc = load_state(b->jobs[job], lr_views, x0, mem, b->parity);
   if (rc != LFSR_OK) return bfail(b, rc, lfsr_last_error(b->jobs[job]));
+  // Re-arm the batch's reduction counters and the persistent form's
+  // barrier count.  Between launches they are zero (a multiple of the grid
+  // for the barrier count) and this is a no-op; after an iteration whose
+  // barrier wait ran out, CTAs that abandoned the work arrived at later
+  // phases' counters while others were still in earlier ones, so a
+  // counter's reset can have dropped an arrival.
+  cudaError_t e = cudaSuccess;
+  if (b->counters)
+    e = cudaMemsetAsync(b->counters, 0, b->cap_counters * sizeof(unsigned int), b->stream);
+  if (e == cudaSuccess && b->bar)
+    e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned long long), b->stream);
+  if (e != cudaSuccess)
+    return bfail(b, LFSR_ECUDA, std::string("batch load: ") + cudaGetErrorString(e));
   return LFSR_OK;
 }
 
@@ -730,6 +887,20 @@ int lfsr_batch_autotune(lfsr_batch* b) {
     b->nla_chunk = best;
     if (e == cudaSuccess) e = build_tables(b);   // drops the graphs of the old shapes
   }
+  // launch form: the per-phase launches against the persistent launch
+  // (when a compiled instance fits the batch)
+  if (e == cudaSuccess && b->persist_ok) {
+    double ms[2] = {0.0, 0.0};
+    for (int form : {LFSR_BATCH_PHASES, LFSR_BATCH_PERSISTENT}) {
+      b->form = form;
+      e = time_form(b, &ms[form]);
+      if (e != cudaSuccess) break;
+    }
+    b->form = (e == cudaSuccess && ms[LFSR_BATCH_PERSISTENT] < ms[LFSR_BATCH_PHASES])
+                  ? LFSR_BATCH_PERSISTENT
+                  : LFSR_BATCH_PHASES;
+    drop_graphs(b);
+  }
   for (lfsr_handle* h : b->jobs) h->parity = b->parity;
   if (e != cudaSuccess)
     return bfail(b, LFSR_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
@@ -769,8 +940,43 @@ int lfsr_batch_set_tuning(lfsr_batch* b, const int* op_tile, int n_groups, int n
 
 int lfsr_batch_launches_per_iteration(const lfsr_batch* b) {
   if (!b) return 0;
+  if (b->form == LFSR_BATCH_PERSISTENT) return 1;
   const int G = (int)b->groups.size();
   return 2 + G + b->cg_iters * (2 + G);
+}
+
+int lfsr_batch_persistent_available(const lfsr_batch* b) { return b && b->persist_ok ? 1 : 0; }
+
+int lfsr_batch_form(const lfsr_batch* b) { return b ? b->form : -1; }
+
+int lfsr_batch_set_form(lfsr_batch* b, int form) {
+  if (!b) return bfail(nullptr, LFSR_EINVAL, "batch is NULL");
+  if (form != LFSR_BATCH_PHASES && form != LFSR_BATCH_PERSISTENT)
+    return bfail(b, LFSR_EINVAL, "form must be LFSR_BATCH_PHASES or LFSR_BATCH_PERSISTENT");
+  if (form == LFSR_BATCH_PERSISTENT && !b->persist_ok)
+    return bfail(b, LFSR_EUNSUPPORTED,
+                 "no compiled persistent iteration fits this batch (operator groups, their tile "
+                 "sides, the NLTV window and patch, the weight scheme or the storage kind)");
+  const cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess)
+    return bfail(b, LFSR_ECUDA, std::string("set form: ") + cudaGetErrorString(e));
+  b->form = form;
+  drop_graphs(b);   // they hold the other form's launches
+  return LFSR_OK;
+}
+
+int lfsr_batch_set_device_wait(lfsr_batch* b, int64_t limit_ns, int test_unreachable) {
+  if (!b) return bfail(nullptr, LFSR_EINVAL, "batch is NULL");
+  if (limit_ns < 0) return bfail(b, LFSR_EINVAL, "limit_ns must be >= 0");
+  const cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess)
+    return bfail(b, LFSR_ECUDA, std::string("set device wait: ") + cudaGetErrorString(e));
+  b->wait_ns = (unsigned long long)limit_ns;
+  b->wait_unreachable = test_unreachable ? 1 : 0;
+  b->g.wait_ns = b->wait_ns;
+  b->g.wait_unreachable = b->wait_unreachable;
+  drop_graphs(b);   // the captured launches hold the old limit
+  return LFSR_OK;
 }
 
 }  // extern "C"

@@ -288,6 +288,40 @@ cudaError_t fast_plan_table(const Geom& g, OpPlan* plan, int smem_limit, int til
 cudaError_t nl_launch(int mode, const Geom& g, const NlPlan& plan, const NlArgs& a,
                       cudaStream_t s);
 
+// The persistent batch iteration (batch_persist.cu): one cooperative launch
+// per ADMM iteration runs every phase of Algorithm 1 for every light field
+// of a batch -- the regulariser block, the data block of each operator
+// group, the x-step initialisation and K x (NLTV apply, normal matrix of
+// each group, CG update) -- over the same work units as the per-phase
+// launches, with a bounded grid barrier between dependent phases.  The
+// launch arguments of one iteration parity live in device memory.
+constexpr int PERSIST_MAX_GROUPS = 2;
+struct PersistArgs {
+  TableArgs nlw, init;               // regulariser block, x-step initialisation
+  TableArgs nla[2], upd[2];          // per CG-step parity
+  TableArgs data[PERSIST_MAX_GROUPS];
+  TableArgs norm[2][PERSIST_MAX_GROUPS];
+  OpPlan P[PERSIST_MAX_GROUPS];      // operator plan of each group (64 x 64 tiles)
+  int cg_iters;
+  int sx_off;                        // float offset of the regulariser block's divergence tile
+};
+// The (scale, kb) of each group, the NLTV window and patch radii and the
+// storage kind decide whether a compiled persistent kernel exists; order[]
+// receives the batch's group index for each slot of PersistArgs.
+bool persist_supported(const Geom& g, const Geom* gg, const int* tile, int n_groups, int* order);
+cudaError_t persist_prepare(const Geom& g, const Geom* gg, const int* order, int n_groups,
+                            int smem_optin);
+// Dynamic shared memory of the launch and CTAs per SM at that size (0: the
+// kernel cannot run with one CTA per SM).
+size_t persist_smem(const Geom& g, const OpPlan* P, int n_groups, int* sx_off);
+int persist_occupancy(const Geom& g, const Geom* gg, const int* order, int n_groups,
+                      size_t smem);
+// args: device pointer of the iteration's PersistArgs; bar: the batch's
+// grid-barrier arrival counter; grid: SMs x 1 (every CTA co-resident).
+cudaError_t persist_launch(const Geom& g, const Geom* gg, const int* order, int n_groups,
+                           const PersistArgs* args, unsigned long long* bar, size_t smem,
+                           int grid, cudaStream_t s);
+
 // Table-driven vector kernels: one CTA per chunk of HR pixels.
 constexpr int VEC_THREADS = 512;
 cudaError_t cg_init_launch(const Geom& g, const TableArgs& t, cudaStream_t s);

@@ -144,9 +144,14 @@ __device__ __forceinline__ void split_bits2(float2 t, unsigned& b0, unsigned& b1
 // SINGLE: one light field whose fields come by value (kernel parameters,
 // read from the constant bank); else a table of light fields, the fields of
 // the current one in registers.
+// The body runs in the kernel below and, as one phase among others, in the
+// persistent batch iteration (batch_persist.cuh): every CTA of the launch
+// calls it, with the dynamic shared memory laid out by P.  run == false
+// takes no unit (the CTA still zeroes its partial slots and arrives at the
+// final reduction, which keeps the arrival counters aligned).
 template <int MODE, int Z, int KB, bool SINGLE, int TILE = FAST_TILE>
-__global__ void __launch_bounds__(FT_THREADS, 1)
-k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs one) {
+__device__ __forceinline__ void op_fast_body(const Geom& g, const OpPlan& P, const TableArgs& t,
+                                             const JobArgs& one, bool run = true) {
   using SH = FastShape<Z, KB, TILE>;
   constexpr int T = SH::T, R = SH::R, NL = SH::NL, NE = SH::NE, MG = SH::MG, NGp = SH::NGp;
   constexpr int NEp = SH::NEp, NHp = SH::NHp, NVp = SH::NVp, VB = SH::VB;
@@ -164,10 +169,10 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
   const int S = g.S;
   const float Sf = (float)S;
   const int NPc = P.NPc, NAc = P.NAc;
-  const int units = t.total_units;
+  const int units = run ? t.total_units : 0;
   // this CTA's contiguous range of units: cost-balanced ranges when given,
   // else the even split
-  const bool ranged = t.cta_unit0 != nullptr;
+  const bool ranged = run && t.cta_unit0 != nullptr;
   const int u_begin = ranged ? __ldg(t.cta_unit0 + blockIdx.x)
                              : (int)((long long)blockIdx.x * units / gridDim.x);
   const int u_end = ranged ? __ldg(t.cta_unit0 + blockIdx.x + 1)
@@ -819,7 +824,12 @@ k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs o
 #undef JF
 #undef JNVB
 #undef JQLR
+}
 
+template <int MODE, int Z, int KB, bool SINGLE, int TILE = FAST_TILE>
+__global__ void __launch_bounds__(FT_THREADS, 1)
+k_operator_fast(const Geom g, const OpPlan P, const TableArgs t, const JobArgs one) {
+  op_fast_body<MODE, Z, KB, SINGLE, TILE>(g, P, t, one);
 }
 
 // Shared-memory layout and tiling of the specialised kernel for tile side

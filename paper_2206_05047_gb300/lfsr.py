@@ -37,6 +37,8 @@ LFSR_ADJOINT_BACKWARD_WARP = 1
 ADJOINTS = {"exact": LFSR_ADJOINT_EXACT, "backward": LFSR_ADJOINT_BACKWARD_WARP}
 LFSR_REQ_QUEUED, LFSR_REQ_ACTIVE, LFSR_REQ_DONE, LFSR_REQ_FETCHED, LFSR_REQ_FAILED = 0, 1, 2, 3, 4
 LFSR_REQ_CANCELLED = 5
+LFSR_BATCH_PHASES, LFSR_BATCH_PERSISTENT = 0, 1
+BATCH_FORMS = {"phases": LFSR_BATCH_PHASES, "persistent": LFSR_BATCH_PERSISTENT}
 # precision names accepted by Solver(precision=...) and the benchmark
 PRECISIONS = {"fp32": LFSR_FP32, "fp16": LFSR_FP16_STORAGE, "bf16": LFSR_BF16_STORAGE,
               "fp16-views32": LFSR_FP16_STORAGE | LFSR_KEEP_VIEWS_FP32,
@@ -54,7 +56,8 @@ EXPORTS = ("lfsr_create", "lfsr_solve", "lfsr_destroy", "lfsr_last_error", "lfsr
            "lfsr_batch_iterate", "lfsr_batch_get_x", "lfsr_batch_stats",
            "lfsr_batch_launches_per_iteration", "lfsr_batch_set_profiling",
            "lfsr_batch_kernel_times", "lfsr_batch_autotune", "lfsr_batch_tuning",
-           "lfsr_batch_set_tuning", "lfsr_estimate_state_bytes", "lfsr_server_create",
+           "lfsr_batch_set_tuning", "lfsr_batch_persistent_available", "lfsr_batch_form",
+           "lfsr_batch_set_form", "lfsr_batch_set_device_wait", "lfsr_estimate_state_bytes", "lfsr_server_create",
            "lfsr_server_destroy", "lfsr_server_last_error", "lfsr_server_submit",
            "lfsr_server_step", "lfsr_server_status", "lfsr_server_fetch", "lfsr_server_stats",
            "lfsr_server_cancel")
@@ -160,6 +163,10 @@ def load_library(path: str = _LIB_PATH):
         "lfsr_server_stats": (C.c_int, [H, C.POINTER(lfsr_server_stats_t)]),
         "lfsr_server_cancel": (C.c_int, [H, C.c_int64]),
         "lfsr_batch_set_tuning": (C.c_int, [H, C.POINTER(C.c_int), C.c_int, C.c_int]),
+        "lfsr_batch_persistent_available": (C.c_int, [H]),
+        "lfsr_batch_form": (C.c_int, [H]),
+        "lfsr_batch_set_form": (C.c_int, [H, C.c_int]),
+        "lfsr_batch_set_device_wait": (C.c_int, [H, C.c_int64, C.c_int]),
         "lfsr_batch_tuning": (C.c_int, [H, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
         "lfsr_batch_kernel_times": (C.c_int, [H, C.POINTER(C.c_double),
                                               C.POINTER(C.c_int64)]),
@@ -448,7 +455,8 @@ def _bcheck(rc: int, batch=None):
 
 
 class Batch:
-    """lfsr_batch: many light fields stepped together, one launch per phase.
+    """lfsr_batch: many light fields stepped together, one launch per phase or
+    one persistent launch per iteration (set_form).
 
     jobs: a list of dicts of create()'s keyword arguments (U, V, H, W, scale,
     blur, disparity, and the solver constants, which must be equal)."""
@@ -504,12 +512,30 @@ class Batch:
         tiles = (C.c_int * 64)()
         chunk = C.c_int(0)
         g = load_library().lfsr_batch_tuning(self.handle, tiles, 64, C.byref(chunk))
-        return {"operator_tile": list(tiles[:g]), "nltv_apply_chunk": chunk.value}
+        return {"operator_tile": list(tiles[:g]), "nltv_apply_chunk": chunk.value,
+                "form": self.form()}
 
     def set_tuning(self, operator_tile, nltv_apply_chunk):
         tiles = (C.c_int * len(operator_tile))(*operator_tile)
         _bcheck(load_library().lfsr_batch_set_tuning(self.handle, tiles, len(operator_tile),
                                                      int(nltv_apply_chunk)), self.handle)
+
+    def persistent_available(self) -> bool:
+        return bool(load_library().lfsr_batch_persistent_available(self.handle))
+
+    def form(self) -> str:
+        f = load_library().lfsr_batch_form(self.handle)
+        return {v: k for k, v in BATCH_FORMS.items()}[f]
+
+    def set_form(self, form: str):
+        """'phases' (one launch per phase) or 'persistent' (one launch per
+        iteration)."""
+        _bcheck(load_library().lfsr_batch_set_form(self.handle, BATCH_FORMS[form]), self.handle)
+
+    def set_device_wait(self, limit_ns: int, test_unreachable: bool = False):
+        _bcheck(load_library().lfsr_batch_set_device_wait(self.handle, int(limit_ns),
+                                                          int(bool(test_unreachable))),
+                self.handle)
 
     def set_profiling(self, on: bool):
         _bcheck(load_library().lfsr_batch_set_profiling(self.handle, int(bool(on))), self.handle)

@@ -136,7 +136,8 @@ def test_batch_tunings_give_the_same_results(tiles, chunk):
     probs, kws = _jobs()
     b = lfsr.Batch(kws)
     b.set_tuning(tiles, chunk)
-    assert b.tuning() == {"operator_tile": list(tiles), "nltv_apply_chunk": chunk}
+    assert b.tuning() == {"operator_tile": list(tiles), "nltv_apply_chunk": chunk,
+                          "form": "phases"}
     for j, pr in enumerate(probs):
         b.load(j, _t(pr.y), _t(pr.x0))
     b.iterate(5)
