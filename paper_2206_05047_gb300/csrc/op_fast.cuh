@@ -31,11 +31,12 @@ namespace lfsr {
 constexpr int FT_THREADS = 512;
 constexpr int FT_VB = 2;   // views processed together per pass through the stages
 
-// Outputs per task m in [4, 8] that needs the fewest 512-thread passes for
-// `rows` x ceil(n / m) tasks (ties: the smaller m, i.e. fewer registers).
-constexpr int pick_block(int rows, int n) {
-  int best = 4, best_passes = 1 << 30;
-  for (int m = 4; m <= 8; ++m) {
+// Outputs per task m in [lo, 8] that needs the fewest 512-thread passes for
+// `rows` x ceil(n / m) tasks (ties: the smaller m, i.e. fewer registers and
+// a shorter chain per thread).
+constexpr int pick_block(int rows, int n, int lo = 4) {
+  int best = lo, best_passes = 1 << 30;
+  for (int m = lo; m <= 8; ++m) {
     const int passes = (rows * ((n + m - 1) / m) + FT_THREADS - 1) / FT_THREADS;
     if (passes < best_passes) {
       best_passes = passes;
@@ -77,7 +78,8 @@ struct FastShape {
   // exactly T / Z values of m
   static constexpr bool ALIGNED = (T % Z) == 0;
   static constexpr int NM = ALIGNED ? T / Z : (T - 1) / Z + 2;  // m values per tile
-  static constexpr int MB5 = pick_block(NG, NM);   // both views per task
+  // (from 3: a single pass then keeps more warps busy with shorter chains)
+  static constexpr int MB5 = pick_block(NG, NM, 3);   // both views per task
   static constexpr int NB5 = (NM + MB5 - 1) / MB5;
   static constexpr int DMIN = -(R / Z) - 1;                  // safe delta bounds (all phases)
   static constexpr int DMAX = (Z - 1 + R) / Z;
@@ -597,12 +599,12 @@ __device__ __forceinline__ void op_fast_body(const Geom& g, const OpPlan& P, con
         float2 fy, fx;
         split_bits2(fma2(tv2, om2, S2), by0, by1, fy);
         split_bits2(fma2(tu2, om2, S2), bx0, bx1, fx);
-        // weights: (1 - fx) is exact (fx is a multiple of the shift's ulp)
-        const float2 omfx = sub2(pk(1.f, 1.f), fx);
+        // weights times the value: the bottom / top rows' shares, then the
+        // right taps' shares and the left ones as the remainders
         const float2 ty = mul2(fy, tv);
         const float2 by = sub2(tv, ty);
-        const float2 tl = mul2(by, omfx), bl = mul2(ty, omfx);
         const float2 tr = mul2(fx, by), br = mul2(fx, ty);
+        const float2 tl = sub2(by, tr), bl = sub2(ty, br);
         scatter(tl.x, bl.x, tr.x, br.x, ap + by0 * (unsigned)NAc + bx0, pend0, pa0, pt0, pb0);
         if (two) scatter(tl.y, bl.y, tr.y, br.y, ap + by1 * (unsigned)NAc + bx1, pend1, pa1, pt1, pb1);
       };
