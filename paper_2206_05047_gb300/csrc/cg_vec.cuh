@@ -23,7 +23,22 @@ __device__ __forceinline__ void cg_init_acc_unit(const TableArgs& tb, int unit, 
   const int c0 = (unit - jp->unit0) * jp->chunk;
   const int c1 = min(n, c0 + jp->chunk);
   double part = 0.0;
-  for (int i = c0 + threadIdx.x; i < c1; i += VEC_THREADS) {
+  // chunks are whole multiples of 32 floats and every buffer starts on a
+  // 256-byte boundary: [c0, c1 & ~3) in float4 steps, then the tail
+  const int v0 = c0 >> 2, v1 = c1 >> 2;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int v = v0 + (int)threadIdx.x; v < v1; v += VEC_THREADS) {
+    const float4 a4 = reinterpret_cast<const float4*>(va)[v];
+    reinterpret_cast<float4*>(va)[v] = z4;
+    const float4 r4 = make_float4(-a4.x, -a4.y, -a4.z, -a4.w);
+    reinterpret_cast<float4*>(rv)[v] = r4;
+    reinterpret_cast<float4*>(x_next)[v] = __ldg(reinterpret_cast<const float4*>(x) + v);
+    part += (double)r4.x * (double)r4.x;
+    part += (double)r4.y * (double)r4.y;
+    part += (double)r4.z * (double)r4.z;
+    part += (double)r4.w * (double)r4.w;
+  }
+  for (int i = 4 * v1 + (int)threadIdx.x; i < c1; i += VEC_THREADS) {
     const float r = -va[i];
     va[i] = 0.f;
     rv[i] = r;

@@ -247,22 +247,35 @@ __device__ __forceinline__ void nla2_unit(const Geom& g, const TableArgs& tb, in
   const int ty = tile / jp->tiles_x, tx = tile - ty * jp->tiles_x;
   const int i0 = ty * T, j0 = tx * T;
   const int TRr = min(T, Hh - i0), TRc = min(T, Wh - j0);
+  // p = r + beta p_old (or p_old) over the tile and a WR halo: every
+  // thread's loads are issued before any is used
   const int first = sc->cg_first;
   const float beta = (float)sc->beta;
-  for (int t = tid; t < NP * NP; t += NA_THREADS) {
+  const bool use_beta = jp->use_beta != 0;
+  const float* __restrict__ r_in = jp->r;
+  const float* __restrict__ p_in = jp->p_old;
+  float* __restrict__ p_out = jp->p_new;
+  constexpr int NST = (NP * NP + NA_THREADS - 1) / NA_THREADS;
+  float ra[NST], pa[NST];
+#pragma unroll
+  for (int it = 0; it < NST; ++it) {
+    const int t = tid + it * NA_THREADS;
     const int rr = t / NP, cc = t - rr * NP;
     const int hi = i0 - WR + rr, hj = j0 - WR + cc;
-    float v = 0.f;
-    if (hi >= 0 && hi < Hh && hj >= 0 && hj < Wh) {
-      const size_t gi = (size_t)hi * Wh + hj;
-      if (jp->use_beta) {
-        v = __ldg(jp->r + gi);
-        if (!first) v = fmaf(beta, __ldg(jp->p_old + gi), v);
-        if (rr >= WR && rr < WR + TRr && cc >= WR && cc < WR + TRc) jp->p_new[gi] = v;
-      } else {
-        v = __ldg(jp->p_old + gi);
-      }
-    }
+    const bool in = t < NP * NP && hi >= 0 && hi < Hh && hj >= 0 && hj < Wh;
+    const size_t gi = in ? (size_t)hi * Wh + hj : 0;
+    ra[it] = (in && use_beta) ? __ldg(r_in + gi) : 0.f;
+    pa[it] = (in && !(use_beta && first)) ? __ldg(p_in + gi) : 0.f;
+  }
+#pragma unroll
+  for (int it = 0; it < NST; ++it) {
+    const int t = tid + it * NA_THREADS;
+    if (t >= NP * NP) break;
+    const int rr = t / NP, cc = t - rr * NP;
+    // outside the image both loads gave 0, so v = 0 there
+    const float v = use_beta ? (first ? ra[it] : fmaf(beta, pa[it], ra[it])) : pa[it];
+    if (use_beta && rr >= WR && rr < WR + TRr && cc >= WR && cc < WR + TRc)
+      p_out[(size_t)(i0 - WR + rr) * Wh + (j0 - WR + cc)] = v;
     sP[rr * NPp + cc] = v;
   }
   __syncthreads();
