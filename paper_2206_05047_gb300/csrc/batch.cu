@@ -338,6 +338,60 @@ cudaError_t balance_groups(lfsr_batch* b) {
   return e;
 }
 
+// Cost-balanced CTA ranges of a batch that cannot time its own launches (a
+// server's, rebuilt whenever a request joins or leaves): each member's unit
+// costs as its handle measured them at creation (the single-light-field
+// kernel runs the same units in the same order at 64 x 64 tiles), a member
+// without them (too few units to time) at the measured members' mean cost
+// per unit scaled by its views per unit; the split packs them over the
+// group's CTAs (see lfsr::split_by_unit_costs).  A group without any
+// measured member keeps the even split.
+cudaError_t member_cost_ranges(lfsr_batch* b) {
+  cudaError_t e = cudaSuccess;
+  for (Group& gr : b->groups) {
+    if (gr.tile != FAST_TILE || gr.units < 2 * gr.grid) continue;
+    double sum = 0.0, sw = 0.0;
+    long long n_meas = 0;
+    int members_meas = 0;
+    for (size_t m = 0; m < gr.members.size(); ++m) {
+      const lfsr_handle* h = b->jobs[gr.members[m]];
+      if ((int)h->unit_cost.size() != gr.units_m[m]) continue;
+      for (double c : h->unit_cost) sum += c;
+      n_meas += (long long)h->unit_cost.size();
+      sw += h->unit_cost_tile;
+      ++members_meas;
+    }
+    if (members_meas == 0) continue;
+    const double mean = sum / (double)n_meas;
+    sw /= members_meas;
+    std::vector<double> base((size_t)gr.units);
+    std::vector<char> tile_start((size_t)gr.units, 0);
+    for (size_t m = 0; m < gr.members.size(); ++m) {
+      const lfsr_handle* h = b->jobs[gr.members[m]];
+      const int pairs = (h->g.sk + FAST_VIEWS - 1) / FAST_VIEWS;
+      const bool meas = (int)h->unit_cost.size() == gr.units_m[m];
+      for (int u = 0; u < gr.units_m[m]; ++u) {
+        const int pr = u % pairs;
+        const int nv = std::min(FAST_VIEWS, h->g.sk - FAST_VIEWS * pr);
+        base[(size_t)gr.unit0[m] + u] = meas ? h->unit_cost[u] : mean * nv / FAST_VIEWS;
+        if (pr == 0) tile_start[(size_t)gr.unit0[m] + u] = 1;
+      }
+    }
+    std::vector<int> r0;
+    double mx = 0.0, mn = 0.0;
+    if (!split_by_unit_costs(base, sw, tile_start, gr.grid, &r0, &mx, &mn)) continue;
+    gr.split[1] = mx / mn;
+    e = fault_alloc() ? cudaErrorMemoryAllocation
+                      : cudaMalloc((void**)&gr.cta_unit0, r0.size() * sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(gr.cta_unit0, r0.data(), r0.size() * sizeof(int), cudaMemcpyHostToDevice,
+                          b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // r0 is a local buffer
+    if (e != cudaSuccess) break;
+  }
+  return e;
+}
+
 // The persistent form for the current groups and tables: whether a compiled
 // instance fits them (else the batch keeps the per-phase launches), its
 // shared memory and grid, and the arguments of both iteration parities
@@ -502,7 +556,7 @@ cudaError_t build_tables(lfsr_batch* b) {
                         b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   drop_graphs(b);
-  if (e == cudaSuccess && b->owns_jobs) e = balance_groups(b);
+  if (e == cudaSuccess) e = b->owns_jobs ? balance_groups(b) : member_cost_ranges(b);
   if (e == cudaSuccess) e = persist_setup(b);
   return e;
 }

@@ -478,37 +478,17 @@ int pack_units(const SplitCost& c, double cap, std::vector<int>* starts) {
 
 }  // namespace
 
-bool lfsr::split_by_cost(const std::vector<long long>& clk, int units, int grid,
-                         const std::vector<char>& tile_start, std::vector<int>* r0,
-                         double ratio[2]) {
-  ratio[0] = ratio[1] = 0.0;
-  if (units < 1 || grid < 1 || (int)tile_start.size() != units ||
-      clk.size() != (size_t)units + grid)
-    return false;
-  std::vector<double> cost(units);
-  std::vector<char> staged(units, 0);
-  std::vector<double> even(grid, 0.0), excess;
-  for (int b = 0; b < grid; ++b) {
-    const int ub = (int)((long long)b * units / grid), ue = (int)((long long)(b + 1) * units / grid);
-    for (int u = ub; u < ue; ++u) {
-      const long long next = u + 1 < ue ? clk[u + 1] : clk[(size_t)units + b];
-      cost[u] = next > clk[u] ? (double)(next - clk[u]) : 1.0;
-      staged[u] = (u == ub || tile_start[u]) ? 1 : 0;
-      even[b] += cost[u];
-    }
-    for (int u = ub; u + 1 < ue; ++u)
-      if (staged[u] && !staged[u + 1]) excess.push_back(cost[u] - cost[u + 1]);
-  }
+bool lfsr::split_by_unit_costs(const std::vector<double>& base, double sw,
+                               const std::vector<char>& tile_start, int grid,
+                               std::vector<int>* r0, double* max_cost, double* mean_cost) {
+  const int units = (int)base.size();
+  if (units < 1 || grid < 1 || (int)tile_start.size() != units) return false;
   SplitCost sc;
   sc.tile_start = &tile_start;
-  if (!excess.empty()) {
-    std::nth_element(excess.begin(), excess.begin() + excess.size() / 2, excess.end());
-    sc.sw = std::max(0.0, excess[excess.size() / 2]);
-  }
-  sc.base.resize(units);
+  sc.sw = sw;
+  sc.base = base;
   double total = 0.0, lo = 0.0;
   for (int u = 0; u < units; ++u) {
-    sc.base[u] = std::max(1.0, cost[u] - (staged[u] ? sc.sw : 0.0));
     total += sc.base[u] + (tile_start[u] ? sc.sw : 0.0);
     lo = std::max(lo, sc.base[u] + sc.sw);
   }
@@ -529,20 +509,57 @@ bool lfsr::split_by_cost(const std::vector<long long>& clk, int units, int grid,
     bal_max = std::max(bal_max, v);
     bal_sum += v;
   }
+  *max_cost = bal_max;
+  *mean_cost = bal_sum / grid;
+  r0->assign((size_t)grid + 1, units);
+  for (size_t r = 0; r < starts.size(); ++r) (*r0)[r] = starts[r];
+  (*r0)[0] = 0;
+  return true;
+}
+
+bool lfsr::split_by_cost(const std::vector<long long>& clk, int units, int grid,
+                         const std::vector<char>& tile_start, std::vector<int>* r0,
+                         double ratio[2], std::vector<double>* base_out, double* sw_out) {
+  ratio[0] = ratio[1] = 0.0;
+  if (units < 1 || grid < 1 || (int)tile_start.size() != units ||
+      clk.size() != (size_t)units + grid)
+    return false;
+  std::vector<double> cost(units);
+  std::vector<char> staged(units, 0);
+  std::vector<double> even(grid, 0.0), excess;
+  for (int b = 0; b < grid; ++b) {
+    const int ub = (int)((long long)b * units / grid), ue = (int)((long long)(b + 1) * units / grid);
+    for (int u = ub; u < ue; ++u) {
+      const long long next = u + 1 < ue ? clk[u + 1] : clk[(size_t)units + b];
+      cost[u] = next > clk[u] ? (double)(next - clk[u]) : 1.0;
+      staged[u] = (u == ub || tile_start[u]) ? 1 : 0;
+      even[b] += cost[u];
+    }
+    for (int u = ub; u + 1 < ue; ++u)
+      if (staged[u] && !staged[u + 1]) excess.push_back(cost[u] - cost[u + 1]);
+  }
+  double sw = 0.0;
+  if (!excess.empty()) {
+    std::nth_element(excess.begin(), excess.begin() + excess.size() / 2, excess.end());
+    sw = std::max(0.0, excess[excess.size() / 2]);
+  }
+  std::vector<double> base(units);
+  for (int u = 0; u < units; ++u) base[u] = std::max(1.0, cost[u] - (staged[u] ? sw : 0.0));
+  if (base_out) *base_out = base;
+  if (sw_out) *sw_out = sw;
   double even_max = 0.0, even_sum = 0.0;
   for (double v : even) {
     even_max = std::max(even_max, v);
     even_sum += v;
   }
   ratio[0] = even_max / (even_sum / grid);
-  ratio[1] = bal_max / (bal_sum / grid);
+  double bal_max = 0.0, bal_mean = 0.0;
+  if (!split_by_unit_costs(base, sw, tile_start, grid, r0, &bal_max, &bal_mean)) return false;
+  ratio[1] = bal_max / bal_mean;
   if (!(bal_max < 0.99 * even_max)) {   // not worth a change: the even split stays
     ratio[1] = ratio[0];
     return false;
   }
-  r0->assign((size_t)grid + 1, units);
-  for (size_t r = 0; r < starts.size(); ++r) (*r0)[r] = starts[r];
-  (*r0)[0] = 0;
   return true;
 }
 
@@ -574,7 +591,9 @@ cudaError_t balance_operator_units(lfsr_handle* h) {
   std::vector<char> tile_start(units);
   for (int u = 0; u < units; ++u) tile_start[u] = u % upt == 0;
   std::vector<int> r0;
-  if (!split_by_cost(c, units, grid, tile_start, &r0, h->op_split)) return cudaSuccess;
+  if (!split_by_cost(c, units, grid, tile_start, &r0, h->op_split, &h->unit_cost,
+                     &h->unit_cost_tile))
+    return cudaSuccess;
   e = dalloc(h, &h->cta_unit0, (size_t)grid + 1);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->cta_unit0, r0.data(), r0.size() * sizeof(int), cudaMemcpyHostToDevice,

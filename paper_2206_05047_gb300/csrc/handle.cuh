@@ -106,6 +106,11 @@ struct lfsr_handle {
   int fchunk = 0;                           // HR pixels per CTA of the fused operator tails
   int* cta_unit0 = nullptr;                 // cost-balanced operator ranges (grid_op + 1), or NULL
   double op_split[2] = {0.0, 0.0};          // max / mean CTA cost: even split, balanced ranges
+  // measured cost of each operator unit (SM clocks, without tile staging) and
+  // of staging a tile, from the timing launch at creation (empty when not
+  // measured); a batch that cannot time its own launches splits with them
+  std::vector<double> unit_cost;
+  double unit_cost_tile = 0.0;
   bool profiling = false;
   std::vector<lfsr::ProfEvent> prof;
   double prof_ms[8] = {0};
@@ -131,7 +136,15 @@ int create_handle(const lfsr_params* params, void* cuda_stream, lfsr_handle** ou
 // with r0 = the grid + 1 range starts, when the split beats the even one by
 // more than 1 %.
 bool split_by_cost(const std::vector<long long>& clk, int units, int grid,
-                   const std::vector<char>& tile_start, std::vector<int>* r0, double ratio[2]);
+                   const std::vector<char>& tile_start, std::vector<int>* r0, double ratio[2],
+                   std::vector<double>* base_out = nullptr, double* sw_out = nullptr);
+// The same split from per-unit costs (base[u], without tile staging) and
+// the cost sw of staging a tile: r0 = the grid + 1 range starts, the
+// slowest range's cost and the mean range cost.  False when the units do
+// not fit `grid` ranges.
+bool split_by_unit_costs(const std::vector<double>& base, double sw,
+                         const std::vector<char>& tile_start, int grid, std::vector<int>* r0,
+                         double* max_cost, double* mean_cost);
 // Work units of a launch kind for this light field.
 int kind_units(const lfsr_handle* h, int kind);
 // Reduction slot (RED_*) of a launch kind.

@@ -119,7 +119,9 @@ int admit(lfsr_server* s) {
       p.views = r.view_list.empty() ? nullptr : r.view_list.data();
       p.proj_err = r.proj_err.empty() ? nullptr : r.proj_err.data();
       lfsr_handle* h = nullptr;
-      int rc = create_handle(&p, s->stream, &h, false);
+      // (its operator units' costs are measured here: the batch splits its
+      // launches with them at each rebuild)
+      int rc = create_handle(&p, s->stream, &h, true);
       if (rc == LFSR_OK && (!h->op.fast || !h->nlf)) rc = LFSR_EUNSUPPORTED;
       const int parity = s->batch ? batch_parity(s->batch) : 0;
       if (rc == LFSR_OK)

@@ -162,3 +162,29 @@ def test_form_choice_and_unsupported_batches():
     assert ei.value.code == lfsr.LFSR_EUNSUPPORTED
     assert b.form() == "phases"
     b.close()
+
+
+def test_persistent_cg_early_exit_matches_per_phase():
+    """With a CG threshold tau the x-step of each light field stops on its own
+    step; the persistent launch skips the finished light fields' work in
+    every later phase exactly as the per-phase launches do."""
+    probs, kws = _jobs(GEOMS_W5, 5, seed0=140)
+    # a threshold above every light field's final |r|^2 of a run without one:
+    # the light fields whose residual falls faster stop before step 5
+    b = lfsr.Batch(kws)
+    _run(b, probs, 5)
+    pis = [b.stats(j)["cg_pi"] for j in range(len(probs))]
+    b.close()
+    for kw in kws:
+        kw["cg_tol"] = float(1.5 * max(pis))
+    b = lfsr.Batch(kws)
+    x_phase = _run(b, probs, 5)
+    steps_phase = [b.stats(j)["cg_steps"] for j in range(len(probs))]
+    b.set_form("persistent")
+    x_pers = _run(b, probs, 5)
+    steps_pers = [b.stats(j)["cg_steps"] for j in range(len(probs))]
+    assert steps_pers == steps_phase
+    assert min(steps_pers) < 5            # the threshold ends some x-steps early
+    for j in range(len(probs)):
+        assert rel_err(x_pers[j], x_phase[j]) <= 1e-5, j
+    b.close()
