@@ -68,7 +68,9 @@ k_batch_iter(const Geom g, const Geom g0, const Geom g1, const PersistArgs* __re
     for (int u = blockIdx.x; u < a->nlw.total_units; u += gridDim.x)
       nlw2_unit<NLW_BLOCK, WR, PR, ST>(g, a->nlw, u, smem, smem + a->sx_off, s_red);
   nlw2_finish(a->nlw);
-  sync();
+  // no barrier: the data rows read none of what the regulariser block
+  // writes (both only add into v, with atomics, and use their own reduction
+  // slots and counters); the initialisation below waits for both
   // data rows of each operator group: A_k x - y_k, prox, duals, v += A_k^T (...)
   persist_op<OP_DATA, Z0, KB0>(g0, a->P[0], a->data[0], ok);
   if constexpr (Z1 != 0) {
