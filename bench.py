@@ -14,6 +14,10 @@ throughput, s_k * Hh * Wh * N / t, in Mpix * ADMM-iter / s.
           CUDA events in the library's profiling mode, against the FP32 ALU
           peak (its bound); plus the whole path's HBM fraction
   cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
+  batched / served  bounded records on the first 16 light fields of the
+          batched configuration: the batch (both launch forms) against serial
+          plain solves, and Poisson arrivals (20 per second for 3 s) served by
+          the continuous-batching server against one plain solve at a time
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun (N > 1) every rank solves its own light field (replicas, weak
@@ -75,7 +79,8 @@ def args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch-record", action="store_true",
-                    help="skip the bounded batched-vs-plain record of the default line")
+                    help="skip the bounded batched-vs-plain and served-vs-plain records of the "
+                         "default line")
     ap.add_argument("--precision", default="fp32",
                     choices=["fp32", "fp16", "bf16", "fp16-views32", "bf16-views32"],
                     help="storage type of views, duals and NLTV weights (arithmetic is f32); "
@@ -504,7 +509,8 @@ def batch_subrecord(dev, stream, n_lf: int = 16, n_iter: int = 10, steps: int = 
     iterations per step, one autotuned batch (one launch per phase and
     operator group, graph-replayed) against the same light fields solved
     one after another by the plain path, in float32 and in 16-bit (fp16)
-    storage, with the PSNR of every light field compared between the two."""
+    storage, with the PSNR of every light field compared between the two.
+    Returns the record and the light fields (descriptions, arrays)."""
     import torch
     from paper_2206_05047_gb300 import lfsr
     t_gen = time.perf_counter()
@@ -594,38 +600,28 @@ def batch_subrecord(dev, stream, n_lf: int = 16, n_iter: int = 10, steps: int = 
                                                     for j in range(len(wls))])),
                      "autotuned": tuning}
     del flush
-    return rec
+    return rec, (wls, probs)
 
 
 # --------------------------------------------------------------------------
 # serving: Poisson arrivals, continuous batching under a memory budget,
 # against the same arrivals served one at a time by the plain path
 # --------------------------------------------------------------------------
-def run_serve(a):
-    import torch
+def serve_compare(wls, probs, kws, rate, seconds, slots, n_iter, seed, stream, plain=True):
+    """Poisson arrivals (rate per second over `seconds`, seeded) drawn from
+    the pool (wls, probs, kws): served by one continuous-batching server
+    (slots, 120 GB budget, 4 iterations per scheduling round), then the same
+    arrivals served first come first served by one plain solve at a time.
+    Wall-clock times on the host, inputs and results in host memory."""
     from paper_2206_05047_gb300 import lfsr
-    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
-        raise SystemExit("the serving workload runs on one GPU")
-    seed = 5000
-    t_gen = time.perf_counter()
-    wls, probs = batch_problems(64, seed)          # the pool requests are drawn from
-    t_gen = time.perf_counter() - t_gen
-    n_iter = a.iterations if a.iterations is not None else wls[0].iterations
     rng = np.random.default_rng(seed)
     arrivals, t = [], 0.0
     while True:
-        t += rng.exponential(1.0 / a.serve_rate)
-        if t > a.serve_seconds:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
             break
         arrivals.append(t)
     picks = rng.integers(0, len(wls), len(arrivals))
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
-    kws = [dict(U=w.U, V=w.V, H=w.H, W=w.W, scale=w.scale, blur=p[2], disparity=p[3],
-                lambda1=w.lambda1, lambda2=w.lambda2, mu=w.mu, nltv_window=w.window,
-                nltv_patch=w.patch, nltv_h=w.h, cg_iters=w.cg_iters, cg_tol=0.0,
-                precision=a.precision) for w, p in zip(wls, probs)]
     work = [wls[k].s_k * wls[k].HR[0] * wls[k].HR[1] * n_iter for k in picks]
     budget = 120 * 10**9
 
@@ -634,17 +630,15 @@ def run_serve(a):
 
     # warm-up: one small request through the server (kernels, allocator)
     small = min(range(len(wls)), key=lambda k: wls[k].H * wls[k].W * wls[k].s_k)
-    warm = lfsr.Server(budget, max_active=a.serve_slots, iterations=2, iterations_per_step=2,
+    warm = lfsr.Server(budget, max_active=slots, iterations=2, iterations_per_step=2,
                        stream=stream)
     warm.submit(probs[small][0], probs[small][1], **kws[small])
     while warm.stats()["done"] < 1:
         warm.step()
     warm.close()
 
-    srv = lfsr.Server(budget, max_active=a.serve_slots, iterations=n_iter, iterations_per_step=4,
+    srv = lfsr.Server(budget, max_active=slots, iterations=n_iter, iterations_per_step=4,
                       stream=stream)
-    clocks = ClockSampler(0)
-    clocks.start()
     ids, done_t, pending = {}, {}, set()
     nxt = 0
     t0 = time.perf_counter()
@@ -667,7 +661,6 @@ def run_serve(a):
         if active == 0 and not pending and nxt < len(arrivals):
             time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
     t_end = max(done_t.values())
-    clk = clocks.stop()
     st = srv.stats()
     lat = [done_t[r] - arrivals[r] for r in range(len(arrivals))]
     xs = {}
@@ -679,10 +672,7 @@ def run_serve(a):
     value = sum(work) / (t_end - arrivals[0]) / 1e6
 
     # the same arrivals, first come first served, one plain solve at a time
-    if a.serve_no_plain:
-        picks_plain = []
-    else:
-        picks_plain = picks
+    picks_plain = picks if plain else []
     solvers = {}
     for k in sorted(set(np.asarray(picks_plain).tolist())):
         solvers[k] = lfsr.Solver(stream=stream, **kws[k])
@@ -702,41 +692,92 @@ def run_serve(a):
         dpsnr.append(synth.psnr(xs[r], gt) - synth.psnr(out[k], gt))
     for sv in solvers.values():
         sv.close()
+    rec = {"value": value, "unit": UNIT, "requests": len(arrivals),
+           "arrivals_per_s": rate, "arrival_window_s": seconds,
+           "ms_first_arrival_to_last_result": 1e3 * (t_end - arrivals[0]),
+           "latency_s": {"p50": pctl(lat, 50), "p99": pctl(lat, 99), "mean": float(np.mean(lat)),
+                         "max": float(np.max(lat))},
+           "plain_serial": None, "served_vs_plain": None, "equal_psnr": None,
+           "peak_state_gb": st["bytes_peak"] / 1e9, "batch_rebuilds": st["batch_rebuilds"],
+           "gpu_launches": int(st["launches"]),
+           "h2d_bytes": int(sum(probs[k][0].nbytes + probs[k][1].nbytes for k in picks)),
+           "d2h_bytes": int(sum(xs[r].nbytes for r in xs))}
     if done_p:
         t_end_p = max(done_p.values())
         lat_p = [done_p[r] - arrivals[r] for r in range(len(arrivals))]
         value_p = sum(work) / (t_end_p - arrivals[0]) / 1e6
-    else:
-        lat_p, value_p, dpsnr = None, None, None
-    h2d = int(sum(probs[k][0].nbytes + probs[k][1].nbytes for k in picks))
-    d2h = int(sum(xs[r].nbytes for r in xs))
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1,
-            "warmup": 1, "ms_per_step": 1e3 * (t_end - arrivals[0]), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[a.precision],
+        rec["plain_serial"] = {"value": value_p, "unit": UNIT,
+                               "latency_s": {"p50": pctl(lat_p, 50), "p99": pctl(lat_p, 99),
+                                             "mean": float(np.mean(lat_p))}}
+        rec["served_vs_plain"] = value / value_p
+        rec["equal_psnr"] = {"max_abs_db": float(np.max(np.abs(dpsnr))),
+                             "mean_db": float(np.mean(dpsnr))}
+    return rec
+
+
+def serve_subrecord(stream, wls, probs, rate: float = 20.0, seconds: float = 3.0,
+                    n_iter: int = 100):
+    """Bounded served-vs-plain record for the default line: Poisson arrivals
+    at `rate` per second for `seconds`, drawn from the light fields of the
+    batched record (the first 16 of the batched configuration), each solved
+    to its N = 100 iterations by the continuous-batching server and,
+    separately, by one plain solve at a time."""
+    kws = [dict(U=w.U, V=w.V, H=w.H, W=w.W, scale=w.scale, blur=p[2], disparity=p[3],
+                lambda1=w.lambda1, lambda2=w.lambda2, mu=w.mu, nltv_window=w.window,
+                nltv_patch=w.patch, nltv_h=w.h, cg_iters=w.cg_iters, cg_tol=0.0,
+                precision="fp32") for w, p in zip(wls, probs)]
+    rec = serve_compare(wls, probs, kws, rate, seconds, 64, n_iter, 5000, stream)
+    rec["pool"] = f"the batched record's {len(wls)} light fields"
+    rec["iterations"] = n_iter
+    rec["timing"] = ("wall clock from the first arrival to the last result on the host; "
+                     "requests and results in host memory")
+    return rec
+
+
+def run_serve(a):
+    import torch
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit("the serving workload runs on one GPU")
+    seed = 5000
+    t_gen = time.perf_counter()
+    wls, probs = batch_problems(64, seed)          # the pool requests are drawn from
+    t_gen = time.perf_counter() - t_gen
+    n_iter = a.iterations if a.iterations is not None else wls[0].iterations
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    kws = [dict(U=w.U, V=w.V, H=w.H, W=w.W, scale=w.scale, blur=p[2], disparity=p[3],
+                lambda1=w.lambda1, lambda2=w.lambda2, mu=w.mu, nltv_window=w.window,
+                nltv_patch=w.patch, nltv_h=w.h, cg_iters=w.cg_iters, cg_tol=0.0,
+                precision=a.precision) for w, p in zip(wls, probs)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    rec = serve_compare(wls, probs, kws, a.serve_rate, a.serve_seconds, a.serve_slots, n_iter,
+                        seed, stream, plain=not a.serve_no_plain)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": rec["ms_first_arrival_to_last_result"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[a.precision],
             "data": "synthetic (seeded textured-plane light fields)",
             "config": {"workload": SERVE_WORKLOAD, "arrivals_per_s": a.serve_rate,
-                       "arrival_window_s": a.serve_seconds, "requests": len(arrivals),
+                       "arrival_window_s": a.serve_seconds, "requests": rec["requests"],
                        "pool": f"64 light fields of the batched distribution (seed {seed})",
-                       "iterations": n_iter, "hbm_budget_gb": budget / 1e9,
+                       "iterations": n_iter, "hbm_budget_gb": 120.0,
                        "slots": a.serve_slots, "iterations_per_step": 4,
-                       "peak_state_gb": st["bytes_peak"] / 1e9,
-                       "batch_rebuilds": st["batch_rebuilds"], "storage": a.precision,
+                       "peak_state_gb": rec["peak_state_gb"],
+                       "batch_rebuilds": rec["batch_rebuilds"], "storage": a.precision,
                        "generation_s": round(t_gen, 1),
                        "timing": "wall clock from the first arrival to the last result on "
                                  "the host; requests and results in host memory"},
-            "latency_s": {"p50": pctl(lat, 50), "p99": pctl(lat, 99), "mean": float(np.mean(lat)),
-                          "max": float(np.max(lat))},
-            "plain_serial": None if value_p is None else {
-                "value": value_p, "unit": UNIT,
-                "latency_s": {"p50": pctl(lat_p, 50), "p99": pctl(lat_p, 99),
-                              "mean": float(np.mean(lat_p))}},
-            "served_vs_plain": None if value_p is None else value / value_p,
-            "equal_psnr": None if dpsnr is None else {"max_abs_db": float(np.max(np.abs(dpsnr))),
-                                                      "mean_db": float(np.mean(dpsnr))},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+            "latency_s": rec["latency_s"],
+            "plain_serial": rec["plain_serial"],
+            "served_vs_plain": rec["served_vs_plain"],
+            "equal_psnr": rec["equal_psnr"],
+            "e2e": {"value": rec["value"], "unit": UNIT, "h2d_bytes_per_step": rec["h2d_bytes"],
+                    "d2h_bytes_per_step": rec["d2h_bytes"]},
             "roofline": None, "cpu_baseline": None,
-            "gpu_launches": int(st["launches"]), "clocks": clk}
+            "gpu_launches": rec["gpu_launches"], "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -896,9 +937,10 @@ def main():
                "sample": f"{iters} ADMM iterations (K = {wl.cg_iters}) of {wl.name} from x0, "
                          f"{dt:.1f} s"}
 
-    batch_rec = None
+    batch_rec = serve_rec = None
     if rank == 0 and world == 1 and not a.no_batch_record and a.workload == "lf9x9_256_x2":
-        batch_rec = batch_subrecord(dev, stream)
+        batch_rec, pool = batch_subrecord(dev, stream)
+        serve_rec = serve_subrecord(stream, *pool)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -925,7 +967,7 @@ def main():
                 "sai_rate": {"value": p * n_iter * a.steps * world / (t_ms / 1e3) / 1e6,
                              "unit": "HR Mpix*iter/s (reference view)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "batched": batch_rec,
+                "batched": batch_rec, "served": serve_rec,
                 "gpu_launches": int(a.steps * launches_per_solve),
                 "launches_per_iteration": launches_per_solve / max(n_iter, 1),
                 "clocks": clk}
