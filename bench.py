@@ -716,18 +716,20 @@ def serve_compare(wls, probs, kws, rate, seconds, slots, n_iter, seed, stream, p
 
 
 def serve_subrecord(stream, wls, probs, rate: float = 20.0, seconds: float = 3.0,
-                    n_iter: int = 100):
+                    n_iter: int = 100, slots: int = 16):
     """Bounded served-vs-plain record for the default line: Poisson arrivals
     at `rate` per second for `seconds`, drawn from the light fields of the
     batched record (the first 16 of the batched configuration), each solved
-    to its N = 100 iterations by the continuous-batching server and,
-    separately, by one plain solve at a time."""
+    to its N = 100 iterations by the continuous-batching server (`slots`
+    requests active at most: fewer slots finish the early requests sooner,
+    more slots batch more) and, separately, by one plain solve at a time."""
     kws = [dict(U=w.U, V=w.V, H=w.H, W=w.W, scale=w.scale, blur=p[2], disparity=p[3],
                 lambda1=w.lambda1, lambda2=w.lambda2, mu=w.mu, nltv_window=w.window,
                 nltv_patch=w.patch, nltv_h=w.h, cg_iters=w.cg_iters, cg_tol=0.0,
                 precision="fp32") for w, p in zip(wls, probs)]
-    rec = serve_compare(wls, probs, kws, rate, seconds, 64, n_iter, 5000, stream)
+    rec = serve_compare(wls, probs, kws, rate, seconds, slots, n_iter, 5000, stream)
     rec["pool"] = f"the batched record's {len(wls)} light fields"
+    rec["slots"] = slots
     rec["iterations"] = n_iter
     rec["timing"] = ("wall clock from the first arrival to the last result on the host; "
                      "requests and results in host memory")
