@@ -514,7 +514,10 @@ int lfsr_server_submit(lfsr_server *s, const lfsr_params *params, const float *l
  * up to iterations_per_step iterations (fewer when one of them is due
  * sooner), then retire the ones that reached their N.  Blocks until the
  * iterations are done.  Returns the number of active requests afterwards
- * (>= 0) or a negative LFSR_E* code. */
+ * (>= 0) or a negative LFSR_E* code.  Admission creates the light field's
+ * state as lfsr_create does, including the two timing launches that measure
+ * its operator units' costs; the active set's launches split their units
+ * over the CTAs by those costs. */
 int lfsr_server_step(lfsr_server *s);
 
 /* *state (LFSR_REQ_*) and *iterations of request id.  Returns LFSR_OK, the
