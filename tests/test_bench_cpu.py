@@ -53,3 +53,22 @@ def test_throttled_clock_records_are_rejected():
     # a power cap is kept; clocks far below their maximum with no reason are a lock
     assert not bench.clocks_rejected(dict(ok, sm_mhz=1700.0, reasons=["sw_power_cap"]))
     assert bench.clocks_rejected(dict(ok, sm_mhz=1200.0))
+
+
+def test_algorithmic_counts_of_the_rooflines():
+    """The benchmark's roofline numerators for the 9 x 9-view, 512^2 light field,
+    against the counts written out: streaming bytes per iteration
+    B_alg = 4 (3 s_k q + 2 s_d p + 3 p) + 4 K 11 p, and 37 FLOP per view and
+    HR pixel for one sum_k A_k^T A_k p at scale 2 with a 7-tap blur."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    from paper_2206_05047_gb300 import synth
+    wl = synth.WORKLOADS["lf9x9_256_x2"]
+    s_k, q, p, s_d, K = 81, 256 * 256, 512 * 512, 48, 5
+    assert (wl.s_k, wl.H * wl.W, wl.HR[0] * wl.HR[1], wl.s_d, wl.cg_iters) == (s_k, q, p, s_d, K)
+    assert bench.alg_bytes_per_iter(wl) == 4 * (3 * s_k * q + 2 * s_d * p + 3 * p) + 4 * K * 11 * p
+    assert bench.alg_bytes_per_iter(wl) == 225_181_696
+    # gather 8 + scatter 8 + blur 4 kb (1/2 + 1/4) = 16 + 21 = 37 FLOP per view and pixel
+    assert bench.normal_flops_per_launch(wl) == s_k * p * 37 == 785_645_568
